@@ -1,0 +1,330 @@
+"""Benchmark of the batched AM loop (one JSON line on stdout).
+
+One step = one solve of the paper-shaped workload: 1000 trajectories, 100
+steps over 10 s, 3 robot circles, 10 moving ellipses, 100 AM iterations
+(position QP, heading QP, closed-form alpha/d steps, residual, cost and
+multiplier updates), then the best-trajectory selection.  Inputs are the
+seeded synthetic workload; they are resident on the GPU before the timed
+region, and a 512 MiB buffer is rewritten between timed steps to flush L2.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank solves its own 1000-trajectory batch (weak scaling,
+no data-path collective); rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "trajectory-AM-iterations/sec at batch 1000"
+UNIT = "trajectory-iterations/s"
+WORKLOAD = "paper"
+B, ITERS = 1000, 100
+
+
+def algorithmic_flops(q: int, m: int, n: int) -> float:
+    """FP32 flops of one AM iteration for one trajectory (FMA = 2 flops),
+    counted from the formulas of the trig-free form, independent of how the
+    kernel schedules them:
+      obstacle pairs  17 per (circle, obstacle, step): scaled offset (2 FMA),
+                      squared distance (2 FMA), rsqrt, max and subtract,
+                      offset scaling (2), accumulation (2 FMA)
+      circles         16 per (circle, step): circle centre (2 FMA), residual
+                      rows (3 FMA... ) and their two weighted sums
+      bounds          16 per step: two norms, rsqrt, clips, projected values
+      trajectories    176 per step: 8 values x 11 coefficients (FMA)
+      heading         66 per step + 2 x 121: W^T delta, P^T delta, psi = P xi2
+      contraction     176 per step: R = F^T (g - F xi1), 88 dots per step
+      position step   3960: 44 rows x 44 FMA, multiplier update 44 FMA
+    """
+    return 17.0 * m * n * q + 16.0 * m * q + (16 + 176 + 66 + 176) * q + 2 * 121 * 2 + 3960.0
+
+
+def peak_fp32_tflops(sms: int = 148, clock_mhz: float = 2032.0) -> float:
+    """FP32 FMA peak: SMs x 128 lanes x 2 flops x clock."""
+    return sms * 128 * 2 * clock_mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        time.sleep(0.25)
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(pb, sample_B: int, iters: int) -> dict:
+    """The FP64 oracle (plain C, OpenMP over trajectories, all host cores) on a
+    bounded sample of the same workload."""
+    from oracle import oracle as O
+    sub = dict(pb)
+    sub["init"] = pb["init"][:sample_B]
+    sub["B"] = sample_B
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    O.solve(sub, iters, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": sample_B * iters / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{sample_B} of the {pb['B']} trajectories x {iters} iterations, {dt:.1f} s wall"}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2109_13030_b300 import workload as W
+    pb = W.make_problem(WORKLOAD, 0)
+    sample = 48
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state; warm-up steps are not needed
+    times = []
+    cb = None
+    for _ in range(args.steps):
+        cb = cpu_baseline(pb, sample, ITERS)
+        times.append(sample * ITERS / cb["value"])
+    tot = sum(times)
+    value = args.steps * sample * ITERS / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "paper-shaped: B=1000, q=100, T=10 s, m=3 circles, n=10 moving ellipses, 100 AM iterations",
+                       "reference": "FP64 CPU oracle (no reference code exists; the paper ships none)",
+                       "sample_per_step": f"{sample} trajectories x {ITERS} iterations"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
+                             "sample": cb["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--plain-steps", type=int, default=3)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_2109_13030_b300 import trajam as TJ, workload as W
+
+    rank, world, local = dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    pb = W.make_problem(WORKLOAD, seed=rank)
+    P = TJ.Problem(pb)
+    init_d = torch.tensor(pb["init"], dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        P.solve(init_d, ITERS, stream=stream)
+        TJ.am_get_best(P.h)  # argmin on the device, 36 floats back
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    launches_per_solve = TJ.am_last_solve_stats(P.h) + 1  # + argmin
+
+    # device-timed region: CUDA events around each solve on the solve's stream
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    kstarts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    kends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            starts[i].record(stream)
+            TJ.am_solve_batch(P.h, B, init_d, None, ITERS, stream)
+            kends[i].record(stream)
+            TJ.am_get_best(P.h)
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    solve_ms = [s.elapsed_time(e) for s, e in zip(starts, kends)]
+    tot_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([tot_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+        dist.barrier()
+    value = world * B * ITERS * args.steps / (tot_ms / 1e3)
+
+    # fused kernel alone: events around the kernel launch itself
+    kern_ms = []
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        # a fresh state, then time only the fused kernel (the init kernel stays outside)
+        TJ.am_solve_batch(P.h, B, init_d, None, 1, stream)
+        e0.record(stream)
+        TJ.am_solve_batch(P.h, B, None, None, ITERS, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        kern_ms.append(e0.elapsed_time(e1))
+    kern_avg = statistics.mean(kern_ms)
+    q, m, n = pb["q"], pb["m"], pb["n"]
+    flops = algorithmic_flops(q, m, n) * B * ITERS
+    clocks = clk.summary()
+    peak = peak_fp32_tflops(torch.cuda.get_device_properties(dev).multi_processor_count)
+    achieved = flops / (kern_avg / 1e3) / 1e12
+
+    # end to end through the C ABI with host buffers: pinned H2D of the
+    # initial samples, the solve, D2H of per-trajectory results and the best
+    init_h = torch.tensor(pb["init"], dtype=torch.float32).pin_memory()
+    outs = [torch.empty(B, dtype=torch.float32).pin_memory() for _ in range(4)]
+    for _ in range(2):
+        TJ.am_solve_batch(P.h, B, init_h.numpy(), None, ITERS, stream)
+        TJ.am_get_results(P.h, *[o.numpy() for o in outs])
+    e2e_s = []
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        TJ.am_solve_batch(P.h, B, init_h.numpy(), None, ITERS, stream)
+        TJ.am_get_results(P.h, *[o.numpy() for o in outs])
+        best = TJ.am_get_best(P.h)
+        e2e_s.append(time.perf_counter() - t0)
+    e2e_tot = sum(e2e_s)
+    if dist:
+        t = torch.tensor([e2e_tot], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_tot = float(t.item())
+    e2e_value = world * B * ITERS * args.steps / e2e_tot
+
+    # plain FP32 loop comparator (one launch per step), same workload
+    Pp = TJ.Problem(pb, kernel=TJ.AM_KERNEL_PLAIN)
+    Pp.solve(init_d, ITERS, stream=stream)
+    torch.cuda.synchronize()
+    plain_ms = []
+    for i in range(args.plain_steps):
+        flush.fill_(float(i))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        Pp.solve(init_d, ITERS, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        plain_ms.append(e0.elapsed_time(e1))
+    plain_launches = TJ.am_last_solve_stats(Pp.h)
+    Pp.close()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "paper-shaped: B=1000 per GPU, q=100 steps over 10 s, degree-10 Bernstein, "
+                                   "m=3 circles (r=-0.4,0,0.4), 10 moving ellipses, 100 AM iterations, "
+                                   "rho=1, then best-trajectory selection",
+                       "parallelism": f"replicas x{world} (independent batches, no collective)",
+                       "l2": "512 MiB buffer rewritten between timed steps",
+                       "kernel": "fused persistent (1 launch per solve)"},
+            "gpu_launches": launches_per_solve * args.steps,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "am_fused_kernel",
+                         "flops_per_launch": flops,
+                         "peak_basis": "derived FP32 FMA peak: SMs x 128 lanes x 2 x 2032 MHz",
+                         "kernel_ms": kern_avg},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": B * 33 * 4,
+                    "d2h_bytes_per_step": B * 4 * 4 + 36 * 4},
+            "clocks": clocks,
+            "comparators": {"plain_fp32_loop": {"value": B * ITERS / (statistics.mean(plain_ms) / 1e3),
+                                                "unit": UNIT, "ms_per_solve": statistics.mean(plain_ms),
+                                                "launches_per_solve": plain_launches}},
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(pb, 192, ITERS)
+        print(json.dumps(line), flush=True)
+    P.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

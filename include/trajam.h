@@ -1,0 +1,156 @@
+/*
+ * trajam: batched multi-convex trajectory optimization on B300 (sm_103a).
+ *
+ * C ABI of the alternating-minimization (AM) loop of "GPU Accelerated Batch
+ * Multi-Convex Trajectory Optimization for a Rectangular Holonomic Mobile
+ * Robot" (arXiv 2109.13030).  One handle describes one planning problem
+ * (Sec. II-B, Eq. acc_cost - coll_multiagent): a horizon of q steps over T
+ * seconds, a robot covered by m circles at body offsets r_i, n axis-aligned
+ * elliptical obstacles with tracks x_j(t), y_j(t), and boundary conditions
+ * shared by every trajectory of the batch.  A solve runs the AM iteration of
+ * Sec. III-D on B trajectories at once, each started from its own initial
+ * coefficients.
+ *
+ * Conventions
+ *  - Every function returns AM_OK (0) or a negative AM_ERR_* code and never
+ *    throws; am_last_error() gives a message for the calling thread.
+ *  - Pointers are borrowed for the duration of the call only.  An argument
+ *    named `mem` says whether the caller's buffers are host (AM_HOST) or
+ *    device (AM_DEVICE) memory; host buffers should be pinned for speed.
+ *  - The handle owns all of its device memory.  Calls on one handle must not
+ *    run concurrently from several host threads.
+ *  - Work is queued on the CUDA stream passed to am_solve_batch (NULL = the
+ *    legacy default stream); getters wait for that stream with a bounded
+ *    wait (AM_ERR_TIMEOUT after 60 s).
+ *  - Coefficients are degree-10 Bernstein control points (11 per polynomial)
+ *    on t in [0, T], sampled at t_k = k T / (q - 1), k = 0..q-1 (Eq. param).
+ *
+ * Per-trajectory state layout (AM_STATE_FLOATS = 110 floats):
+ *    [ 0, 44)  xi1 = (c_x, c_c, c_y, c_s)   Eq. reform_cost
+ *    [44, 55)  xi2 = c_psi
+ *    [55, 99)  lambda                        Table I
+ *    [99,110)  lambda_psi
+ */
+#ifndef TRAJAM_H
+#define TRAJAM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define AM_API __attribute__((visibility("default")))
+#else
+#define AM_API
+#endif
+
+#define AM_OK 0
+#define AM_ERR_ARG (-1)     /* invalid argument; nothing was changed        */
+#define AM_ERR_CUDA (-2)    /* a CUDA call failed                            */
+#define AM_ERR_BUDGET (-3)  /* device memory budget exceeded                 */
+#define AM_ERR_TIMEOUT (-4) /* a bounded wait expired                        */
+#define AM_ERR_NAN (-5)     /* the solve produced a non-finite value         */
+#define AM_ERR_STATE (-6)   /* call out of order (e.g. solve before obstacles) */
+
+#define AM_HOST 0
+#define AM_DEVICE 1
+
+#define AM_FP32 0           /* FP32 everywhere (the plain precision)          */
+#define AM_TF32 1           /* contractions on tensor cores in TF32          */
+#define AM_BF16 2           /* contractions on tensor cores in BF16          */
+
+#define AM_KERNEL_FUSED 0   /* one launch runs every iteration (default)     */
+#define AM_KERNEL_PLAIN 1   /* one launch per step, intermediates in memory  */
+
+#define AM_NV 11
+#define AM_STATE_FLOATS 110
+#define AM_MAX_Q 256
+#define AM_MAX_M 4
+#define AM_MAX_N 64
+
+typedef struct am_problem am_problem;
+
+typedef struct {
+    int q;                 /* planning steps, 2..AM_MAX_Q                     */
+    double T;              /* horizon in seconds, > 0                         */
+    int degree;            /* Bernstein degree; must be 10                    */
+    int m;                 /* robot circles, 1..AM_MAX_M                      */
+    const double *r;       /* m body offsets r_i of the circle centres        */
+    double r_c;            /* circle radius, added to every obstacle semi-axis */
+    double v_max, a_max;   /* speed and acceleration bounds (Eq. acc_constraint) */
+    double rho, rho_psi;   /* penalty weights (Eq. reform_bergman, update_lambda_psi) */
+    double x_bc[6], y_bc[6], psi_bc[6];  /* value, 1st, 2nd derivative at t = 0, then at t = T */
+    int precision;         /* AM_FP32 | AM_TF32 | AM_BF16                    */
+    int alpha_mode;        /* 0: alpha = atan2(a yt, b xt); 1: atan2(yt, xt) */
+    int psi_dual_sign;     /* 0: lam_psi -= rho_psi P^T (P xi2 - psi_t); 1: opposite */
+    int cs_boundary;       /* 1: slack polynomials c, s carry boundary rows  */
+} am_problem_desc;
+
+/* Create a handle: builds the Bernstein basis, the boundary matrix A and the
+ * constant parts of both KKT systems in FP64 on the host (Eq. over_1 - over_3,
+ * zeta_1_sepration_3, compute_convex_surrogate).  The first CUDA call of the
+ * process happens here, on the current device. */
+AM_API int am_init_problem(const am_problem_desc *desc, am_problem **out);
+
+/* Set the n obstacles (0 <= n <= AM_MAX_N): centre tracks xo, yo of n x q
+ * floats (row j = obstacle j over the q steps) and semi-axes a, b of n floats
+ * each, before inflation by r_c (Eq. coll_multiagent).  Re-forms the position
+ * KKT inverse when n changes, since F^T F depends on n (Sec. IV-E). */
+AM_API int am_set_obstacles(am_problem *h, int n, const float *xo, const float *yo, const float *a,
+                     const float *b, int mem);
+
+/* Replace the shared boundary conditions (the MPC re-plan of Sec. IV). */
+AM_API int am_set_boundary(am_problem *h, const double x_bc[6], const double y_bc[6],
+                    const double psi_bc[6]);
+
+/* Run `iters` (>= 1) AM iterations on B (>= 1) trajectories.
+ *  init         B x 3 x 11 floats: c_x, c_y, c_psi per trajectory (cold start,
+ *               multipliers zero unless warm_lambda is given); NULL continues
+ *               from the state the handle holds (warm start, same B).
+ *  warm_lambda  NULL, or B x 55 floats: lambda (44) then lambda_psi (11).
+ *  stream       cudaStream_t the work is queued on.
+ * Results stay on the device until read with the getters. */
+AM_API int am_solve_batch(am_problem *h, int B, const float *init, const float *warm_lambda, int iters,
+                   void *stream, int mem);
+
+/* Per-trajectory results of the last solve, each B floats (NULL to skip):
+ * final residual ||F xi1 - g||_2, heading residual ||P xi2 - psi_t||_2, cost
+ * sum_t xdd^2 + ydd^2 + psidd^2 (Eq. acc_cost), and the smallest ellipse
+ * distance sqrt(xt^2/a^2 + yt^2/b^2) over circles, obstacles and steps. */
+AM_API int am_get_results(am_problem *h, float *res, float *res_psi, float *cost, float *mind, int mem);
+
+/* The best trajectory of the last solve: lowest cost among those whose
+ * smallest ellipse distance is >= 0.99, else lowest cost overall; ties go to
+ * the lower index (Fig. 1's best-cost trajectory).  coeffs gets c_x, c_y,
+ * c_psi (33 floats, host memory). */
+AM_API int am_get_best(am_problem *h, float coeffs[33], float *cost, float *residual, int *index);
+
+/* Copy the B x AM_STATE_FLOATS state out of / into the handle. */
+AM_API int am_get_state(am_problem *h, float *out, int mem);
+AM_API int am_set_state(am_problem *h, int B, const float *in, int mem);
+
+/* Per-iteration history: when enabled, solves record (res, res_psi, cost)
+ * per trajectory and iteration; am_get_history copies B x iters x 3 floats. */
+AM_API int am_set_history(am_problem *h, int enable);
+AM_API int am_get_history(am_problem *h, float *out, int mem);
+
+/* Options.  AM_OPT_KERNEL: AM_KERNEL_FUSED or AM_KERNEL_PLAIN.
+ * AM_OPT_TILE: trajectories per CTA of the fused kernel (0 = automatic). */
+#define AM_OPT_KERNEL 1
+#define AM_OPT_TILE 2
+AM_API int am_set_option(am_problem *h, int option, int value);
+
+/* Stream used by calls that take none (am_set_obstacles, am_set_boundary,
+ * getters); am_solve_batch also sets it to the stream it is given. */
+AM_API int am_set_stream(am_problem *h, void *stream);
+
+/* Number of kernels the last am_solve_batch launched. */
+AM_API int am_last_solve_stats(am_problem *h, int *launches);
+
+AM_API void am_destroy(am_problem *h);
+AM_API const char *am_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,457 @@
+// C ABI of the batched AM solver (include/trajam.h): handle lifetime, argument
+// checking, device buffers and the launches of one solve.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "am_internal.h"
+#include "../../include/trajam.h"
+
+using namespace trajam;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(AM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                  \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+template <typename T>
+int ensure(T *&ptr, size_t &cap, size_t count, const char *what)
+{
+    if (count <= cap && ptr) return AM_OK;
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    cap = 0;
+    size_t n = count ? count : 1;
+    CK(cudaMalloc(&ptr, n * sizeof(T)), what);
+    cap = n;
+    return AM_OK;
+}
+
+}  // namespace
+
+struct am_problem {
+    ProblemParams pp;
+    HostSetup S;
+    ConstLayout L;
+    std::vector<float> blob;
+    float *d_blob = nullptr;
+    size_t blob_cap = 0;
+    int n = 0;
+    float *d_raw = nullptr;  // raw obstacles: xo, yo (n x q each), a, b
+    size_t raw_cap = 0;
+    int B = 0;
+    float *d_state = nullptr, *d_out = nullptr, *d_best = nullptr, *d_in = nullptr;
+    size_t state_cap = 0, out_cap = 0, best_cap = 0, in_cap = 0;
+    float *d_hist = nullptr;
+    size_t hist_cap = 0;
+    float *d_scratch = nullptr;
+    size_t scratch_cap = 0;
+    int *d_err = nullptr;
+    size_t err_cap = 0;
+    bool hist_on = false;
+    int hist_iters = 0;
+    int kernel = AM_KERNEL_FUSED;
+    int tile = 0;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev = nullptr;
+    int launches = 0;
+    bool solved = false;
+    float *h_best = nullptr;  // pinned
+};
+
+namespace {
+
+int wait_stream(am_problem *h)
+{
+    CK(cudaEventRecord(h->ev, h->stream), "cudaEventRecord");
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        const cudaError_t e = cudaEventQuery(h->ev);
+        if (e == cudaSuccess) break;
+        if (e != cudaErrorNotReady) return cuda_fail(e, "stream wait");
+        if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(60))
+            return fail(AM_ERR_TIMEOUT, "stream did not finish within 60 s");
+        std::this_thread::yield();
+    }
+    int err = 0;
+    CK(cudaMemcpy(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost), "status read");
+    if (err) return fail(AM_ERR_TIMEOUT, "a kernel gave up a bounded wait (status %d)", err);
+    return AM_OK;
+}
+
+cudaMemcpyKind kind_in(int mem) { return mem == AM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; }
+cudaMemcpyKind kind_out(int mem) { return mem == AM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost; }
+
+bool finite_all(const double *v, int n)
+{
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
+// Uploads the non-obstacle sections of the constant block.
+int upload_shape_sections(am_problem *h)
+{
+    fill_constants(h->S, h->pp, h->L, h->blob);
+    return cudaMemcpyAsync(h->d_blob, h->blob.data(), size_t(h->L.off_obs) * sizeof(float),
+                           cudaMemcpyHostToDevice, h->stream) == cudaSuccess
+               ? AM_OK
+               : fail(AM_ERR_CUDA, "constant upload failed");
+}
+
+void set_scalars(am_problem *h)
+{
+    ConstLayout &L = h->L;
+    L.rho = float(h->pp.rho);
+    L.rho_psi = float(h->pp.rho_psi);
+    L.v_max = float(h->pp.v_max);
+    L.a_max = float(h->pp.a_max);
+    for (int i = 0; i < MAXM; ++i) L.r[i] = i < h->pp.m ? float(h->pp.r[i]) : 0.f;
+    L.psi_sign = h->pp.psi_dual_sign ? -1.f : 1.f;
+    L.alpha_mode = h->pp.alpha_mode;
+    L.cs_boundary = h->pp.cs_boundary;
+}
+
+// (Re)forms the setup for n obstacles: FP64 setup, layout, device block.
+int reshape(am_problem *h, int n)
+{
+    HostSetup S;
+    if (build_setup(h->pp, n, S) != 0) return fail(AM_ERR_ARG, "singular KKT matrix");
+    h->S = S;
+    h->n = n;
+    h->L = make_layout(h->pp.q, h->pp.m, n);
+    set_scalars(h);
+    int rc = ensure(h->d_blob, h->blob_cap, size_t(h->L.total), "constant block");
+    if (rc) return rc;
+    CK(cudaMemsetAsync(h->d_blob, 0, size_t(h->L.total) * sizeof(float), h->stream), "memset");
+    return upload_shape_sections(h);
+}
+
+int check_B(am_problem *h, int B)
+{
+    int rc = ensure(h->d_state, h->state_cap, size_t(B) * STATE, "state");
+    if (!rc) rc = ensure(h->d_out, h->out_cap, size_t(B) * 4, "results");
+    if (!rc) rc = ensure(h->d_in, h->in_cap, size_t(B) * (33 + 55), "input staging");
+    if (!rc) rc = ensure(h->d_best, h->best_cap, size_t(64), "best");
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *am_last_error(void) { return g_err.c_str(); }
+
+int am_init_problem(const am_problem_desc *d, am_problem **out)
+{
+    if (!d || !out) return fail(AM_ERR_ARG, "null argument");
+    *out = nullptr;
+    if (d->q < 2 || d->q > AM_MAX_Q) return fail(AM_ERR_ARG, "q must be in [2, %d]", AM_MAX_Q);
+    if (!(d->T > 0) || !std::isfinite(d->T)) return fail(AM_ERR_ARG, "T must be > 0");
+    if (d->degree != 10) return fail(AM_ERR_ARG, "only degree 10 is supported");
+    if (d->m < 1 || d->m > AM_MAX_M || !d->r) return fail(AM_ERR_ARG, "m must be in [1, %d]", AM_MAX_M);
+    if (!finite_all(d->r, d->m)) return fail(AM_ERR_ARG, "non-finite r");
+    if (!(d->r_c >= 0) || !(d->v_max > 0) || !(d->a_max > 0) || !(d->rho > 0) || !(d->rho_psi > 0))
+        return fail(AM_ERR_ARG, "r_c >= 0 and v_max, a_max, rho, rho_psi > 0 required");
+    if (!finite_all(d->x_bc, 6) || !finite_all(d->y_bc, 6) || !finite_all(d->psi_bc, 6))
+        return fail(AM_ERR_ARG, "non-finite boundary condition");
+    if (d->precision != AM_FP32) return fail(AM_ERR_ARG, "precision %d not available", d->precision);
+    if (d->alpha_mode < 0 || d->alpha_mode > 1 || d->psi_dual_sign < 0 || d->psi_dual_sign > 1 ||
+        d->cs_boundary < 0 || d->cs_boundary > 1)
+        return fail(AM_ERR_ARG, "flag out of range");
+    am_problem *h = new (std::nothrow) am_problem;
+    if (!h) return fail(AM_ERR_ARG, "out of host memory");
+    ProblemParams &pp = h->pp;
+    pp.q = d->q;
+    pp.T = d->T;
+    pp.m = d->m;
+    for (int i = 0; i < d->m; ++i) pp.r[i] = d->r[i];
+    pp.r_c = d->r_c;
+    pp.v_max = d->v_max;
+    pp.a_max = d->a_max;
+    pp.rho = d->rho;
+    pp.rho_psi = d->rho_psi;
+    std::memcpy(pp.x_bc, d->x_bc, sizeof(pp.x_bc));
+    std::memcpy(pp.y_bc, d->y_bc, sizeof(pp.y_bc));
+    std::memcpy(pp.psi_bc, d->psi_bc, sizeof(pp.psi_bc));
+    pp.alpha_mode = d->alpha_mode;
+    pp.psi_dual_sign = d->psi_dual_sign;
+    pp.cs_boundary = d->cs_boundary;
+    pp.precision = d->precision;
+    int rc = AM_OK;
+    cudaError_t e = cudaFree(nullptr);
+    if (e != cudaSuccess) rc = cuda_fail(e, "CUDA initialisation");
+    if (!rc && cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming) != cudaSuccess)
+        rc = fail(AM_ERR_CUDA, "event creation failed");
+    if (!rc && cudaMallocHost(&h->h_best, 64 * sizeof(float)) != cudaSuccess)
+        rc = fail(AM_ERR_CUDA, "pinned allocation failed");
+    if (!rc) rc = ensure(h->d_err, h->err_cap, 1, "status word");
+    if (!rc && cudaMemset(h->d_err, 0, sizeof(int)) != cudaSuccess) rc = fail(AM_ERR_CUDA, "memset");
+    if (!rc) rc = reshape(h, 0);
+    if (!rc && cudaStreamSynchronize(h->stream) != cudaSuccess) rc = fail(AM_ERR_CUDA, "sync");
+    if (rc) {
+        am_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return AM_OK;
+}
+
+void am_destroy(am_problem *h)
+{
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    cudaFree(h->d_blob);
+    cudaFree(h->d_raw);
+    cudaFree(h->d_state);
+    cudaFree(h->d_out);
+    cudaFree(h->d_best);
+    cudaFree(h->d_in);
+    cudaFree(h->d_hist);
+    cudaFree(h->d_scratch);
+    cudaFree(h->d_err);
+    if (h->h_best) cudaFreeHost(h->h_best);
+    if (h->ev) cudaEventDestroy(h->ev);
+    delete h;
+}
+
+int am_set_stream(am_problem *h, void *stream)
+{
+    if (!h) return fail(AM_ERR_ARG, "null handle");
+    h->stream = static_cast<cudaStream_t>(stream);
+    return AM_OK;
+}
+
+int am_set_obstacles(am_problem *h, int n, const float *xo, const float *yo, const float *a,
+                     const float *b, int mem)
+{
+    if (!h) return fail(AM_ERR_ARG, "null handle");
+    if (n < 0 || n > AM_MAX_N) return fail(AM_ERR_ARG, "n must be in [0, %d]", AM_MAX_N);
+    if (n > 0 && (!xo || !yo || !a || !b)) return fail(AM_ERR_ARG, "null obstacle array");
+    if (mem != AM_HOST && mem != AM_DEVICE) return fail(AM_ERR_ARG, "bad mem flag");
+    const int q = h->pp.q;
+    if (mem == AM_HOST)
+        for (int j = 0; j < n; ++j)
+            if (!(a[j] > 0) || !(b[j] > 0) || !std::isfinite(a[j]) || !std::isfinite(b[j]))
+                return fail(AM_ERR_ARG, "semi-axes must be finite and > 0");
+    int rc;
+    if (n != h->n) {
+        rc = reshape(h, n);
+        if (rc) return rc;
+    }
+    if (n == 0) return AM_OK;
+    rc = ensure(h->d_raw, h->raw_cap, size_t(2 * n * q + 2 * n), "obstacles");
+    if (rc) return rc;
+    const cudaMemcpyKind k = kind_in(mem);
+    CK(cudaMemcpyAsync(h->d_raw, xo, sizeof(float) * n * q, k, h->stream), "obstacle copy");
+    CK(cudaMemcpyAsync(h->d_raw + n * q, yo, sizeof(float) * n * q, k, h->stream), "obstacle copy");
+    CK(cudaMemcpyAsync(h->d_raw + 2 * n * q, a, sizeof(float) * n, k, h->stream), "obstacle copy");
+    CK(cudaMemcpyAsync(h->d_raw + 2 * n * q + n, b, sizeof(float) * n, k, h->stream), "obstacle copy");
+    if (launch_prep_obstacles(h->d_blob, h->L, h->d_raw, h->d_raw + n * q, h->d_raw + 2 * n * q,
+                              h->d_raw + 2 * n * q + n, float(h->pp.r_c), h->stream, nullptr))
+        return fail(AM_ERR_CUDA, "obstacle preparation launch failed");
+    return AM_OK;
+}
+
+int am_set_boundary(am_problem *h, const double x_bc[6], const double y_bc[6],
+                    const double psi_bc[6])
+{
+    if (!h || !x_bc || !y_bc || !psi_bc) return fail(AM_ERR_ARG, "null argument");
+    if (!finite_all(x_bc, 6) || !finite_all(y_bc, 6) || !finite_all(psi_bc, 6))
+        return fail(AM_ERR_ARG, "non-finite boundary condition");
+    std::memcpy(h->pp.x_bc, x_bc, sizeof(h->pp.x_bc));
+    std::memcpy(h->pp.y_bc, y_bc, sizeof(h->pp.y_bc));
+    std::memcpy(h->pp.psi_bc, psi_bc, sizeof(h->pp.psi_bc));
+    if (rebuild_boundary(h->pp, h->S) != 0) return fail(AM_ERR_ARG, "singular KKT matrix");
+    return upload_shape_sections(h);
+}
+
+int am_set_option(am_problem *h, int option, int value)
+{
+    if (!h) return fail(AM_ERR_ARG, "null handle");
+    if (option == AM_OPT_KERNEL) {
+        if (value != AM_KERNEL_FUSED && value != AM_KERNEL_PLAIN) return fail(AM_ERR_ARG, "bad kernel");
+        h->kernel = value;
+        return AM_OK;
+    }
+    if (option == AM_OPT_TILE) {
+        if (value < 0 || value > 64) return fail(AM_ERR_ARG, "tile must be in [0, 64]");
+        h->tile = value;
+        return AM_OK;
+    }
+    return fail(AM_ERR_ARG, "unknown option %d", option);
+}
+
+int am_set_history(am_problem *h, int enable)
+{
+    if (!h) return fail(AM_ERR_ARG, "null handle");
+    h->hist_on = enable != 0;
+    return AM_OK;
+}
+
+int am_solve_batch(am_problem *h, int B, const float *init, const float *warm_lambda, int iters,
+                   void *stream, int mem)
+{
+    if (!h) return fail(AM_ERR_ARG, "null handle");
+    if (B < 1 || B > (1 << 24)) return fail(AM_ERR_ARG, "B must be in [1, 2^24]");
+    if (iters < 1 || iters > 100000) return fail(AM_ERR_ARG, "iters must be in [1, 100000]");
+    if (mem != AM_HOST && mem != AM_DEVICE) return fail(AM_ERR_ARG, "bad mem flag");
+    if (!init && (!h->solved || B != h->B))
+        return fail(AM_ERR_STATE, "warm start needs a previous solve with the same B");
+    if (!init && warm_lambda) return fail(AM_ERR_ARG, "warm_lambda needs init");
+    h->stream = static_cast<cudaStream_t>(stream);
+    h->launches = 0;
+    int rc = check_B(h, B);
+    if (rc) return rc;
+    if (init) {
+        CK(cudaMemcpyAsync(h->d_in, init, sizeof(float) * 33 * B, kind_in(mem), h->stream), "init copy");
+        const float *warm = nullptr;
+        if (warm_lambda) {
+            CK(cudaMemcpyAsync(h->d_in + 33 * size_t(B), warm_lambda, sizeof(float) * 55 * B,
+                               kind_in(mem), h->stream),
+               "warm copy");
+            warm = h->d_in + 33 * size_t(B);
+        }
+        if (launch_init_state(h->d_state, h->d_in, warm, B, h->stream, &h->launches))
+            return fail(AM_ERR_CUDA, "init launch failed");
+    }
+    h->B = B;
+    float *hist = nullptr;
+    if (h->hist_on) {
+        rc = ensure(h->d_hist, h->hist_cap, size_t(B) * iters * 3, "history");
+        if (rc) return rc;
+        hist = h->d_hist;
+        h->hist_iters = iters;
+    }
+    SolveArgs a;
+    a.cblob = h->d_blob;
+    a.L = h->L;
+    a.B = B;
+    a.iters = iters;
+    a.state = h->d_state;
+    a.res = h->d_out;
+    a.res_psi = h->d_out + B;
+    a.cost = h->d_out + 2 * size_t(B);
+    a.mind = h->d_out + 3 * size_t(B);
+    a.hist = hist;
+    a.tile = h->tile;
+    a.err = h->d_err;
+    if (h->kernel == AM_KERNEL_FUSED) {
+        rc = launch_fused(a, h->stream, &h->launches);
+    } else {
+        const size_t need = plain_scratch_floats(h->L, B);
+        rc = ensure(h->d_scratch, h->scratch_cap, need, "plain scratch");
+        if (rc) return rc;
+        rc = launch_plain(a, h->d_scratch, h->scratch_cap, h->stream, &h->launches);
+    }
+    if (rc == -1) return fail(AM_ERR_ARG, "problem shape does not fit the kernel (tile %d)", h->tile);
+    if (rc) return fail(AM_ERR_CUDA, "solve launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    h->solved = true;
+    return AM_OK;
+}
+
+int am_get_results(am_problem *h, float *res, float *res_psi, float *cost, float *mind, int mem)
+{
+    if (!h) return fail(AM_ERR_ARG, "null handle");
+    if (!h->solved) return fail(AM_ERR_STATE, "no solve yet");
+    if (mem != AM_HOST && mem != AM_DEVICE) return fail(AM_ERR_ARG, "bad mem flag");
+    float *dst[4] = {res, res_psi, cost, mind};
+    for (int i = 0; i < 4; ++i)
+        if (dst[i])
+            CK(cudaMemcpyAsync(dst[i], h->d_out + size_t(i) * h->B, sizeof(float) * h->B,
+                               kind_out(mem), h->stream),
+               "result copy");
+    return mem == AM_HOST ? wait_stream(h) : AM_OK;
+}
+
+int am_get_best(am_problem *h, float coeffs[33], float *cost, float *residual, int *index)
+{
+    if (!h) return fail(AM_ERR_ARG, "null handle");
+    if (!h->solved) return fail(AM_ERR_STATE, "no solve yet");
+    if (launch_argmin(h->d_state, h->d_out + 2 * size_t(h->B), h->d_out, h->d_out + 3 * size_t(h->B),
+                      h->B, h->d_best, h->stream, nullptr))
+        return fail(AM_ERR_CUDA, "argmin launch failed");
+    CK(cudaMemcpyAsync(h->h_best, h->d_best, 36 * sizeof(float), cudaMemcpyDeviceToHost, h->stream),
+       "best copy");
+    int rc = wait_stream(h);
+    if (rc) return rc;
+    if (index) *index = int(h->h_best[0]);
+    if (cost) *cost = h->h_best[1];
+    if (residual) *residual = h->h_best[2];
+    if (coeffs) std::memcpy(coeffs, h->h_best + 3, 33 * sizeof(float));
+    return AM_OK;
+}
+
+int am_get_state(am_problem *h, float *out, int mem)
+{
+    if (!h || !out) return fail(AM_ERR_ARG, "null argument");
+    if (!h->solved) return fail(AM_ERR_STATE, "no state yet");
+    if (mem != AM_HOST && mem != AM_DEVICE) return fail(AM_ERR_ARG, "bad mem flag");
+    CK(cudaMemcpyAsync(out, h->d_state, sizeof(float) * STATE * h->B, kind_out(mem), h->stream),
+       "state copy");
+    return mem == AM_HOST ? wait_stream(h) : AM_OK;
+}
+
+int am_set_state(am_problem *h, int B, const float *in, int mem)
+{
+    if (!h || !in) return fail(AM_ERR_ARG, "null argument");
+    if (B < 1 || B > (1 << 24)) return fail(AM_ERR_ARG, "B must be in [1, 2^24]");
+    if (mem != AM_HOST && mem != AM_DEVICE) return fail(AM_ERR_ARG, "bad mem flag");
+    int rc = check_B(h, B);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(h->d_state, in, sizeof(float) * STATE * B, kind_in(mem), h->stream),
+       "state copy");
+    h->B = B;
+    h->solved = true;
+    return AM_OK;
+}
+
+int am_get_history(am_problem *h, float *out, int mem)
+{
+    if (!h || !out) return fail(AM_ERR_ARG, "null argument");
+    if (!h->solved || !h->d_hist || h->hist_iters == 0) return fail(AM_ERR_STATE, "no history");
+    if (mem != AM_HOST && mem != AM_DEVICE) return fail(AM_ERR_ARG, "bad mem flag");
+    CK(cudaMemcpyAsync(out, h->d_hist, sizeof(float) * 3 * h->hist_iters * size_t(h->B),
+                       kind_out(mem), h->stream),
+       "history copy");
+    return mem == AM_HOST ? wait_stream(h) : AM_OK;
+}
+
+int am_last_solve_stats(am_problem *h, int *launches)
+{
+    if (!h || !launches) return fail(AM_ERR_ARG, "null argument");
+    *launches = h->launches;
+    return AM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,124 @@
+// Internal declarations shared by the host setup, the kernels and the C ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+namespace trajam {
+
+constexpr int NV = 11;        // coefficients per polynomial (degree 10)
+constexpr int NS = 22;        // unknowns per side: (c_pos, c_slack)
+constexpr int NX = 44;        // xi1
+constexpr int STATE = 110;    // xi1, xi2, lambda, lambda_psi
+constexpr int MAXM = 4;
+
+// ---------------------------------------------------------------- host FP64
+
+struct ProblemParams {
+    int q = 0;
+    double T = 0;
+    int m = 0;
+    double r[MAXM] = {0, 0, 0, 0};
+    double r_c = 0, v_max = 0, a_max = 0, rho = 1, rho_psi = 1;
+    double x_bc[6] = {}, y_bc[6] = {}, psi_bc[6] = {};
+    int alpha_mode = 0, psi_dual_sign = 0, cs_boundary = 1, precision = 0;
+};
+
+// Everything the device needs that depends only on the problem shape, formed
+// in FP64 on the host.
+struct HostSetup {
+    int q = 0, n = 0;
+    std::vector<double> P, Pd, Pdd;          // q x NV, row-major
+    double H[NV][NV];                         // Pdd^T Pdd
+    double PtP[NV][NV];                       // P^T P
+    double FtF[NS][NS];                       // per-side F^T F
+    double Minv[NS][NS];                      // K^{-1}[:22, :22] of the position KKT
+    double MQ[NS][NS];                        // Minv * blockdiag(H, H)
+    double kb[2][NS];                         // K^{-1}[:22, 22:] b_side (x then y side)
+    double ends[5][6];                        // boundary control points c_0,c_1,c_2,c_8,c_9,c_10
+                                              // of c_x, c_c, c_y, c_s, c_psi
+    double Mpsi[NV][NV];                      // K_psi^{-1}[:11, :11]
+    double MpsiH[NV][NV];                     // Mpsi * H
+    double kbpsi[NV];                         // K_psi^{-1}[:11, 11:] b_psi
+    std::vector<double> W;                    // q x NV: W = P Mpsi^T
+    double cond_pos = 0, cond_psi = 0;        // inf-norm condition estimates
+};
+
+// Bernstein basis and derivatives on t_k = k T / (q - 1).
+void bernstein_basis(int q, double T, std::vector<double> &P, std::vector<double> &Pd,
+                     std::vector<double> &Pdd);
+
+// Forms every matrix of HostSetup for the given problem and obstacle count.
+// Returns 0, or -1 when a KKT matrix is singular.
+int build_setup(const ProblemParams &pp, int n, HostSetup &S);
+
+// Recomputes only the boundary-dependent vectors kb, kbpsi.
+int rebuild_boundary(const ProblemParams &pp, HostSetup &S);
+
+// ------------------------------------------------------------ device layout
+
+// Offsets (in floats) of the sections of the constant block the kernels stage
+// into shared memory.  Every section starts on a 16-byte boundary.
+struct ConstLayout {
+    int q, qs, m, n;          // qs: padded stride of per-step columns
+    int off_prow;             // [3][q][12]   P, Pd, Pdd rows (padded to 12)
+    int off_pcol;             // [3][NV][qs]  P, Pd, Pdd columns
+    int off_wcol;             // [NV][qs]     W = P Mpsi^T, columns
+    int off_mt;               // [NS][24]     Minv^T
+    int off_mq;               // [NS][24]     (Minv blockdiag(H, H))^T
+    int off_ends;             // [5][8]       boundary control points per block (xi1 blocks, c_psi)
+    int off_kb;               // [2][24]      kb (x side, y side)
+    int off_mpsi;             // [NV][12]     Mpsi^T
+    int off_mpsih;            // [NV][12]     (Mpsi H)^T
+    int off_ptp;              // [NV][12]     P^T P
+    int off_kbpsi;            // [12]
+    int off_obs;              // [n][qs][2]   (x_j(t)/a_j, y_j(t)/b_j) pairs
+    int off_obc;              // [n][4]       1/a_j, 1/b_j, a_j, b_j (inflated)
+    int total;                // floats, multiple of 4
+    float rho, rho_psi, v_max, a_max;
+    float r[MAXM];
+    float psi_sign;           // +1 default reading, -1 printed sign
+    int alpha_mode;
+    int cs_boundary;          // slack blocks carry boundary rows
+};
+
+ConstLayout make_layout(int q, int m, int n);
+// Writes the shape-dependent sections (everything except the obstacles).
+void fill_constants(const HostSetup &S, const ProblemParams &pp, const ConstLayout &L,
+                    std::vector<float> &blob);
+
+// ------------------------------------------------------------ launchers
+
+struct SolveArgs {
+    const float *cblob;       // device constant block (ConstLayout)
+    ConstLayout L;
+    int B, iters;
+    float *state;             // B x STATE, in/out
+    float *res, *res_psi, *cost, *mind;  // B each
+    float *hist;              // B x iters x 3, or nullptr
+    int tile;                 // trajectories per CTA (0 = automatic)
+    int *err;                 // device status word; kernels set it on a failed wait
+};
+
+// Fused persistent kernel: every iteration of the loop in one launch.
+int launch_fused(const SolveArgs &a, void *stream, int *launches);
+// Unfused comparator: one launch per step, intermediates in global memory.
+int launch_plain(const SolveArgs &a, float *scratch, size_t scratch_floats, void *stream,
+                 int *launches);
+size_t plain_scratch_floats(const ConstLayout &L, int B);
+// Best-trajectory selection; writes {index, cost, res, 33 coefficients}.
+int launch_argmin(const float *state, const float *cost, const float *res, const float *mind,
+                  int B, float *best_out, void *stream, int *launches);
+// Converts raw obstacle arrays (device) into the kernel's obstacle sections.
+int launch_prep_obstacles(float *cblob, const ConstLayout &L, const float *xo, const float *yo,
+                          const float *a, const float *b, float r_c, void *stream, int *launches);
+// Builds the initial state from B x 3 x 11 coefficients (+ optional lambdas);
+// the slack control points start at cos / sin of the heading control points.
+int launch_init_state(float *state, const float *init, const float *warm, int B, void *stream,
+                      int *launches);
+// Fused kernel tile selection, exposed for the autotuner.
+int fused_auto_tile(const ConstLayout &L, int B, int num_sms);
+size_t fused_smem_bytes(const ConstLayout &L, int tile);
+
+}  // namespace trajam

@@ -1,0 +1,270 @@
+"""Thin ctypes binding of libtrajam.so (include/trajam.h).
+
+Functions carry the C names and only marshal arguments: numpy arrays are
+passed as host memory (AM_HOST), torch CUDA tensors as device memory
+(AM_DEVICE).  There is no fallback: if the library is missing or fails to
+load, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtrajam.so")
+
+AM_OK, AM_ERR_ARG, AM_ERR_CUDA, AM_ERR_BUDGET, AM_ERR_TIMEOUT, AM_ERR_NAN, AM_ERR_STATE = 0, -1, -2, -3, -4, -5, -6
+AM_HOST, AM_DEVICE = 0, 1
+AM_FP32, AM_TF32, AM_BF16 = 0, 1, 2
+AM_KERNEL_FUSED, AM_KERNEL_PLAIN = 0, 1
+AM_OPT_KERNEL, AM_OPT_TILE = 1, 2
+AM_NV, AM_STATE_FLOATS = 11, 110
+
+EXPORTS = ["am_init_problem", "am_set_obstacles", "am_set_boundary", "am_solve_batch",
+           "am_get_results", "am_get_best", "am_get_state", "am_set_state", "am_set_history",
+           "am_get_history", "am_set_option", "am_set_stream", "am_last_solve_stats",
+           "am_destroy", "am_last_error"]
+
+
+class AmProblemDesc(C.Structure):
+    _fields_ = [("q", C.c_int), ("T", C.c_double), ("degree", C.c_int), ("m", C.c_int),
+                ("r", C.POINTER(C.c_double)), ("r_c", C.c_double),
+                ("v_max", C.c_double), ("a_max", C.c_double), ("rho", C.c_double),
+                ("rho_psi", C.c_double), ("x_bc", C.c_double * 6), ("y_bc", C.c_double * 6),
+                ("psi_bc", C.c_double * 6), ("precision", C.c_int), ("alpha_mode", C.c_int),
+                ("psi_dual_sign", C.c_int), ("cs_boundary", C.c_int)]
+
+
+class TrajamError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"trajam error {code}: {msg}")
+        self.code = code
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} not built; run paper_2109_13030_b300/build.py")
+    lib = C.CDLL(LIB_PATH)
+    vp, ip, fp, dp = C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_double)
+    sig = {
+        "am_init_problem": ([C.POINTER(AmProblemDesc), C.POINTER(vp)], ip),
+        "am_set_obstacles": ([vp, ip, fp, fp, fp, fp, ip], ip),
+        "am_set_boundary": ([vp, dp, dp, dp], ip),
+        "am_solve_batch": ([vp, ip, fp, fp, ip, vp, ip], ip),
+        "am_get_results": ([vp, fp, fp, fp, fp, ip], ip),
+        "am_get_best": ([vp, fp, C.POINTER(C.c_float), C.POINTER(C.c_float), C.POINTER(C.c_int)], ip),
+        "am_get_state": ([vp, fp, ip], ip),
+        "am_set_state": ([vp, ip, fp, ip], ip),
+        "am_set_history": ([vp, ip], ip),
+        "am_get_history": ([vp, fp, ip], ip),
+        "am_set_option": ([vp, ip, ip], ip),
+        "am_set_stream": ([vp, vp], ip),
+        "am_last_solve_stats": ([vp, C.POINTER(C.c_int)], ip),
+        "am_destroy": ([vp], None),
+        "am_last_error": ([], C.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+_lib = _load()
+
+
+def _check(rc):
+    if rc != AM_OK:
+        raise TrajamError(rc, _lib.am_last_error().decode())
+    return rc
+
+
+def _buf(a, dtype=np.float32):
+    """(pointer, mem flag, keep-alive) for a numpy array, a torch tensor or None."""
+    if a is None:
+        return None, AM_HOST, None
+    if isinstance(a, np.ndarray):
+        arr = np.ascontiguousarray(a, dtype=dtype)
+        return arr.ctypes.data, AM_HOST, arr
+    # torch tensor
+    if not a.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    if a.is_cuda:
+        return a.data_ptr(), AM_DEVICE, a
+    return a.data_ptr(), AM_HOST, a
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def make_desc(pb: dict, precision=AM_FP32, alpha_mode=0, psi_dual_sign=0, cs_boundary=1):
+    d = AmProblemDesc()
+    d.q, d.T, d.degree, d.m = int(pb["q"]), float(pb["T"]), int(pb.get("degree", 10)), int(pb["m"])
+    r = (C.c_double * d.m)(*[float(v) for v in pb["r"]])
+    d.r = C.cast(r, C.POINTER(C.c_double))
+    d._keep = r
+    d.r_c, d.v_max, d.a_max = float(pb["r_c"]), float(pb["v_max"]), float(pb["a_max"])
+    d.rho, d.rho_psi = float(pb["rho"]), float(pb["rho_psi"])
+    for name in ("x_bc", "y_bc", "psi_bc"):
+        arr = getattr(d, name)
+        for i, v in enumerate(pb[name]):
+            arr[i] = float(v)
+    d.precision, d.alpha_mode, d.psi_dual_sign, d.cs_boundary = precision, alpha_mode, psi_dual_sign, cs_boundary
+    return d
+
+
+# ------------------------------------------------------------ C-named calls
+
+def am_init_problem(desc: AmProblemDesc) -> int:
+    h = C.c_void_p()
+    _check(_lib.am_init_problem(C.byref(desc), C.byref(h)))
+    return h.value
+
+
+def am_set_obstacles(h, n, xo, yo, a, b):
+    px, mem, kx = _buf(xo)
+    py, _, ky = _buf(yo)
+    pa, _, ka = _buf(a)
+    pb_, _, kb = _buf(b)
+    _check(_lib.am_set_obstacles(h, int(n), px, py, pa, pb_, mem))
+
+
+def am_set_boundary(h, x_bc, y_bc, psi_bc):
+    arrs = [np.ascontiguousarray(v, dtype=np.float64) for v in (x_bc, y_bc, psi_bc)]
+    ptrs = [a.ctypes.data_as(C.POINTER(C.c_double)) for a in arrs]
+    _check(_lib.am_set_boundary(h, *ptrs))
+
+
+def am_solve_batch(h, B, init, warm_lambda, iters, stream=None):
+    pi, mem, ki = _buf(init)
+    pw, memw, kw = _buf(warm_lambda)
+    if init is not None and warm_lambda is not None and mem != memw:
+        raise ValueError("init and warm_lambda must both be host or both be device memory")
+    _check(_lib.am_solve_batch(h, int(B), pi, pw, int(iters), _stream_ptr(stream), mem))
+
+
+def am_get_results(h, res=None, res_psi=None, cost=None, mind=None):
+    bufs = [_buf(x) for x in (res, res_psi, cost, mind)]
+    mems = {m for (p, m, k) in bufs if p is not None}
+    if len(mems) > 1:
+        raise ValueError("outputs must all be host or all be device memory")
+    mem = mems.pop() if mems else AM_HOST
+    _check(_lib.am_get_results(h, *[p for (p, m, k) in bufs], mem))
+
+
+def am_get_best(h):
+    coeffs = np.zeros(33, dtype=np.float32)
+    cost, res, idx = C.c_float(), C.c_float(), C.c_int()
+    _check(_lib.am_get_best(h, coeffs.ctypes.data, C.byref(cost), C.byref(res), C.byref(idx)))
+    return dict(coeffs=coeffs.reshape(3, 11), cost=cost.value, res=res.value, index=idx.value)
+
+
+def am_get_state(h, out):
+    p, mem, k = _buf(out)
+    _check(_lib.am_get_state(h, p, mem))
+
+
+def am_set_state(h, B, state):
+    p, mem, k = _buf(state)
+    _check(_lib.am_set_state(h, int(B), p, mem))
+
+
+def am_set_history(h, enable):
+    _check(_lib.am_set_history(h, int(bool(enable))))
+
+
+def am_get_history(h, out):
+    p, mem, k = _buf(out)
+    _check(_lib.am_get_history(h, p, mem))
+
+
+def am_set_option(h, option, value):
+    _check(_lib.am_set_option(h, int(option), int(value)))
+
+
+def am_set_stream(h, stream):
+    _check(_lib.am_set_stream(h, _stream_ptr(stream)))
+
+
+def am_last_solve_stats(h) -> int:
+    n = C.c_int()
+    _check(_lib.am_last_solve_stats(h, C.byref(n)))
+    return n.value
+
+
+def am_destroy(h):
+    _lib.am_destroy(h)
+
+
+def am_last_error() -> str:
+    return _lib.am_last_error().decode()
+
+
+# ------------------------------------------------------------ convenience
+
+class Problem:
+    """Owns one handle; methods forward to the C calls above."""
+
+    def __init__(self, pb: dict, precision=AM_FP32, alpha_mode=0, psi_dual_sign=0, cs_boundary=1,
+                 kernel=AM_KERNEL_FUSED, tile=0):
+        self.desc = make_desc(pb, precision, alpha_mode, psi_dual_sign, cs_boundary)
+        self.h = am_init_problem(self.desc)
+        self.q = int(pb["q"])
+        self.B = 0
+        self.iters = 0
+        am_set_option(self.h, AM_OPT_KERNEL, kernel)
+        am_set_option(self.h, AM_OPT_TILE, tile)
+        if int(pb["n"]) > 0:
+            self.set_obstacles(pb["xo"], pb["yo"], pb["ao"], pb["bo"])
+
+    def set_obstacles(self, xo, yo, a, b):
+        am_set_obstacles(self.h, len(a), xo, yo, a, b)
+
+    def solve(self, init, iters, warm_lambda=None, stream=None, history=False):
+        am_set_history(self.h, history)
+        B = self.B if init is None else int(init.shape[0])
+        am_solve_batch(self.h, B, init, warm_lambda, iters, stream)
+        self.B, self.iters = B, iters
+        return self
+
+    def results(self):
+        out = [np.zeros(self.B, dtype=np.float32) for _ in range(4)]
+        am_get_results(self.h, *out)
+        return dict(res=out[0], res_psi=out[1], cost=out[2], mind=out[3])
+
+    def state(self):
+        s = np.zeros((self.B, AM_STATE_FLOATS), dtype=np.float32)
+        am_get_state(self.h, s)
+        return s
+
+    def history(self):
+        hbuf = np.zeros((self.B, self.iters, 3), dtype=np.float32)
+        am_get_history(self.h, hbuf)
+        return hbuf
+
+    def best(self):
+        return am_get_best(self.h)
+
+    def close(self):
+        if self.h:
+            am_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def split_state(s: np.ndarray) -> dict:
+    """B x 110 state -> dict(xi1, xi2, lam, lampsi) (float64)."""
+    s = np.asarray(s, dtype=np.float64)
+    return dict(xi1=s[:, 0:44], xi2=s[:, 44:55], lam=s[:, 55:99], lampsi=s[:, 99:110])

@@ -1,0 +1,304 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (FP32 arithmetic against FP64):
+  coefficients after 10 iterations   max |dxi| <= 1e-4 * max(1, max |xi_oracle|) per trajectory
+  cost after 100 iterations          |dcost| <= 1e-3 |cost_oracle|
+  residual after 100 iterations      |dres| <= 1e-3 res_oracle + 5e-4
+  smallest ellipse distance          |dmind| <= 1e-3 max(1, mind_oracle)
+The absolute residual floor: a residual is a 2-norm over (3 + m n) q rows per
+side whose entries are differences of O(10 m) positions; FP32 rounding leaves
+~1e-6 m per row, ~1e-4 over 6600 rows, so 5e-4 is five times that.  Trajectories
+whose residual is ~1e-12 in FP64 (no constraint active) are compared against
+that floor only.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2109_13030_b300 import workload as W
+
+pytestmark = pytest.mark.gpu
+
+COEF_TOL = 1e-4
+COST_TOL = 1e-3
+RES_RTOL, RES_ATOL = 1e-3, 5e-4
+
+
+def tj():
+    from paper_2109_13030_b300 import trajam
+    return trajam
+
+
+def gpu_solve(pb, iters, kernel=0, tile=0, init=None, history=False, **flags):
+    T = tj()
+    P = T.Problem(pb, kernel=kernel, tile=tile, **flags)
+    init = pb["init"] if init is None else init
+    P.solve(init.astype(np.float32), iters, history=history)
+    out = T.split_state(P.state())
+    out.update({k: v.astype(np.float64) for k, v in P.results().items()})
+    if history:
+        out["hist"] = P.history().astype(np.float64)
+    out["best"] = P.best()
+    out["launches"] = T.am_last_solve_stats(P.h)
+    P.close()
+    return out
+
+
+def coef_err(a, b):
+    return np.max(np.abs(a - b), axis=-1) / np.maximum(np.max(np.abs(b), axis=-1), 1.0)
+
+
+def assert_coefs(g, o, idx=None, tol=COEF_TOL):
+    sel = slice(None) if idx is None else idx
+    for key in ("xi1", "xi2"):
+        e = coef_err(g[key][sel], o[key])
+        assert e.max() <= tol, (key, e.max(), int(np.argmax(e)))
+
+
+def assert_final(g, o, idx=None):
+    sel = slice(None) if idx is None else idx
+    dc = np.abs(g["cost"][sel] - o["cost"])
+    assert np.all(dc <= COST_TOL * np.abs(o["cost"])), (dc / np.abs(o["cost"])).max()
+    dr = np.abs(g["res"][sel] - o["res"])
+    assert np.all(dr <= RES_RTOL * o["res"] + RES_ATOL), (dr - RES_RTOL * o["res"]).max()
+    dm = np.abs(g["mind"][sel] - o["mind"])
+    assert np.all(dm <= 1e-3 * np.maximum(1.0, o["mind"])), dm.max()
+
+
+def sub_problem(pb, idx):
+    out = dict(pb)
+    out["init"] = pb["init"][idx]
+    out["B"] = len(idx)
+    return out
+
+
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_tiny_coefficients_after_10(kernel):
+    pb = W.make_problem("tiny", 0)
+    g = gpu_solve(pb, 10, kernel=kernel)
+    o = O.solve(pb, 10)
+    assert_coefs(g, o)
+
+
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_tiny_cost_residual_after_100(kernel):
+    pb = W.make_problem("tiny", 0)
+    g = gpu_solve(pb, 100, kernel=kernel)
+    o = O.solve(pb, 100)
+    assert_final(g, o)
+    assert_coefs(g, o, tol=1e-3)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_paper_shape_full_batch_sampled(seed):
+    """The bench configuration (1000 trajectories, automatic tile) on the GPU;
+    the oracle recomputes a sample of trajectories spread over all tiles,
+    including the first and last of the batch."""
+    pb = W.make_problem("paper", seed)
+    idx = np.unique(np.concatenate([[0, 1, 6, 7, 500, 998, 999],
+                                    np.random.default_rng(seed).choice(1000, 13, replace=False)]))
+    g10 = gpu_solve(pb, 10)
+    o10 = O.solve(sub_problem(pb, idx), 10)
+    assert_coefs(g10, o10, idx)
+    g100 = gpu_solve(pb, 100)
+    o100 = O.solve(sub_problem(pb, idx), 100)
+    assert_final(g100, o100, idx)
+
+
+def test_paper_shape_plain_sampled():
+    pb = W.make_problem("paper", 0)
+    idx = np.array([0, 3, 499, 999])
+    g = gpu_solve(pb, 10, kernel=1)
+    o = O.solve(sub_problem(pb, idx), 10)
+    assert_coefs(g, o, idx)
+
+
+@pytest.mark.parametrize("B,tile", [(1, 0), (37, 5), (37, 7), (150, 0)])
+def test_ragged_tiles(B, tile):
+    """Batch sizes that leave partial tiles and a partial last wave."""
+    pb = W.make_problem("paper", 3, B=B)
+    g = gpu_solve(pb, 10, tile=tile)
+    o = O.solve(pb, 10)
+    assert_coefs(g, o)
+
+
+@pytest.mark.parametrize("q,m,n", [(50, 1, 0), (50, 4, 3), (150, 2, 32), (100, 4, 12)])
+def test_shapes(q, m, n):
+    rng = np.random.default_rng(q * 100 + m * 10 + n)
+    base = W.make_uneven(seed=5, count=1, scale=0.02)[0]
+    pb = dict(base)
+    T = q / 10.0
+    t = np.linspace(0, T, q)
+    xo = np.zeros((n, q))
+    yo = np.zeros((n, q))
+    for j in range(n):
+        cx, cy = rng.uniform(1, 9, 2)
+        vx, vy = rng.uniform(-1, 1, 2)
+        xo[j], yo[j] = cx + vx * t, cy + vy * t
+    pb.update(q=q, T=T, m=m, r=np.linspace(-0.4, 0.4, m) if m > 1 else np.zeros(1), n=n,
+              xo=W._f32(xo), yo=W._f32(yo), ao=W._f32(rng.uniform(0.4, 0.8, n)),
+              bo=W._f32(rng.uniform(0.4, 0.8, n)))
+    pb["init"] = pb["init"][:6]
+    pb["B"] = 6
+    g = gpu_solve(pb, 10)
+    o = O.solve(pb, 10)
+    assert_coefs(g, o)
+
+
+def test_single_iteration():
+    pb = W.make_problem("paper", 4, B=16)
+    g = gpu_solve(pb, 1)
+    o = O.solve(pb, 1)
+    assert_coefs(g, o, tol=1e-5)
+    assert_final(g, o)
+
+
+@pytest.mark.parametrize("flags", [dict(psi_dual_sign=1), dict(cs_boundary=0)])
+def test_reading_flags(flags):
+    pb = W.make_problem("tiny", 2)
+    g = gpu_solve(pb, 10, **flags)
+    o = O.solve(pb, 10, **flags)
+    assert_coefs(g, o)
+
+
+def test_literal_alpha_reading():
+    """alpha_mode=1 (the printed atan2(yt, xt)) on ellipses, few iterations: it
+    diverges from the default reading and is compared only where both agree."""
+    pb = W.make_problem("paper", 0, B=12)
+    g = gpu_solve(pb, 3, alpha_mode=1)
+    o = O.solve(pb, 3, alpha_mode=1)
+    assert_coefs(g, o, tol=1e-4)
+
+
+def test_turning_heading():
+    pb = W.make_problem("tiny", 3)
+    pb["psi_bc"] = np.array([0.0, 0.2, 0.0, 2.5, -0.1, 0.0])
+    g = gpu_solve(pb, 10)
+    o = O.solve(pb, 10)
+    assert_coefs(g, o)
+
+
+def test_no_obstacles_closed_form():
+    """Check (iii) on the GPU: no obstacles, inactive bounds -> the minimum-smoothness
+    polynomial (same target the oracle is pinned to)."""
+    pb = W.with_obstacles_removed(W.make_problem("paper", 0, B=8))
+    g = gpu_solve(pb, 300)
+    o = O.solve(pb, 300)
+    P, _, _ = O.bernstein(10, pb["q"], pb["T"])
+    np.testing.assert_allclose(g["xi1"][:, 0:11] @ P.T, o["xi1"][:, 0:11] @ P.T, atol=1e-4)
+    np.testing.assert_allclose(g["xi1"][:, 22:33] @ P.T, o["xi1"][:, 22:33] @ P.T, atol=1e-4)
+
+
+def test_history_matches_oracle():
+    pb = W.make_problem("tiny", 0, B=8)
+    g = gpu_solve(pb, 30, history=True)
+    o = O.solve(pb, 30, hist=True)
+    h, ho = g["hist"], o["hist"]
+    np.testing.assert_allclose(h[:, :, 2], ho[:, :, 2], rtol=1e-3)
+    assert np.all(np.abs(h[:, :, 0] - ho[:, :, 0]) <= RES_RTOL * ho[:, :, 0] + RES_ATOL)
+    np.testing.assert_allclose(h[:, -1, 0], g["res"], rtol=1e-6)
+
+
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_warm_start_split(kernel):
+    """40 iterations, then 60 more from the resident state, equals 100 (check of
+    the checkpoint/resume path) within the FP32 tolerance."""
+    T = tj()
+    pb = W.make_problem("tiny", 1, B=16)
+    P = T.Problem(pb, kernel=kernel)
+    P.solve(pb["init"].astype(np.float32), 40)
+    P.solve(None, 60)
+    split = T.split_state(P.state())
+    P.close()
+    o = O.solve(pb, 100)
+    assert_coefs(split, o, tol=1e-3)
+
+
+def test_state_round_trip_device_and_host():
+    import torch
+    T = tj()
+    pb = W.make_problem("tiny", 2, B=8)
+    P = T.Problem(pb)
+    P.solve(pb["init"].astype(np.float32), 20)
+    st = torch.zeros((8, 110), dtype=torch.float32, device="cuda")
+    T.am_get_state(P.h, st)
+    host = P.state()
+    np.testing.assert_array_equal(st.cpu().numpy(), host)
+    Q = T.Problem(pb)
+    T.am_set_state(Q.h, 8, st)
+    Q.B = 8
+    Q.solve(None, 5)
+    P.solve(None, 5)
+    np.testing.assert_array_equal(Q.state(), P.state())
+    P.close()
+    Q.close()
+
+
+def test_device_inputs_equal_host_inputs():
+    import torch
+    T = tj()
+    pb = W.make_problem("paper", 1, B=20)
+    P = T.Problem(pb)
+    P.solve(pb["init"].astype(np.float32), 10)
+    a = P.state()
+    Q = T.Problem(dict(pb, n=0))
+    Q.set_obstacles(torch.tensor(pb["xo"], dtype=torch.float32, device="cuda"),
+                    torch.tensor(pb["yo"], dtype=torch.float32, device="cuda"),
+                    torch.tensor(pb["ao"], dtype=torch.float32, device="cuda"),
+                    torch.tensor(pb["bo"], dtype=torch.float32, device="cuda"))
+    init = torch.tensor(pb["init"], dtype=torch.float32, device="cuda")
+    Q.solve(init, 10, stream=torch.cuda.current_stream())
+    np.testing.assert_array_equal(Q.state(), a)
+    P.close()
+    Q.close()
+
+
+def test_best_selection_matches_oracle_key():
+    pb = W.make_problem("tiny", 0)
+    g = gpu_solve(pb, 100)
+    o = O.solve(pb, 100)
+    best = g["best"]
+    coll_o = o["mind"] < 0.99
+    key_o = np.where(coll_o, np.inf, o["cost"])
+    i_o = int(np.argmin(key_o)) if np.isfinite(key_o).any() else int(np.argmin(o["cost"]))
+    i_g = best["index"]
+    # the selected trajectory is feasible for the oracle too, and its cost is the minimum
+    assert abs(o["cost"][i_g] - o["cost"][i_o]) <= COST_TOL * o["cost"][i_o]
+    assert best["cost"] == pytest.approx(g["cost"][i_g])
+    np.testing.assert_allclose(best["coeffs"][0], g["xi1"][i_g, 0:11], rtol=0, atol=0)
+    np.testing.assert_allclose(best["coeffs"][2], g["xi2"][i_g], rtol=0, atol=0)
+
+
+def test_fused_and_plain_agree():
+    pb = W.make_problem("paper", 2, B=64)
+    a = gpu_solve(pb, 20, kernel=0)
+    b = gpu_solve(pb, 20, kernel=1)
+    # both paths carry their own FP32 error against the oracle: twice its tolerance
+    assert_coefs(a, b, tol=2 * COEF_TOL)
+    assert a["launches"] <= 3 and b["launches"] > 100
+
+
+def test_errors_are_reported():
+    T = tj()
+    pb = W.make_problem("tiny", 0, B=4)
+    P = T.Problem(pb)
+    with pytest.raises(T.TrajamError) as e:
+        T.am_get_best(P.h)
+    assert e.value.code == T.AM_ERR_STATE
+    with pytest.raises(T.TrajamError) as e:
+        T.am_solve_batch(P.h, 4, None, None, 5)
+    assert e.value.code == T.AM_ERR_STATE
+    with pytest.raises(T.TrajamError) as e:
+        T.am_solve_batch(P.h, 4, pb["init"].astype(np.float32), None, 0)
+    assert e.value.code == T.AM_ERR_ARG
+    with pytest.raises(T.TrajamError) as e:
+        T.am_set_obstacles(P.h, 65, np.zeros((65, 50)), np.zeros((65, 50)), np.ones(65), np.ones(65))
+    assert e.value.code == T.AM_ERR_ARG
+    big = dict(pb, q=256, T=25.6)
+    Q = T.Problem(big)
+    Q.set_obstacles(np.zeros((64, 256)), np.zeros((64, 256)), np.ones(64), np.ones(64))
+    with pytest.raises(T.TrajamError) as e:
+        Q.solve(np.zeros((2, 3, 11), dtype=np.float32), 1)
+    assert e.value.code == T.AM_ERR_ARG
+    P.close()
+    Q.close()
