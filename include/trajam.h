@@ -147,6 +147,32 @@ AM_API int am_set_stream(am_problem *h, void *stream);
 /* Number of kernels the last am_solve_batch launched. */
 AM_API int am_last_solve_stats(am_problem *h, int *launches);
 
+/* Allocation-free solve (no counterpart in the paper; an operational entry
+ * point).  Runs the plain loop (AM_KERNEL_PLAIN's kernels) on caller-owned
+ * device buffers and keeps every intermediate in a fixed 32 MiB area that is
+ * part of the library's device image, so the call itself never allocates:
+ * for callers that cannot call cudaMalloc at solve time -- a real-time
+ * re-planning step whose budget cudaMalloc's unbounded, device-synchronising
+ * latency would break, or code running under an allocator or a stream
+ * capture that forbids raw allocations.
+ *  h        a handle set up beforehand (am_init_problem, am_set_obstacles);
+ *           only its device constants are read, its buffers are untouched.
+ *  state    device, B x AM_STATE_FLOATS, in/out (the cold-start state has
+ *           xi1 = (c_x, cos c_psi, c_y, sin c_psi), lambda = 0).
+ *  res, res_psi, cost, mind   device, B floats each (as am_get_results).
+ * Returns AM_ERR_BUDGET, with the sizes in am_last_error(), when the batch
+ * needs more than the fixed area holds (about 650 trajectories at q = 100,
+ * m = 3, n = 10).  The first call on a device looks up the area's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  All calls in the process share the one
+ * area: calls that overlap on the GPU (other streams, other host threads)
+ * race and must be serialised by the caller.  Nothing in the area needs to
+ * start at zero: every word a call reads it has written earlier in the same
+ * call. */
+AM_API int am_solve_batch_noalloc(const am_problem *h, int B, float *state, float *res,
+                                  float *res_psi, float *cost, float *mind, int iters,
+                                  void *stream);
+
 AM_API void am_destroy(am_problem *h);
 AM_API const char *am_last_error(void);
 

@@ -455,3 +455,19 @@ int am_last_solve_stats(am_problem *h, int *launches)
 }
 
 }  // extern "C"
+
+namespace trajam {
+
+// Read-only view of a handle's device constants, for entry points defined in
+// other translation units.  Records the message and returns the code on error.
+int handle_constants(const am_problem *h, const float **cblob, ConstLayout *L)
+{
+    if (!h) return fail(AM_ERR_ARG, "null handle");
+    *cblob = h->d_blob;
+    *L = h->L;
+    return AM_OK;
+}
+
+int report_error(int code, const char *msg) { return fail(code, "%s", msg); }
+
+}  // namespace trajam

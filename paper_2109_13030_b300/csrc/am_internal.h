@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <vector>
 
+struct am_problem;
+
 namespace trajam {
 
 constexpr int NV = 11;        // coefficients per polynomial (degree 10)
@@ -117,6 +119,9 @@ int launch_prep_obstacles(float *cblob, const ConstLayout &L, const float *xo, c
 // the slack control points start at cos / sin of the heading control points.
 int launch_init_state(float *state, const float *init, const float *warm, int B, void *stream,
                       int *launches);
+// Handle accessors for entry points outside the C-ABI file.
+int handle_constants(const ::am_problem *h, const float **cblob, ConstLayout *L);
+int report_error(int code, const char *msg);
 // Fused kernel tile selection, exposed for the autotuner.
 int fused_auto_tile(const ConstLayout &L, int B, int num_sms);
 size_t fused_smem_bytes(const ConstLayout &L, int tile);

@@ -6,7 +6,11 @@
 // kernel is measured against.
 #include <cuda_runtime.h>
 
+#include <cstdio>
+#include <mutex>
+
 #include "am_internal.h"
+#include "../../include/trajam.h"
 
 namespace trajam {
 namespace {
@@ -432,3 +436,89 @@ int launch_plain(const SolveArgs &a, float *scratch, size_t scratch_floats, void
 }
 
 }  // namespace trajam
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the plain loop.
+//
+// Some callers must not allocate device memory at solve time: a real-time
+// re-planning step has a fixed time budget, and cudaMalloc/cudaFree can block
+// for an unbounded time and synchronise the whole device; code running while a
+// stream is being captured, or under an external memory manager that owns all
+// device allocations, may not call them at all.  For them the plain loop can
+// keep its intermediates in a fixed area that is part of this library's device
+// image: every GPU that loads the library holds it until the process exits.
+//
+// kNoallocScratchFloats bounds the batch: the loop needs plain_scratch_floats()
+// floats, about (17 + 3 m n) q + 300 per trajectory (12.8 k floats at q = 100,
+// m = 3, n = 10, i.e. up to 650 trajectories in 32 MiB).
+namespace {
+
+constexpr size_t kNoallocScratchFloats = size_t(8) << 20;  // 32 MiB of FP32
+static __device__ __align__(256) float g_noalloc_scratch[kNoallocScratchFloats];
+
+constexpr int kMaxDevices = 128;
+std::mutex g_noalloc_mu;
+float *g_noalloc_addr[kMaxDevices] = {};
+
+// Device address of the fixed area on the current device.  Host code cannot
+// use the symbol itself (it names a host-side stand-in), so the address is
+// looked up once per device, with that device current, and cached.
+int noalloc_scratch(float **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return trajam::report_error(AM_ERR_CUDA, cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return trajam::report_error(AM_ERR_ARG, "device index out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return trajam::report_error(AM_ERR_CUDA, "cudaGetSymbolAddress of the fixed scratch area failed");
+        g_noalloc_addr[dev] = static_cast<float *>(p);
+    }
+    *out = g_noalloc_addr[dev];
+    return AM_OK;
+}
+
+}  // namespace
+
+extern "C" AM_API int am_solve_batch_noalloc(const am_problem *h, int B, float *state, float *res,
+                                             float *res_psi, float *cost, float *mind, int iters,
+                                             void *stream)
+{
+    using namespace trajam;
+    const float *cblob = nullptr;
+    ConstLayout L;
+    int rc = handle_constants(h, &cblob, &L);
+    if (rc) return rc;
+    if (!state || !res || !res_psi || !cost || !mind) return report_error(AM_ERR_ARG, "null device buffer");
+    if (B < 1 || iters < 1 || iters > 100000) return report_error(AM_ERR_ARG, "B >= 1 and 1 <= iters <= 100000 required");
+    const size_t need = plain_scratch_floats(L, B);
+    if (need > kNoallocScratchFloats) {
+        char msg[200];
+        snprintf(msg, sizeof(msg),
+                 "batch of %d needs %zu floats of scratch; the fixed area holds %zu (32 MiB)", B, need,
+                 kNoallocScratchFloats);
+        return report_error(AM_ERR_BUDGET, msg);
+    }
+    float *scratch = nullptr;
+    rc = noalloc_scratch(&scratch);
+    if (rc) return rc;
+    SolveArgs a;
+    a.cblob = cblob;
+    a.L = L;
+    a.B = B;
+    a.iters = iters;
+    a.state = state;
+    a.res = res;
+    a.res_psi = res_psi;
+    a.cost = cost;
+    a.mind = mind;
+    a.hist = nullptr;
+    a.tile = 0;
+    a.err = nullptr;
+    rc = launch_plain(a, scratch, kNoallocScratchFloats, stream, nullptr);
+    if (rc) return report_error(AM_ERR_CUDA, "plain loop launch failed");
+    return AM_OK;
+}

@@ -25,7 +25,7 @@ AM_NV, AM_STATE_FLOATS = 11, 110
 EXPORTS = ["am_init_problem", "am_set_obstacles", "am_set_boundary", "am_solve_batch",
            "am_get_results", "am_get_best", "am_get_state", "am_set_state", "am_set_history",
            "am_get_history", "am_set_option", "am_set_stream", "am_last_solve_stats",
-           "am_destroy", "am_last_error"]
+           "am_solve_batch_noalloc", "am_destroy", "am_last_error"]
 
 
 class AmProblemDesc(C.Structure):
@@ -62,6 +62,7 @@ def _load():
         "am_set_option": ([vp, ip, ip], ip),
         "am_set_stream": ([vp, vp], ip),
         "am_last_solve_stats": ([vp, C.POINTER(C.c_int)], ip),
+        "am_solve_batch_noalloc": ([vp, ip, fp, fp, fp, fp, fp, ip, vp], ip),
         "am_destroy": ([vp], None),
         "am_last_error": ([], C.c_char_p),
     }
@@ -197,6 +198,15 @@ def am_last_solve_stats(h) -> int:
     n = C.c_int()
     _check(_lib.am_last_solve_stats(h, C.byref(n)))
     return n.value
+
+
+def am_solve_batch_noalloc(h, B, state, res, res_psi, cost, mind, iters, stream=None):
+    """Allocation-free plain-loop solve on caller-owned device tensors."""
+    bufs = [_buf(x) for x in (state, res, res_psi, cost, mind)]
+    if any(m != AM_DEVICE for (_, m, _) in bufs):
+        raise ValueError("am_solve_batch_noalloc takes device buffers only")
+    _check(_lib.am_solve_batch_noalloc(h, int(B), *[p for (p, _, _) in bufs], int(iters),
+                                       _stream_ptr(stream)))
 
 
 def am_destroy(h):
