@@ -51,6 +51,25 @@ def algorithmic_flops(q: int, m: int, n: int) -> float:
     return 17.0 * m * n * q + 16.0 * m * q + (16 + 176 + 66 + 176) * q + 2 * 121 * 2 + 3960.0
 
 
+def measured_traffic():
+    """DRAM bytes per launch of the fused kernel from the committed ncu summary,
+    if that summary was taken on the current kernel source (else None)."""
+    import hashlib
+    import re
+    prof = os.path.join(ROOT, "profiles", "am_fused_kernel_paper_b1000.md")
+    src = os.path.join(ROOT, "paper_2109_13030_b300", "csrc", "am_fused.cu")
+    try:
+        text = open(prof).read()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    m = re.search(r"am_fused.cu: `([0-9a-f]{16})`", text)
+    t = re.search(r"dram__bytes_read.sum / write.sum \| ([\d,]+) B / ([\d,]+) B", text)
+    if not m or not t or m.group(1) != sha:
+        return None
+    return int(t.group(1).replace(",", "")) + int(t.group(2).replace(",", ""))
+
+
 def peak_fp32_tflops(sms: int = 148, clock_mhz: float = 2032.0) -> float:
     """FP32 FMA peak: SMs x 128 lanes x 2 flops x clock."""
     return sms * 128 * 2 * clock_mhz * 1e6 / 1e12
@@ -305,7 +324,7 @@ def main():
                        "kernel": "fused persistent (1 launch per solve)"},
             "gpu_launches": launches_per_solve * args.steps,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": measured_traffic(),
                          "kernel": "am_fused_kernel",
                          "flops_per_launch": flops,
                          "peak_basis": "derived FP32 FMA peak: SMs x 128 lanes x 2 x 2032 MHz",

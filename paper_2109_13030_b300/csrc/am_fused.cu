@@ -1,12 +1,12 @@
 // Fused persistent kernel of the batched alternating-minimization loop
 // (Sec. III-D, steps 1-5, and the batch solution of Sec. III-E).
 //
-// One CTA stays resident on each SM and works through tiles of T trajectories.
-// It stages the constant block into shared memory once (bulk async copy,
-// completion on an mbarrier), keeps xi1, xi2, lambda, lambda_psi and the
-// residual contraction R = F^T (g - F xi1) of every trajectory of the tile in
-// shared memory for all iterations, and writes the state back only after the
-// last one.  Nothing per element (alpha, d, g) is ever stored.
+// One CTA stays resident on each SM and works through tiles of T <= 8
+// trajectories.  It stages the constant block into shared memory once (bulk
+// async copy, completion on an mbarrier), keeps xi1, xi2, lambda, lambda_psi
+// and the residual contraction R = F^T (g - F xi1) of every trajectory of the
+// tile in shared memory for all iterations, and writes the state back only
+// after the last one.  Nothing per element (alpha, d, g) is ever stored.
 //
 // The position step of Eq. over_3, xi1' = Minv (lam + rho F^T g) + kb, is
 // evaluated in the algebraically equal increment form
@@ -14,23 +14,31 @@
 // (from Minv Qbar + N A = I, kb = N b and A xi1 = b), so FP32 works on the
 // small constraint residual instead of on |F^T g| ~ 1e3, which the explicit
 // inverse would amplify by its conditioning.  The multiplier update of
-// Eq. update_lambda_1 is lam' = lam + rho R with the same R.  A solve starts
-// from a reference xi1 whose boundary control points are set from the
-// boundary conditions, so A xi1 = b holds from the first step on.
+// Eq. update_lambda_1 is lam' = lam + rho R with the same R.  The heading
+// step of Eq. compute_convex_surrogate is treated the same way.  A solve
+// starts from a reference whose boundary control points are set from the
+// boundary conditions, so A xi = b holds from the first step on.
 //
-// Thread roles inside a tile (all threads run every phase; idle ones skip):
-//   per-step phases   thread <-> (trajectory tt, step t), tt*q + t < T*q
-//   dot phases        thread <-> (trajectory, output, part) tasks
+// The two contractions over the time steps -- R (Pd^T rv + Pdd^T ra + P^T r0
+// and P^T r1 per side) and the heading right-hand side (W^T delta, P^T delta)
+// -- are dense products of a [rows x steps] operand written by the sweep with
+// constant basis columns.  They run on the tensor cores as mma.sync
+// m16n8k8 TF32 with each FP32 operand split into a TF32 high part and a TF32
+// remainder (three products: hi*hi + hi*lo + lo*hi), which keeps FP32-level
+// accuracy.
+//
 // Phases of one iteration, separated by __syncthreads():
 //   XI1   lam += rho R; xi1 += Minv (lam - Q xi1 + rho R); lambda_psi update
 //         (Eq. update_lambda_psi); per-trajectory sums of the last sweep
-//   EVAL  x, xdot, xddot, y, ..., c, s at step t (Eq. param); psi_t target
-//   PSI   xi2 = Mpsi lam_psi + kbpsi + rho W^T psi_t (Eq. compute_convex_surrogate)
-//   SWEEP psi = P xi2; the closed-form alpha/d steps for every circle and
-//         obstacle (Eq. zeta_2 - compute_da) in the trig-free form
-//         (xt, yt) * max(1, 1/sqrt(xt^2/a^2 + yt^2/b^2)), the velocity and
-//         acceleration projections, and the per-step residual vectors of R
-//   DOT   R per side: Pd^T rv + Pdd^T ra + P^T r0 and P^T r1
+//   EVAL  x, xdot, xddot, y, ..., c, s at step t (Eq. param); heading target
+//         psi_t and delta = psi_t - P xi2; Mpsi lam_psi - Mpsi H xi2
+//   PSI   W^T delta and P^T delta on the tensor cores
+//   SWEEP xi2 += Mpsi (lam_psi - H xi2) + rho W^T delta; psi = P xi2; the
+//         closed-form alpha/d steps for every circle and obstacle (Eq. zeta_2 -
+//         compute_da) in the trig-free form (xt, yt) max(1, 1/sqrt(xt^2/a^2 +
+//         yt^2/b^2)), the velocity and acceleration projections, and the
+//         per-step residual vectors of R
+//   DOT   R on the tensor cores
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -41,14 +49,24 @@ namespace trajam {
 namespace {
 
 constexpr int kMaxThreads = 768;
-constexpr int kVecs = 12;       // per-step vectors in G
+constexpr int kMaxTile = 8;     // rows (side, trajectory) of one 16-row MMA tile
 constexpr float kTwoPi = 6.28318530717958647692f;
 constexpr float kPi = 3.14159265358979323846f;
 
 struct Smem {
-    int cst, xi1, lam, rb, xi2, dx2, lps, ptp, G, psit, bar, total;  // float offsets
+    int cst, xi1, lam, rb, xi2, dx2, lps, ptp, wdt, bas, G2, RS, GX, PS, bar, total;
 };
 
+// Shared-memory layout (float offsets).
+//   xi1, lam  [2][T][48]   double-buffered, padded blocks of 12 per polynomial
+//   rb        [T][48]      R per side: c_pos rows 0..10, c_slack rows 12..22
+//   xi2       [2][T][12]   double-buffered c_psi;  dx2 [T][12] last increment
+//   lps       [T][12]      lambda_psi
+//   ptp, wdt, bas [8][12]  P^T delta, W^T delta, Mpsi lam_psi - Mpsi H xi2
+//   G2        [16][RS]     residual vectors, row = side*8 + trajectory,
+//                          segments rv | ra | r0 | r1 of qs steps each
+//   GX        [T][4][qs]   per-step squared residual, heading residual, cost, distance
+//   PS        [8][qs]      delta = psi_t - P xi2 per trajectory
 __host__ __device__ inline Smem smem_layout(const ConstLayout &L, int T)
 {
     Smem s;
@@ -57,12 +75,16 @@ __host__ __device__ inline Smem smem_layout(const ConstLayout &L, int T)
     s.xi1 = o; o += 2 * T * 48;
     s.lam = o; o += 2 * T * 48;
     s.rb = o; o += T * 48;
-    s.xi2 = o; o += 2 * T * 12;   // double-buffered c_psi
-    s.dx2 = o; o += T * 12;       // last heading increment
+    s.xi2 = o; o += 2 * T * 12;
+    s.dx2 = o; o += T * 12;
     s.lps = o; o += T * 12;
-    s.ptp = o; o += T * 12;
-    s.G = o; o += T * kVecs * L.qs;
-    s.psit = o; o += T * L.qs;
+    s.ptp = o; o += kMaxTile * 12;
+    s.wdt = o; o += kMaxTile * 12;
+    s.bas = o; o += kMaxTile * 12;
+    s.RS = 4 * L.qs + 4;  // 4 mod 8 (qs is): eight rows at one offset hit distinct banks
+    s.G2 = o; o += 16 * s.RS;
+    s.GX = o; o += T * 4 * L.qs;
+    s.PS = o; o += kMaxTile * L.qs;
     o = (o + 3) & ~3;
     s.bar = o; o += 4;  // one 8-byte mbarrier, kept 16-byte aligned
     s.total = o;
@@ -94,6 +116,55 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
         : "memory");
     return ok != 0;
 }
+
+// ------------------------------------------------------------ tensor cores
+
+// Round a finite FP32 value to the nearest TF32 (ties away from zero): add half
+// a TF32 unit to the magnitude bits and clear the 13 low mantissa bits.  A carry
+// into the exponent gives the correctly rounded next binade.
+__device__ __forceinline__ uint32_t round_tf32(uint32_t bits)
+{
+    return (bits + 0x1000u) & 0xFFFFE000u;
+}
+
+// x = hi + lo with hi, lo both TF32: |x - hi| <= 2^-11 |x| and lo = round(x - hi),
+// so hi + lo is within ~2^-22 |x| of x.  Full-rate integer and FP32 operations
+// only (no conversion instruction).
+__device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo)
+{
+    hi = round_tf32(__float_as_uint(x));
+    lo = round_tf32(__float_as_uint(x - __uint_as_float(hi)));
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2,
+                                         uint32_t a3, uint32_t b0, uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// One 16x8x8 step of D += A B in three TF32 products, into three independent
+// accumulators (lo*hi, hi*lo, hi*hi) so consecutive steps do not wait on one
+// accumulator; the caller sums them at the end.
+// a: A[g][k], A[g+8][k], A[g][k+4], A[g+8][k+4]; b: B[k][n], B[k+4][n] with
+// g = lane/4, k = lane%4 within the step, n = lane/4 (PTX m16n8k8 layouts).
+__device__ __forceinline__ void mma3x(float (&d0)[4], float (&d1)[4], float (&d2)[4],
+                                      const float (&a)[4], float b0, float b1)
+{
+    uint32_t ah[4], al[4], bh0, bl0, bh1, bl1;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) split_tf32(a[i], ah[i], al[i]);
+    split_tf32(b0, bh0, bl0);
+    split_tf32(b1, bh1, bl1);
+    mma_tf32(d0, al[0], al[1], al[2], al[3], bh0, bh1);
+    mma_tf32(d1, ah[0], ah[1], ah[2], ah[3], bl0, bl1);
+    mma_tf32(d2, ah[0], ah[1], ah[2], ah[3], bh0, bh1);
+}
+
+// ------------------------------------------------------------------ small
 
 // Side-row r (0..21) of (c_pos, c_slack) -> padded index within a 24-float side block.
 __device__ __forceinline__ int rowpad(int r) { return r < NV ? r : r + 1; }
@@ -146,6 +217,53 @@ __device__ __forceinline__ Tile tile_of(int i, int B, int ntiles)
 //   first: lam' = lam,          xi1' = xi1 + Minv (lam + rho R) - MQ xi1
 //   later: lam' = lam + rho R,  xi1' = xi1 + Minv (lam + 2 rho R) - MQ xi1
 //   post (no solve): lam' = lam + rho R, xi1' = xi1
+// Position step on the tensor cores, one 16-row tile (row = side*8 + trajectory):
+//   D[row][np] = sum_k A[row][k] Bt[np][k],  A = [lam + coef R | xi1],  Bt = [Minv | -Minv Q]
+// on padded indices (k, np in 0..23 per side, 11 and 23 are zero pads), then
+// xi1' = xi1 + D and lam' = lam (first) or lam + rho R.  Three warp tasks, one
+// per n-tile of 8 output columns.
+__device__ void xi1_mma(const KParams &p, float *sm, const Smem &S, const Tile &tl, int cur,
+                        bool first)
+{
+    const ConstLayout &L = p.L;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, tq = lane & 3;
+    const float rho = L.rho, coef = first ? rho : 2.f * rho;
+    const bool valid = g < tl.count;
+    const int tt = valid ? g : 0;
+    const float *lam = sm + S.lam + (cur * p.T + tt) * 48;
+    const float *xi = sm + S.xi1 + (cur * p.T + tt) * 48;
+    const float *R = sm + S.rb + tt * 48;
+    for (int nt = warp; nt < 3; nt += blockDim.x >> 5) {
+        const float *brow = sm + S.cst + L.off_xib + (nt * 8 + g) * 52;
+        float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f}, d2[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int ks = 0; ks < 6; ++ks) {
+            const int k0 = ks * 8 + tq, k1 = k0 + 4;
+            float a[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int k = (e < 2) ? k0 : k1, side = e & 1;
+                const int o = side * 24 + (k < 24 ? k : k - 24);
+                a[e] = !valid ? 0.f : k < 24 ? fmaf(coef, R[o], lam[o]) : xi[o];
+            }
+            mma3x(d0, d1, d2, a, brow[k0], brow[k1]);
+        }
+        if (valid) {
+            float *lam_n = sm + S.lam + ((cur ^ 1) * p.T + tt) * 48;
+            float *xi_n = sm + S.xi1 + ((cur ^ 1) * p.T + tt) * 48;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int c = nt * 8 + 2 * tq + (e & 1);
+                if (c == NV || c == 23) continue;  // pads stay zero
+                const int o = (e >> 1) * 24 + c;
+                xi_n[o] = xi[o] + (d0[e] + d1[e] + d2[e]);
+                lam_n[o] = first ? lam[o] : fmaf(rho, R[o], lam[o]);
+            }
+        }
+    }
+}
+
 __device__ void phase_xi1(const KParams &p, float *sm, const Smem &S, const Tile &tl, int cur,
                           bool first, bool solve, bool sums, bool final_out, int kprev)
 {
@@ -153,9 +271,17 @@ __device__ void phase_xi1(const KParams &p, float *sm, const Smem &S, const Tile
     const float *cst = sm + S.cst;
     const float rho = L.rho;
     const int Tn = tl.count;
-    const int n_xi = Tn * 44, n_lp = Tn * NV, n_sc = sums ? Tn * 4 : 0;
+    // With the position step on the tensor cores (warps 0..2), the remaining
+    // tasks go to the threads after them when the block has enough.
+    const int n_xi = solve ? 0 : Tn * 44, n_lp = Tn * NV, n_sc = sums ? Tn * 4 : 0;
     const int ntask = n_xi + n_lp + n_sc;
-    for (int task = threadIdx.x; task < ntask; task += blockDim.x) {
+    int base = 0;
+    if (solve) {
+        xi1_mma(p, sm, S, tl, cur, first);
+        if (int(blockDim.x) >= 96 + ntask) base = 96;
+    }
+    const int stride = int(blockDim.x) - base;
+    for (int task = int(threadIdx.x) - base; task >= 0 && task < ntask; task += stride) {
         if (task < n_xi) {
             const int tt = task / 44, rem = task - 44 * tt, side = rem / NS, row = rem - NS * side;
             const float *lam = sm + S.lam + (cur * p.T + tt) * 48 + 24 * side;
@@ -190,7 +316,7 @@ __device__ void phase_xi1(const KParams &p, float *sm, const Smem &S, const Tile
             lp[k] -= L.psi_sign * L.rho_psi * (a - sm[S.ptp + tt * 12 + k]);
         } else {
             const int s = task - n_xi - n_lp, tt = s >> 2, w = s & 3;
-            const float *gv = sm + S.G + (tt * kVecs + 8 + w) * L.qs;
+            const float *gv = sm + S.GX + (tt * 4 + w) * L.qs;
             float v;
             if (w < 3) {
                 const float4 *g = reinterpret_cast<const float4 *>(gv);
@@ -218,101 +344,106 @@ __device__ void phase_xi1(const KParams &p, float *sm, const Smem &S, const Tile
     }
 }
 
-// DOT phase: R = F^T (g - F xi1) per trajectory and side from the per-step
-// residual vectors.  Task = (trajectory, side, k, part); parts 0..2 contract
-// rv, ra, r0 with Pd, Pdd, P and are summed into the c_pos row k; part 3
-// contracts r1 with P into the c_slack row k.
-__device__ void phase_dot(const KParams &p, float *sm, const Smem &S, const Tile &tl)
+// Zero the accumulators the tensor-core phases add into, and form
+// Mpsi lam_psi - Mpsi H xi2 for the heading step.  Runs in the EVAL phase
+// (after XI1 has read R and P^T delta, before PSI and DOT write them).
+__device__ void prepare_accumulators(const KParams &p, float *sm, const Smem &S, const Tile &tl,
+                                     int cur2)
 {
     const ConstLayout &L = p.L;
-    const int ntask = tl.count * 88;
-    const int q4 = L.qs / 4;
-    for (int base = 0; base < ntask; base += blockDim.x) {
-        const int task = base + threadIdx.x;
-        float tot = 0.f;
-        int tt = 0, side = 0, k = 0, part = 0;
-        if (task < ntask) {
-            part = task & 3;
-            const int g = task >> 2;
-            tt = g / NS;
-            const int rem = g - NS * tt;
-            side = rem / NV;
-            k = rem - NV * side;
-            const int bsel = part == 0 ? 1 : part == 1 ? 2 : 0;
-            const float4 *col = reinterpret_cast<const float4 *>(sm + S.cst + L.off_pcol + (bsel * NV + k) * L.qs);
-            const float4 *vec = reinterpret_cast<const float4 *>(sm + S.G + (tt * kVecs + 4 * side + part) * L.qs);
-            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-#pragma unroll 5
-            for (int i = 0; i < q4; ++i) {
-                const float4 a = vec[i], b = col[i];
-                a0 = fmaf(a.x, b.x, a0);
-                a1 = fmaf(a.y, b.y, a1);
-                a2 = fmaf(a.z, b.z, a2);
-                a3 = fmaf(a.w, b.w, a3);
-            }
-            tot = (a0 + a1) + (a2 + a3);
+    const float *cst = sm + S.cst;
+    const int Tn = tl.count;
+    for (int i = threadIdx.x; i < Tn * 48; i += blockDim.x) sm[S.rb + i] = 0.f;
+    for (int i = threadIdx.x; i < Tn * 24; i += blockDim.x) {
+        const int tt = i / 24, j = i - 24 * tt;
+        if (j < 12) {
+            sm[S.ptp + tt * 12 + j] = 0.f;
+            sm[S.wdt + tt * 12 + j] = 0.f;
         }
-        const float s1 = __shfl_down_sync(0xffffffffu, tot, 1);
-        const float s2 = __shfl_down_sync(0xffffffffu, tot, 2);
-        if (task < ntask) {
-            float *R = sm + S.rb + tt * 48 + 24 * side;
-            if (part == 0) R[k] = tot + s1 + s2;
-            else if (part == 3) R[12 + k] = tot;
+        if (j < NV) {
+            const float *lp = sm + S.lps + tt * 12;
+            const float *x2 = sm + S.xi2 + (cur2 * p.T + tt) * 12;
+            float b0 = 0.f, b1 = 0.f;
+#pragma unroll
+            for (int c = 0; c < NV; ++c) {
+                b0 = fmaf(cst[L.off_mpsi + c * 12 + j], lp[c], b0);
+                b1 = fmaf(cst[L.off_mpsih + c * 12 + j], x2[c], b1);
+            }
+            sm[S.bas + tt * 12 + j] = b0 - b1;
         }
     }
 }
 
-// PSI phase: the heading step of Eq. compute_convex_surrogate in increment form,
-//   xi2' = xi2 + Mpsi (lam_psi - H xi2) + rho W^T delta,  W = P Mpsi^T,
-// with delta = psi_t - P xi2 per step (equal to Mpsi (lam_psi + rho P^T psi_t)
-// + kbpsi when A xi2 = b_psi), plus P^T delta for the multiplier update.
-// Task = (trajectory, output kk in 0..21, chunk 0..3); the four chunks of one
-// output sit in adjacent lanes and are summed with shuffles.
-__device__ void phase_psi(const KParams &p, float *sm, const Smem &S, const Tile &tl, int cur2)
+// DOT phase on the tensor cores.  One 16-row tile: row = side*8 + trajectory.
+// Eight warp tasks: (segment rv | ra | r0 | r1, n-tile 0/1).  The c_pos rows
+// sum the rv, ra and r0 segment products (shared atomics), the c_slack rows
+// take r1.
+__device__ void phase_dot(const KParams &p, float *sm, const Smem &S, const Tile &tl)
 {
     const ConstLayout &L = p.L;
-    const float *cst = sm + S.cst;
-    const int ntask = tl.count * 88;
-    const int q4 = L.qs / 4;
-    for (int base = 0; base < ntask; base += blockDim.x) {
-        const int task = base + threadIdx.x;
-        float tot = 0.f;
-        int tt = 0, kk = 0, chunk = 0;
-        if (task < ntask) {
-            chunk = task & 3;
-            const int g = task >> 2;
-            tt = g / NS;
-            kk = g - NS * tt;
-            const float4 *col = reinterpret_cast<const float4 *>(
-                cst + (kk < NV ? L.off_wcol + kk * L.qs : L.off_pcol + (kk - NV) * L.qs));
-            const float4 *ps = reinterpret_cast<const float4 *>(sm + S.psit + tt * L.qs);
-            float a0 = 0.f, a1 = 0.f;
-            for (int i = chunk; i < q4; i += 4) {
-                const float4 a = ps[i], b = col[i];
-                a0 = fmaf(a.x, b.x, a0);
-                a1 = fmaf(a.y, b.y, a1);
-                a0 = fmaf(a.z, b.z, a0);
-                a1 = fmaf(a.w, b.w, a1);
-            }
-            tot = a0 + a1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, tq = lane & 3;
+    const int nks = (L.q + 7) >> 3;
+    for (int task = warp; task < 8; task += blockDim.x >> 5) {
+        const int seg = task >> 1, nt = task & 1;
+        const int bsel = seg == 0 ? 1 : seg == 1 ? 2 : 0;  // Pd, Pdd, P, P
+        const int k = nt * 8 + g;
+        const bool kv = k < NV;
+        const float *bcol = sm + S.cst + L.off_pcol + (bsel * NV + (kv ? k : 0)) * L.qs;
+        const float *a_lo = sm + S.G2 + g * S.RS + seg * L.qs;
+        const float *a_hi = a_lo + 8 * S.RS;
+        float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f}, d2[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 2
+        for (int ks = 0; ks < nks; ++ks) {
+            const int c0 = ks * 8 + tq;
+            const float a[4] = {a_lo[c0], a_hi[c0], a_lo[c0 + 4], a_hi[c0 + 4]};
+            const float b0 = kv ? bcol[c0] : 0.f, b1 = kv ? bcol[c0 + 4] : 0.f;
+            mma3x(d0, d1, d2, a, b0, b1);
         }
-        tot += __shfl_xor_sync(0xffffffffu, tot, 1);
-        tot += __shfl_xor_sync(0xffffffffu, tot, 2);
-        if (task < ntask && chunk == 0) {
-            if (kk < NV) {
-                const float *lp = sm + S.lps + tt * 12;
-                const float *x2 = sm + S.xi2 + (cur2 * p.T + tt) * 12;
-                float b0 = 0.f, b1 = 0.f;
+        if (g < tl.count) {
 #pragma unroll
-                for (int c = 0; c < NV; ++c) {
-                    b0 = fmaf(cst[L.off_mpsi + c * 12 + kk], lp[c], b0);
-                    b1 = fmaf(cst[L.off_mpsih + c * 12 + kk], x2[c], b1);
-                }
-                const float d = fmaf(L.rho, tot, b0 - b1);
-                sm[S.dx2 + tt * 12 + kk] = d;
-                sm[S.xi2 + ((cur2 ^ 1) * p.T + tt) * 12 + kk] = x2[kk] + d;
-            } else {
-                sm[S.ptp + tt * 12 + (kk - NV)] = tot;
+            for (int e = 0; e < 4; ++e) {
+                const int side = e >> 1, col = nt * 8 + 2 * tq + (e & 1);
+                if (col >= NV) continue;
+                float *R = sm + S.rb + g * 48 + 24 * side;
+                if (seg < 3) atomicAdd(R + col, d0[e] + d1[e] + d2[e]);
+                else R[12 + col] = d0[e] + d1[e] + d2[e];
+            }
+        }
+    }
+}
+
+// PSI phase on the tensor cores: W^T delta (cols 0..10) and P^T delta (cols
+// 11..21) per trajectory; rows 0..7 = trajectories, rows 8..15 are zero.
+// Six warp tasks: three n-tiles x two halves of the steps, summed with shared
+// atomics.
+__device__ void phase_psi(const KParams &p, float *sm, const Smem &S, const Tile &tl)
+{
+    const ConstLayout &L = p.L;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, tq = lane & 3;
+    const int nks = (L.q + 7) >> 3, quarter = (nks + 1) >> 1;
+    for (int task = warp; task < 6; task += blockDim.x >> 5) {
+        const int nt = task % 3, part = task / 3;
+        const int col = nt * 8 + g;
+        const float *bcol = col < NV ? sm + S.cst + L.off_wcol + col * L.qs
+                          : col < NS ? sm + S.cst + L.off_pcol + (col - NV) * L.qs : nullptr;
+        const float *arow = sm + S.PS + g * L.qs;
+        float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f}, d2[4] = {0.f, 0.f, 0.f, 0.f};
+        const int k0 = part * quarter, k1 = min(nks, k0 + quarter);
+        for (int ks = k0; ks < k1; ++ks) {
+            const int c0 = ks * 8 + tq;
+            const float a[4] = {arow[c0], 0.f, arow[c0 + 4], 0.f};
+            const float b0 = bcol ? bcol[c0] : 0.f, b1 = bcol ? bcol[c0 + 4] : 0.f;
+            mma3x(d0, d1, d2, a, b0, b1);
+        }
+        if (g < tl.count && k1 > k0) {
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int c = nt * 8 + 2 * tq + e;
+                const float v = d0[e] + d1[e] + d2[e];
+                if (c < NV) atomicAdd(sm + S.wdt + g * 12 + c, v);
+                else if (c < NS) atomicAdd(sm + S.ptp + g * 12 + (c - NV), v);
             }
         }
     }
@@ -351,17 +482,15 @@ __device__ __forceinline__ void eval_xy(const float *sm, const Smem &S, const Co
 // (circle, obstacle) pair and the bounds, and the per-step residual vectors
 // (g - F xi1 summed per row block).  g is built from r; F xi1 from ref when
 // PRO (first step of a solve: g from the initial samples, F xi1 from the
-// boundary-consistent reference), else from r as well.
-// RES also accumulates the step's squared residual and cost; FIN the smallest
-// squared ellipse distance.
+// boundary-consistent reference), else from r as well.  x2 holds the heading
+// coefficients to use.  RES also accumulates the step's squared residual and
+// cost; FIN the smallest squared ellipse distance.
 template <int M, bool LIT, bool RES, bool FIN, bool PRO>
-__device__ __forceinline__ void sweep(float *sm, const Smem &S, const ConstLayout &L, const float *xi2,
-                                      int t, int tt, const float (&Prow)[12], StepRegs &r,
-                                      const StepRegs &ref)
+__device__ __forceinline__ void sweep(float *sm, const Smem &S, const ConstLayout &L,
+                                      const float (&x2)[12], int t, int tt,
+                                      const float (&Prow)[12], StepRegs &r, const StepRegs &ref)
 {
     const float *cst = sm + S.cst;
-    float x2[12];
-    load12(x2, xi2);
     const float psi = dot11(Prow, x2);
     float psidd = 0.f;
     if (RES) {
@@ -453,37 +582,39 @@ __device__ __forceinline__ void sweep(float *sm, const Smem &S, const ConstLayou
             rob += fn * fmaf(dx, dx, dy * dy) + 2.f * fmaf(dx, ax[i], dy * ay[i]) + ee[i];
         }
     }
-    float *G = sm + S.G + tt * kVecs * L.qs + t;
     const int qs = L.qs;
+    float *Gx = sm + S.G2 + tt * S.RS + t;        // side x: row tt
+    float *Gy = Gx + 8 * S.RS;                    // side y: row 8 + tt
     const float svm = sv - 1.f, sam = sa - 1.f;
     // v and a rows: projected value - F xi1 value
-    G[0 * qs] = PRO ? fmaf(r.xd, svm, r.xd - ref.xd) : r.xd * svm;
-    G[1 * qs] = PRO ? fmaf(r.xdd, sam, r.xdd - ref.xdd) : r.xdd * sam;
-    G[2 * qs] = r0x;
-    G[3 * qs] = r1x + dcx;
-    G[4 * qs] = PRO ? fmaf(r.yd, svm, r.yd - ref.yd) : r.yd * svm;
-    G[5 * qs] = PRO ? fmaf(r.ydd, sam, r.ydd - ref.ydd) : r.ydd * sam;
-    G[6 * qs] = r0y;
-    G[7 * qs] = r1y + dsy;
+    Gx[0] = PRO ? fmaf(r.xd, svm, r.xd - ref.xd) : r.xd * svm;
+    Gx[qs] = PRO ? fmaf(r.xdd, sam, r.xdd - ref.xdd) : r.xdd * sam;
+    Gx[2 * qs] = r0x;
+    Gx[3 * qs] = r1x + dcx;
+    Gy[0] = PRO ? fmaf(r.yd, svm, r.yd - ref.yd) : r.yd * svm;
+    Gy[qs] = PRO ? fmaf(r.ydd, sam, r.ydd - ref.ydd) : r.ydd * sam;
+    Gy[2 * qs] = r0y;
+    Gy[3 * qs] = r1y + dsy;
+    float *GX = sm + S.GX + tt * 4 * qs + t;
     if (RES) {
-        G[8 * qs] = v2 * svm * svm + a2 * sam * sam + rob + dcx * dcx + dsy * dsy;
+        GX[0] = v2 * svm * svm + a2 * sam * sam + rob + dcx * dcx + dsy * dsy;
         const float dp = psi - r.psi_t;
-        G[9 * qs] = dp * dp;
-        G[10 * qs] = fmaf(r.xdd, r.xdd, fmaf(r.ydd, r.ydd, psidd * psidd));
+        GX[qs] = dp * dp;
+        GX[2 * qs] = fmaf(r.xdd, r.xdd, fmaf(r.ydd, r.ydd, psidd * psidd));
     }
-    if (FIN) G[11 * qs] = dmin;
+    if (FIN) GX[3 * qs] = dmin;
     r.psi_prev = psi;
     r.psi_cur = psi;
 }
 
 template <int M, bool LIT>
-__device__ void sweep_dispatch(float *sm, const Smem &S, const ConstLayout &L, const float *xi2,
+__device__ void sweep_dispatch(float *sm, const Smem &S, const ConstLayout &L, const float (&x2)[12],
                                int tt, int t, const float (&Prow)[12], StepRegs &r, bool res,
                                bool fin)
 {
-    if (fin) sweep<M, LIT, true, true, false>(sm, S, L, xi2, t, tt, Prow, r, r);
-    else if (res) sweep<M, LIT, true, false, false>(sm, S, L, xi2, t, tt, Prow, r, r);
-    else sweep<M, LIT, false, false, false>(sm, S, L, xi2, t, tt, Prow, r, r);
+    if (fin) sweep<M, LIT, true, true, false>(sm, S, L, x2, t, tt, Prow, r, r);
+    else if (res) sweep<M, LIT, true, false, false>(sm, S, L, x2, t, tt, Prow, r, r);
+    else sweep<M, LIT, false, false, false>(sm, S, L, x2, t, tt, Prow, r, r);
 }
 
 template <int M, bool LIT>
@@ -506,19 +637,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1) am_fused_kernel(KParams p)
                      :: "r"(smem_u32(bar)), "r"(bytes) : "memory");
         bulk_load(sm + S.cst, p.cblob, bytes, bar);
     }
-    // zero the per-step buffers (their padding past q must read as zero)
-    for (int i = threadIdx.x; i < p.T * (kVecs + 1) * L.qs; i += blockDim.x) sm[S.G + i] = 0.f;
-    for (int i = threadIdx.x; i < 2 * p.T * 48; i += blockDim.x) {
-        sm[S.xi1 + i] = 0.f;
-        sm[S.lam + i] = 0.f;
-    }
-    for (int i = threadIdx.x; i < p.T * 48; i += blockDim.x) sm[S.rb + i] = 0.f;
-    for (int i = threadIdx.x; i < p.T * 12; i += blockDim.x) {
-        sm[S.xi2 + i] = 0.f;
-        sm[S.xi2 + p.T * 12 + i] = 0.f;
-        sm[S.dx2 + i] = 0.f;
-        sm[S.lps + i] = 0.f;
-    }
+    // Zero everything past the constants (the padding of the per-step arrays
+    // past q, and the unused rows of the MMA tiles, must read as zero).
+    for (int i = S.xi1 + threadIdx.x; i < S.bar; i += blockDim.x) sm[i] = 0.f;
     // Bounded wait for the staged constants; the block agrees on the outcome
     // before anyone leaves, so no thread is left waiting at a barrier.
     int ok = 0;
@@ -531,7 +652,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) am_fused_kernel(KParams p)
     for (int tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x) {
         const Tile tl = tile_of(tile, p.B, p.ntiles);
         const int Tn = tl.count;
-        // The tile's state: xi1 as given into buffer 1, multipliers into buffer 0.
+        // The tile's state: xi1, xi2 as given into buffer 1, multipliers into buffer 0.
         for (int i = threadIdx.x; i < Tn * STATE; i += blockDim.x) {
             const int tt = i / STATE, e = i - STATE * tt;
             const float v = p.state[(size_t)tl.first * STATE + i];
@@ -540,6 +661,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) am_fused_kernel(KParams p)
             else if (e < 99) sm[S.lam + tt * 48 + ((e - 55) / NV) * 12 + (e - 55) % NV] = v;
             else sm[S.lps + tt * 12 + (e - 99)] = v;
         }
+        for (int i = threadIdx.x; i < Tn * 48; i += blockDim.x) sm[S.rb + i] = 0.f;
         __syncthreads();
         // Reference xi1, xi2 into buffer 0: boundary control points from the
         // boundary conditions on every block that has boundary rows, the rest as given.
@@ -569,10 +691,11 @@ __global__ void __launch_bounds__(kMaxThreads, 1) am_fused_kernel(KParams p)
         // residual against the reference.
         if (stepper) {
             StepRegs ref;
+            float x2[12];
             eval_xy(sm, S, L, sm + S.xi1 + (p.T + tt) * 48, t, Prow, r);
             eval_xy(sm, S, L, sm + S.xi1 + tt * 48, t, Prow, ref);
-            sweep<M, LIT, false, false, true>(sm, S, L, sm + S.xi2 + (p.T + tt) * 12, t, tt, Prow, r, ref);
-            float x2[12];
+            load12(x2, sm + S.xi2 + (p.T + tt) * 12);
+            sweep<M, LIT, false, false, true>(sm, S, L, x2, t, tt, Prow, r, ref);
             load12(x2, sm + S.xi2 + tt * 12);
             r.psi_cur = dot11(Prow, x2);  // heading of the reference c_psi
         }
@@ -591,15 +714,34 @@ __global__ void __launch_bounds__(kMaxThreads, 1) am_fused_kernel(KParams p)
                 // psi_t = psi + wrap(atan2(s, c) - psi), psi the previous heading;
                 // the heading step works on delta = psi_t - P xi2
                 r.psi_t = r.psi_prev + wrap_pi(atan2f(r.s, r.c) - r.psi_prev);
-                sm[S.psit + tt * L.qs + t] = r.psi_t - r.psi_cur;
+                sm[S.PS + tt * L.qs + t] = r.psi_t - r.psi_cur;
             }
+            prepare_accumulators(p, sm, S, tl, cur2);
             __syncthreads();
-            phase_psi(p, sm, S, tl, cur2);
+            phase_psi(p, sm, S, tl);
+            __syncthreads();
+            if (stepper) {
+                // xi2' = xi2 + (Mpsi lam_psi - Mpsi H xi2) + rho W^T delta
+                float x2[12], w[12], b[12];
+                load12(x2, sm + S.xi2 + (cur2 * p.T + tt) * 12);
+                load12(w, sm + S.wdt + tt * 12);
+                load12(b, sm + S.bas + tt * 12);
+                float d2[12];
+#pragma unroll
+                for (int c = 0; c < 12; ++c) {
+                    d2[c] = fmaf(L.rho, w[c], b[c]);
+                    x2[c] += d2[c];
+                }
+                if (t == 0) {
+#pragma unroll
+                    for (int c = 0; c < NV; ++c) {
+                        sm[S.xi2 + ((cur2 ^ 1) * p.T + tt) * 12 + c] = x2[c];
+                        sm[S.dx2 + tt * 12 + c] = d2[c];
+                    }
+                }
+                sweep_dispatch<M, LIT>(sm, S, L, x2, tt, t, Prow, r, res, k == p.iters - 1);
+            }
             cur2 ^= 1;
-            __syncthreads();
-            if (stepper)
-                sweep_dispatch<M, LIT>(sm, S, L, sm + S.xi2 + (cur2 * p.T + tt) * 12, tt, t, Prow, r,
-                                       res, k == p.iters - 1);
             __syncthreads();
             phase_dot(p, sm, S, tl);
             __syncthreads();
@@ -628,12 +770,18 @@ size_t fused_smem_bytes(const ConstLayout &L, int tile)
     return size_t(smem_layout(L, tile).total) * sizeof(float);
 }
 
+int fused_max_tile(const ConstLayout &L)
+{
+    int tmax = kMaxThreads / (L.q > 88 ? L.q : 88);
+    if (tmax > kMaxTile) tmax = kMaxTile;
+    while (tmax > 1 && fused_smem_bytes(L, tmax) > 227 * 1024) --tmax;
+    return tmax < 1 ? 1 : tmax;
+}
+
 int fused_auto_tile(const ConstLayout &L, int B, int num_sms)
 {
     // Largest tile that fits one CTA per SM, then shrink so every SM gets work.
-    int tmax = kMaxThreads / (L.q > 88 ? L.q : 88);
-    if (tmax < 1) tmax = 1;
-    while (tmax > 1 && fused_smem_bytes(L, tmax) > 227 * 1024) --tmax;
+    const int tmax = fused_max_tile(L);
     int want = (B + num_sms - 1) / num_sms;
     if (want < 1) want = 1;
     return want < tmax ? want : tmax;
@@ -647,7 +795,7 @@ int launch_fused(const SolveArgs &a, void *stream, int *launches)
     const ConstLayout &L = a.L;
     int T = a.tile > 0 ? a.tile : fused_auto_tile(L, a.B, sms);
     const int tq = T * (L.q > 88 ? L.q : 88);
-    if (tq > kMaxThreads || T < 1) return -1;
+    if (tq > kMaxThreads || T < 1 || T > kMaxTile) return -1;
     const size_t smem = fused_smem_bytes(L, T);
     if (smem > 227 * 1024) return -1;
     const int threads = (tq + 31) & ~31;

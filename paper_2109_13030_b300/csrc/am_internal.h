@@ -69,6 +69,7 @@ struct ConstLayout {
     int off_wcol;             // [NV][qs]     W = P Mpsi^T, columns
     int off_mt;               // [NS][24]     Minv^T
     int off_mq;               // [NS][24]     (Minv blockdiag(H, H))^T
+    int off_xib;              // [24][52]     [Minv | -Minv Q] on padded indices, row = output
     int off_ends;             // [5][8]       boundary control points per block (xi1 blocks, c_psi)
     int off_kb;               // [2][24]      kb (x side, y side)
     int off_mpsi;             // [NV][12]     Mpsi^T

@@ -306,10 +306,11 @@ ConstLayout make_layout(int q, int m, int n)
     L.q = q;
     L.m = m;
     L.n = n;
-    // A column stride that is 4 mod 8 keeps 128-bit shared loads of
-    // consecutive columns on distinct banks.
-    int qs = align4(q);
-    if (qs % 8 == 0) qs += 4;
+    // Per-step columns are zero-padded to a multiple of 8 steps (the k-step of
+    // the tensor-core contractions), and the stride is 4 mod 8 so that eight
+    // rows read at the same column offset, and 128-bit loads of consecutive
+    // columns, fall on distinct banks.
+    const int qs = ((q + 7) & ~7) + 4;
     L.qs = qs;
     int o = 0;
     L.off_prow = o; o = align4(o + 3 * q * 12);
@@ -317,6 +318,7 @@ ConstLayout make_layout(int q, int m, int n)
     L.off_wcol = o; o = align4(o + NV * qs);
     L.off_mt = o; o = align4(o + NS * 24);
     L.off_mq = o; o = align4(o + NS * 24);
+    L.off_xib = o; o = align4(o + 24 * 52);
     L.off_ends = o; o = align4(o + 5 * 8);
     L.off_kb = o; o = align4(o + 2 * 24);
     L.off_mpsi = o; o = align4(o + NV * 12);
@@ -348,6 +350,16 @@ void fill_constants(const HostSetup &S, const ProblemParams &pp, const ConstLayo
         for (int b = 0; b < NS; ++b) {
             blob[L.off_mt + b * 24 + a] = float(S.Minv[a][b]);
             blob[L.off_mq + b * 24 + a] = float(S.MQ[a][b]);
+        }
+    // Tensor-core operand of the position step: row np (padded output index,
+    // 11 and 23 are pads), column kp < 24 multiplies lam + coef R, kp >= 24
+    // multiplies xi1 (both on padded indices).
+    auto unpad = [](int i) { return i < NV ? i : (i == NV || i == 2 * NV + 1) ? -1 : i - 1; };
+    for (int np = 0; np < 24; ++np)
+        for (int kp = 0; kp < 48; ++kp) {
+            const int a = unpad(np), b = unpad(kp % 24);
+            if (a < 0 || b < 0) continue;
+            blob[L.off_xib + np * 52 + kp] = float(kp < 24 ? S.Minv[a][b] : -S.MQ[a][b]);
         }
     for (int blk = 0; blk < 5; ++blk)
         for (int e = 0; e < 6; ++e) blob[L.off_ends + blk * 8 + e] = float(S.ends[blk][e]);
