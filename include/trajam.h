@@ -173,6 +173,42 @@ AM_API int am_solve_batch_noalloc(const am_problem *h, int B, float *state, floa
                                   float *res_psi, float *cost, float *mind, int iters,
                                   void *stream);
 
+/* Loads a cold-start (or warm) state for B trajectories without solving, as
+ * am_solve_batch does before its first iteration (init: B x 3 x 11
+ * coefficients c_x, c_y, c_psi; warm_lambda: optional B x 55 lambda, lambda_psi).
+ * Used to prepare the problems of a group. */
+AM_API int am_init_state(am_problem *h, int B, const float *init, const float *warm_lambda,
+                         void *stream, int mem);
+
+/* Groups: many problems of different shapes (q, m, n, B) advanced by one
+ * persistent launch (the uneven batching of many independent planning
+ * problems, Sec. III-D applied per trajectory).  Each CTA takes (problem,
+ * tile) work items from a counter, costliest tiles first, and stages a
+ * problem's constants only when its next item belongs to another problem.
+ * A group references its problems, which must outlive it; each problem keeps
+ * its own state, results (am_get_results, am_get_best) and constants.  Every
+ * problem needs a state (am_init_state or an earlier solve) before
+ * am_group_solve.  On a non-default stream a solve is captured once into a
+ * CUDA graph and replayed while the group, the iteration count, the block size
+ * and the stream stay the same; changing a problem's batch size or obstacle
+ * count needs a fresh group. */
+typedef struct am_group am_group;
+AM_API int am_group_create(am_problem *const *problems, int count, am_group **out);
+/* Runs iters iterations of every problem of the group; asynchronous. */
+AM_API int am_group_solve(am_group *g, int iters, void *stream);
+/* Times the group's solve over the block sizes that fit every problem and
+ * keeps the fastest; the problems' states are restored afterwards.  Writes
+ * the chosen block size and its time per solve (ms). */
+AM_API int am_group_autotune(am_group *g, int iters, void *stream, int *threads, float *ms);
+/* AM_GOPT_THREADS: block size (0 = largest, else a multiple of 32).
+ * AM_GOPT_GRAPH: 1 = capture and replay on non-default streams (default). */
+#define AM_GOPT_THREADS 1
+#define AM_GOPT_GRAPH 2
+AM_API int am_group_set_option(am_group *g, int option, int value);
+/* Launches issued by this group so far and work items of its last solve. */
+AM_API int am_group_stats(am_group *g, int *launches, int *items);
+AM_API void am_group_destroy(am_group *g);
+
 AM_API void am_destroy(am_problem *h);
 AM_API const char *am_last_error(void);
 

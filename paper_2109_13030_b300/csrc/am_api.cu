@@ -2,6 +2,7 @@
 // checking, device buffers and the launches of one solve.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -471,3 +472,302 @@ int handle_constants(const am_problem *h, const float **cblob, ConstLayout *L)
 int report_error(int code, const char *msg) { return fail(code, "%s", msg); }
 
 }  // namespace trajam
+
+// ----------------------------------------------------------------- groups
+
+struct am_group {
+    std::vector<am_problem *> probs;
+    int threads = 0;        // block size; 0 = tuned or the kernel maximum
+    bool use_graph = true;
+    FusedProblem *d_probs = nullptr;
+    size_t probs_cap = 0;
+    int *d_items = nullptr;
+    size_t items_cap = 0;
+    int *d_counter = nullptr;
+    size_t counter_cap = 0;
+    std::vector<FusedProblem> h_probs, up_probs;  // built, last uploaded
+    std::vector<int> h_items, up_items;
+    cudaGraphExec_t gexec = nullptr;
+    int g_iters = -1, g_threads = -1, g_nitems = -1;
+    size_t g_smem = 0;
+    cudaStream_t g_stream = nullptr;
+    const FusedProblem *g_probs = nullptr;
+    const int *g_items = nullptr;
+    int launches = 0, nitems = 0;
+    float *d_save = nullptr;  // state copies while tuning
+    size_t save_cap = 0;
+};
+
+namespace {
+
+void drop_graph(am_group *g)
+{
+    if (g->gexec) cudaGraphExecDestroy(g->gexec);
+    g->gexec = nullptr;
+    g->g_iters = g->g_threads = g->g_nitems = -1;
+}
+
+// Work list: per problem its tile size for this block size and its tiles; the
+// problems with the costliest tiles first (longest-processing-time order), the
+// tiles of one problem together so a CTA rarely re-stages constants.
+int build_work(am_group *g, int threads, int iters, size_t *smem)
+{
+    const int np = int(g->probs.size());
+    g->h_probs.resize(np);
+    std::memset(static_cast<void *>(g->h_probs.data()), 0, sizeof(FusedProblem) * np);
+    std::vector<std::pair<double, int>> order;
+    *smem = 0;
+    for (int i = 0; i < np; ++i) {
+        am_problem *h = g->probs[i];
+        const int T = group_tile(h->L, threads);
+        if (T < 1) return fail(AM_ERR_ARG, "problem %d (q=%d, n=%d) does not fit a block of %d", i, h->pp.q, h->n, threads);
+        FusedProblem &f = g->h_probs[i];
+        f.cblob = h->d_blob;
+        f.L = h->L;
+        f.B = h->B;
+        f.iters = iters;
+        f.T = T;
+        f.ntiles = (h->B + T - 1) / T;
+        f.state = h->d_state;
+        f.res = h->d_out;
+        f.res_psi = h->d_out + h->B;
+        f.cost = h->d_out + 2 * size_t(h->B);
+        f.mind = h->d_out + 3 * size_t(h->B);
+        f.hist = nullptr;
+        f.err = h->d_err;  // a failed wait shows in the problem's own getters
+        const size_t sm = fused_smem_bytes(h->L, T);
+        if (sm > *smem) *smem = sm;
+        const double tile_cost = double(T) * h->pp.q * (12.0 * h->pp.m * h->n + 250.0);
+        order.push_back({-tile_cost, i});
+    }
+    std::sort(order.begin(), order.end());
+    g->h_items.clear();
+    for (auto &o : order)
+        for (int t = 0; t < g->h_probs[o.second].ntiles; ++t) {
+            g->h_items.push_back(o.second);
+            g->h_items.push_back(t);
+        }
+    g->nitems = int(g->h_items.size() / 2);
+    return AM_OK;
+}
+
+int group_launch(am_group *g, int iters, cudaStream_t st)
+{
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int threads = g->threads > 0 ? g->threads : fused_max_threads();
+    size_t smem = 0;
+    int rc = build_work(g, threads, iters, &smem);
+    if (rc) return rc;
+    rc = ensure(g->d_probs, g->probs_cap, g->h_probs.size(), "group descriptors");
+    if (!rc) rc = ensure(g->d_items, g->items_cap, g->h_items.size(), "group work list");
+    if (rc) return rc;
+    // Upload only what changed since the last solve (descriptors are compared
+    // bytewise: they are zero-filled before their fields are set).  A copy from
+    // pageable memory has read its source when the call returns.
+    const size_t pb = sizeof(FusedProblem) * g->h_probs.size(), ib = sizeof(int) * g->h_items.size();
+    if (g->up_probs.size() != g->h_probs.size() || std::memcmp(g->up_probs.data(), g->h_probs.data(), pb)) {
+        CK(cudaMemcpyAsync(g->d_probs, g->h_probs.data(), pb, cudaMemcpyHostToDevice, st), "descriptor upload");
+        g->up_probs = g->h_probs;
+    }
+    if (g->up_items != g->h_items) {
+        CK(cudaMemcpyAsync(g->d_items, g->h_items.data(), ib, cudaMemcpyHostToDevice, st), "work list upload");
+        g->up_items = g->h_items;
+    }
+    GroupLaunch gl;
+    gl.d_probs = g->d_probs;
+    gl.d_items = g->d_items;
+    gl.nitems = g->nitems;
+    gl.d_counter = g->d_counter;
+    gl.threads = threads;
+    gl.smem = smem;
+    gl.grid = g->nitems < sms ? g->nitems : sms;
+    const bool graph = g->use_graph && st != nullptr;
+    if (!graph) {
+        rc = launch_group(gl, st, &g->launches);
+        return rc == -1 ? fail(AM_ERR_ARG, "group does not fit the kernel")
+                        : rc ? fail(AM_ERR_CUDA, "group launch failed") : AM_OK;
+    }
+    if (!g->gexec || g->g_iters != iters || g->g_threads != threads || g->g_nitems != g->nitems ||
+        g->g_smem != smem || g->g_stream != st) {
+        drop_graph(g);
+        cudaGraph_t graph_obj = nullptr;
+        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
+        rc = launch_group(gl, st, nullptr);
+        cudaError_t e = cudaStreamEndCapture(st, &graph_obj);
+        if (rc || e != cudaSuccess) {
+            if (graph_obj) cudaGraphDestroy(graph_obj);
+            return fail(AM_ERR_CUDA, "graph capture of the group launch failed");
+        }
+        e = cudaGraphInstantiate(&g->gexec, graph_obj, 0);
+        cudaGraphDestroy(graph_obj);
+        if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+        g->g_iters = iters;
+        g->g_threads = threads;
+        g->g_nitems = g->nitems;
+        g->g_smem = smem;
+        g->g_stream = st;
+        g->g_probs = g->d_probs;
+        g->g_items = g->d_items;
+    }
+    CK(cudaGraphLaunch(g->gexec, st), "graph launch");
+    ++g->launches;
+    return AM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int am_init_state(am_problem *h, int B, const float *init, const float *warm_lambda, void *stream,
+                  int mem)
+{
+    if (!h || !init) return fail(AM_ERR_ARG, "null argument");
+    if (B < 1 || B > (1 << 24)) return fail(AM_ERR_ARG, "B must be in [1, 2^24]");
+    if (mem != AM_HOST && mem != AM_DEVICE) return fail(AM_ERR_ARG, "bad mem flag");
+    h->stream = static_cast<cudaStream_t>(stream);
+    int rc = check_B(h, B);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(h->d_in, init, sizeof(float) * 33 * B, kind_in(mem), h->stream), "init copy");
+    const float *warm = nullptr;
+    if (warm_lambda) {
+        CK(cudaMemcpyAsync(h->d_in + 33 * size_t(B), warm_lambda, sizeof(float) * 55 * B, kind_in(mem),
+                           h->stream),
+           "warm copy");
+        warm = h->d_in + 33 * size_t(B);
+    }
+    if (launch_init_state(h->d_state, h->d_in, warm, B, h->stream, nullptr))
+        return fail(AM_ERR_CUDA, "init launch failed");
+    CK(cudaMemsetAsync(h->d_out, 0, sizeof(float) * 4 * B, h->stream), "memset");
+    h->B = B;
+    h->solved = true;
+    return AM_OK;
+}
+
+int am_group_create(am_problem *const *problems, int count, am_group **out)
+{
+    if (!problems || !out || count < 1) return fail(AM_ERR_ARG, "need at least one problem");
+    *out = nullptr;
+    for (int i = 0; i < count; ++i)
+        if (!problems[i]) return fail(AM_ERR_ARG, "null problem %d", i);
+    am_group *g = new (std::nothrow) am_group;
+    if (!g) return fail(AM_ERR_ARG, "out of host memory");
+    g->probs.assign(problems, problems + count);
+    const int rc = ensure(g->d_counter, g->counter_cap, 1, "work counter");
+    if (rc) {
+        am_group_destroy(g);
+        return rc;
+    }
+    *out = g;
+    return AM_OK;
+}
+
+void am_group_destroy(am_group *g)
+{
+    if (!g) return;
+    drop_graph(g);
+    cudaFree(g->d_probs);
+    cudaFree(g->d_items);
+    cudaFree(g->d_counter);
+    cudaFree(g->d_save);
+    delete g;
+}
+
+int am_group_set_option(am_group *g, int option, int value)
+{
+    if (!g) return fail(AM_ERR_ARG, "null group");
+    if (option == AM_GOPT_THREADS) {
+        if (value != 0 && (value < 32 || value > fused_max_threads() || value % 32))
+            return fail(AM_ERR_ARG, "threads must be 0 or a multiple of 32 up to %d", fused_max_threads());
+        g->threads = value;
+        return AM_OK;
+    }
+    if (option == AM_GOPT_GRAPH) {
+        g->use_graph = value != 0;
+        if (!g->use_graph) drop_graph(g);
+        return AM_OK;
+    }
+    return fail(AM_ERR_ARG, "unknown group option %d", option);
+}
+
+int am_group_solve(am_group *g, int iters, void *stream)
+{
+    if (!g) return fail(AM_ERR_ARG, "null group");
+    if (iters < 1 || iters > 100000) return fail(AM_ERR_ARG, "iters must be in [1, 100000]");
+    for (size_t i = 0; i < g->probs.size(); ++i)
+        if (!g->probs[i]->solved) return fail(AM_ERR_STATE, "problem %zu has no state (am_init_state)", i);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int before = g->launches;
+    int rc = group_launch(g, iters, st);
+    if (rc) return rc;
+    for (am_problem *h : g->probs) {
+        h->stream = st;
+        h->launches = g->launches - before;
+    }
+    return AM_OK;
+}
+
+int am_group_autotune(am_group *g, int iters, void *stream, int *threads_out, float *ms_out)
+{
+    if (!g) return fail(AM_ERR_ARG, "null group");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // Solves advance the states: keep copies and put them back afterwards.
+    size_t total = 0;
+    for (am_problem *h : g->probs) total += size_t(h->B) * STATE;
+    int rc = ensure(g->d_save, g->save_cap, total, "tuning copies");
+    if (rc) return rc;
+    size_t o = 0;
+    for (am_problem *h : g->probs) {
+        CK(cudaMemcpyAsync(g->d_save + o, h->d_state, sizeof(float) * STATE * h->B,
+                           cudaMemcpyDeviceToDevice, st), "save state");
+        o += size_t(h->B) * STATE;
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int saved = g->threads;
+    int best = 0;
+    float best_ms = 1e30f;
+    for (int threads = 256; threads <= fused_max_threads(); threads += 64) {
+        size_t smem = 0;
+        g->threads = threads;
+        if (build_work(g, threads, iters, &smem) != AM_OK) continue;
+        if (am_group_solve(g, iters, stream) != AM_OK) continue;  // warm-up (and graph capture)
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 3; ++r) am_group_solve(g, iters, stream);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= 3.f;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = threads;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    g->threads = best ? best : saved;
+    o = 0;
+    for (am_problem *h : g->probs) {
+        CK(cudaMemcpyAsync(h->d_state, g->d_save + o, sizeof(float) * STATE * h->B,
+                           cudaMemcpyDeviceToDevice, st), "restore state");
+        o += size_t(h->B) * STATE;
+    }
+    CK(cudaStreamSynchronize(st), "sync");
+    if (!best) return fail(AM_ERR_ARG, "no block size fits every problem of the group");
+    if (threads_out) *threads_out = best;
+    if (ms_out) *ms_out = best_ms;
+    return AM_OK;
+}
+
+int am_group_stats(am_group *g, int *launches, int *items)
+{
+    if (!g) return fail(AM_ERR_ARG, "null group");
+    if (launches) *launches = g->launches;
+    if (items) *items = g->nitems;
+    return AM_OK;
+}
+
+}  // extern "C"

@@ -71,6 +71,7 @@ __host__ __device__ inline Smem smem_layout(const ConstLayout &L, int T)
 {
     Smem s;
     int o = 0;
+    s.bar = o; o += 4;  // one 8-byte mbarrier at a fixed offset, 16-byte aligned
     s.cst = o; o += L.total;
     s.xi1 = o; o += 2 * T * 48;
     s.lam = o; o += 2 * T * 48;
@@ -86,7 +87,6 @@ __host__ __device__ inline Smem smem_layout(const ConstLayout &L, int T)
     s.GX = o; o += T * 4 * L.qs;
     s.PS = o; o += kMaxTile * L.qs;
     o = (o + 3) & ~3;
-    s.bar = o; o += 4;  // one 8-byte mbarrier, kept 16-byte aligned
     s.total = o;
     return s;
 }
@@ -196,13 +196,7 @@ struct Tile {
     int first, count;  // trajectories [first, first + count)
 };
 
-struct KParams {
-    const float *cblob;
-    ConstLayout L;
-    int B, iters, T, ntiles;
-    float *state, *res, *res_psi, *cost, *mind, *hist;
-    int *err;
-};
+using KParams = FusedProblem;
 
 __device__ __forceinline__ Tile tile_of(int i, int B, int ntiles)
 {
@@ -617,153 +611,221 @@ __device__ void sweep_dispatch(float *sm, const Smem &S, const ConstLayout &L, c
     else sweep<M, LIT, false, false, false>(sm, S, L, x2, t, tt, Prow, r, r);
 }
 
-template <int M, bool LIT>
-__global__ void __launch_bounds__(kMaxThreads, 1) am_fused_kernel(KParams p)
+// Stage a problem's constant block into shared memory with one bulk async
+// copy and zero the rest of the dynamic area (the padding of the per-step
+// arrays past q, and the unused rows of the MMA tiles, must read as zero).
+// The wait on the mbarrier is bounded, and the block agrees on its outcome
+// before anyone leaves, so no thread is left waiting at a barrier.
+__device__ bool stage_constants(const KParams &p, float *sm, const Smem &S, uint64_t *bar,
+                                uint32_t parity)
 {
-    extern __shared__ __align__(128) float sm[];
-    const ConstLayout &L = p.L;
-    const Smem S = smem_layout(L, p.T);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + S.bar);
+    if (threadIdx.x == 0) {
+        const uint32_t bytes = uint32_t(p.L.total) * 4u;
+        // order the block's earlier generic-proxy accesses of this area
+        // before the asynchronous copy overwrites it
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n"
+                     :: "r"(smem_u32(bar)), "r"(bytes) : "memory");
+        bulk_load(sm + S.cst, p.cblob, bytes, bar);
+    }
+    for (int i = S.xi1 + threadIdx.x; i < S.total; i += blockDim.x) sm[i] = 0.f;
+    int ok = 0;
+    for (int spin = 0; spin < (1 << 24) && !ok; ++spin) ok = mbar_try_wait(bar, parity) ? 1 : 0;
+    return __syncthreads_and(ok) != 0;
+}
 
-    // Stage the constant block once per CTA.
+__device__ void init_barrier(uint64_t *bar)
+{
     if (threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" :: "r"(smem_u32(bar)));
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        const uint32_t bytes = uint32_t(L.total) * 4u;
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n"
-                     :: "r"(smem_u32(bar)), "r"(bytes) : "memory");
-        bulk_load(sm + S.cst, p.cblob, bytes, bar);
+}
+
+// All iterations of the AM loop for one tile of trajectories of one problem
+// whose constants are staged in shared memory.
+template <int M, bool LIT>
+__device__ void run_tile(const KParams &p, float *sm, const Smem &S, const Tile &tl)
+{
+    const ConstLayout &L = p.L;
+    const int Tn = tl.count;
+    // The tile's state: xi1, xi2 as given into buffer 1, multipliers into buffer 0.
+    for (int i = threadIdx.x; i < Tn * STATE; i += blockDim.x) {
+        const int tt = i / STATE, e = i - STATE * tt;
+        const float v = p.state[(size_t)tl.first * STATE + i];
+        if (e < 44) sm[S.xi1 + (p.T + tt) * 48 + (e / NV) * 12 + e % NV] = v;
+        else if (e < 55) sm[S.xi2 + (p.T + tt) * 12 + (e - 44)] = v;
+        else if (e < 99) sm[S.lam + tt * 48 + ((e - 55) / NV) * 12 + (e - 55) % NV] = v;
+        else sm[S.lps + tt * 12 + (e - 99)] = v;
     }
-    // Zero everything past the constants (the padding of the per-step arrays
-    // past q, and the unused rows of the MMA tiles, must read as zero).
-    for (int i = S.xi1 + threadIdx.x; i < S.bar; i += blockDim.x) sm[i] = 0.f;
-    // Bounded wait for the staged constants; the block agrees on the outcome
-    // before anyone leaves, so no thread is left waiting at a barrier.
-    int ok = 0;
-    for (int spin = 0; spin < (1 << 24) && !ok; ++spin) ok = mbar_try_wait(bar, 0) ? 1 : 0;
-    if (!__syncthreads_and(ok)) {
-        if (threadIdx.x == 0) atomicExch(p.err, 1);
-        return;
+    for (int i = threadIdx.x; i < Tn * 48; i += blockDim.x) sm[S.rb + i] = 0.f;
+    __syncthreads();
+    // Reference xi1, xi2 into buffer 0: boundary control points from the
+    // boundary conditions on every block that has boundary rows, the rest as given.
+    for (int i = threadIdx.x; i < Tn * 55; i += blockDim.x) {
+        const int tt = i / 55, e = i - 55 * tt, blk = e / NV, k = e - NV * blk;
+        const bool has_bc = (blk == 0 || blk == 2 || blk == 4 || L.cs_boundary);
+        float *src = blk < 4 ? sm + S.xi1 + (p.T + tt) * 48 + blk * 12 : sm + S.xi2 + (p.T + tt) * 12;
+        float *dst = blk < 4 ? sm + S.xi1 + tt * 48 + blk * 12 : sm + S.xi2 + tt * 12;
+        float v = src[k];
+        if (has_bc && k <= 2) v = sm[S.cst + L.off_ends + blk * 8 + k];
+        if (has_bc && k >= 8) v = sm[S.cst + L.off_ends + blk * 8 + (k - 5)];
+        dst[k] = v;
     }
+    __syncthreads();
 
-    for (int tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x) {
-        const Tile tl = tile_of(tile, p.B, p.ntiles);
-        const int Tn = tl.count;
-        // The tile's state: xi1, xi2 as given into buffer 1, multipliers into buffer 0.
-        for (int i = threadIdx.x; i < Tn * STATE; i += blockDim.x) {
-            const int tt = i / STATE, e = i - STATE * tt;
-            const float v = p.state[(size_t)tl.first * STATE + i];
-            if (e < 44) sm[S.xi1 + (p.T + tt) * 48 + (e / NV) * 12 + e % NV] = v;
-            else if (e < 55) sm[S.xi2 + (p.T + tt) * 12 + (e - 44)] = v;
-            else if (e < 99) sm[S.lam + tt * 48 + ((e - 55) / NV) * 12 + (e - 55) % NV] = v;
-            else sm[S.lps + tt * 12 + (e - 99)] = v;
-        }
-        for (int i = threadIdx.x; i < Tn * 48; i += blockDim.x) sm[S.rb + i] = 0.f;
+    const int tid = threadIdx.x;
+    const bool stepper = tid < Tn * L.q;
+    const int tt = stepper ? tid / L.q : 0;
+    const int t = stepper ? tid - tt * L.q : 0;
+    float Prow[12];
+    load12(Prow, sm + S.cst + L.off_prow + t * 12);
+    StepRegs r;
+    r.psi_t = 0.f;
+    int cur = 0, cur2 = 0;
+
+    // Step 1 of Sec. III-D: xi3, xi4 and g from the initial samples, the
+    // residual against the reference.
+    if (stepper) {
+        StepRegs ref;
+        float x2[12];
+        eval_xy(sm, S, L, sm + S.xi1 + (p.T + tt) * 48, t, Prow, r);
+        eval_xy(sm, S, L, sm + S.xi1 + tt * 48, t, Prow, ref);
+        load12(x2, sm + S.xi2 + (p.T + tt) * 12);
+        sweep<M, LIT, false, false, true>(sm, S, L, x2, t, tt, Prow, r, ref);
+        load12(x2, sm + S.xi2 + tt * 12);
+        r.psi_cur = dot11(Prow, x2);  // heading of the reference c_psi
+    }
+    __syncthreads();
+    phase_dot(p, sm, S, tl);
+    __syncthreads();
+
+    for (int k = 0; k < p.iters; ++k) {
+        const bool res = (p.hist != nullptr) || (k == p.iters - 1);
+        const bool prev_res = (p.hist != nullptr) && k > 0;
+        phase_xi1(p, sm, S, tl, cur, k == 0, true, prev_res, false, k - 1);
+        cur ^= 1;
         __syncthreads();
-        // Reference xi1, xi2 into buffer 0: boundary control points from the
-        // boundary conditions on every block that has boundary rows, the rest as given.
-        for (int i = threadIdx.x; i < Tn * 55; i += blockDim.x) {
-            const int tt = i / 55, e = i - 55 * tt, blk = e / NV, k = e - NV * blk;
-            const bool has_bc = (blk == 0 || blk == 2 || blk == 4 || L.cs_boundary);
-            float *src = blk < 4 ? sm + S.xi1 + (p.T + tt) * 48 + blk * 12 : sm + S.xi2 + (p.T + tt) * 12;
-            float *dst = blk < 4 ? sm + S.xi1 + tt * 48 + blk * 12 : sm + S.xi2 + tt * 12;
-            float v = src[k];
-            if (has_bc && k <= 2) v = sm[S.cst + L.off_ends + blk * 8 + k];
-            if (has_bc && k >= 8) v = sm[S.cst + L.off_ends + blk * 8 + (k - 5)];
-            dst[k] = v;
-        }
-        __syncthreads();
-
-        const int tid = threadIdx.x;
-        const bool stepper = tid < Tn * L.q;
-        const int tt = stepper ? tid / L.q : 0;
-        const int t = stepper ? tid - tt * L.q : 0;
-        float Prow[12];
-        load12(Prow, sm + S.cst + L.off_prow + t * 12);
-        StepRegs r;
-        r.psi_t = 0.f;
-        int cur = 0, cur2 = 0;
-
-        // Step 1 of Sec. III-D: xi3, xi4 and g from the initial samples, the
-        // residual against the reference.
         if (stepper) {
-            StepRegs ref;
-            float x2[12];
-            eval_xy(sm, S, L, sm + S.xi1 + (p.T + tt) * 48, t, Prow, r);
-            eval_xy(sm, S, L, sm + S.xi1 + tt * 48, t, Prow, ref);
-            load12(x2, sm + S.xi2 + (p.T + tt) * 12);
-            sweep<M, LIT, false, false, true>(sm, S, L, x2, t, tt, Prow, r, ref);
-            load12(x2, sm + S.xi2 + tt * 12);
-            r.psi_cur = dot11(Prow, x2);  // heading of the reference c_psi
+            eval_xy(sm, S, L, sm + S.xi1 + (cur * p.T + tt) * 48, t, Prow, r);
+            // psi_t = psi + wrap(atan2(s, c) - psi), psi the previous heading;
+            // the heading step works on delta = psi_t - P xi2
+            r.psi_t = r.psi_prev + wrap_pi(atan2f(r.s, r.c) - r.psi_prev);
+            sm[S.PS + tt * L.qs + t] = r.psi_t - r.psi_cur;
         }
+        prepare_accumulators(p, sm, S, tl, cur2);
+        __syncthreads();
+        phase_psi(p, sm, S, tl);
+        __syncthreads();
+        if (stepper) {
+            // xi2' = xi2 + (Mpsi lam_psi - Mpsi H xi2) + rho W^T delta
+            float x2[12], w[12], b[12];
+            load12(x2, sm + S.xi2 + (cur2 * p.T + tt) * 12);
+            load12(w, sm + S.wdt + tt * 12);
+            load12(b, sm + S.bas + tt * 12);
+            float d2[12];
+#pragma unroll
+            for (int c = 0; c < 12; ++c) {
+                d2[c] = fmaf(L.rho, w[c], b[c]);
+                x2[c] += d2[c];
+            }
+            if (t == 0) {
+#pragma unroll
+                for (int c = 0; c < NV; ++c) {
+                    sm[S.xi2 + ((cur2 ^ 1) * p.T + tt) * 12 + c] = x2[c];
+                    sm[S.dx2 + tt * 12 + c] = d2[c];
+                }
+            }
+            sweep_dispatch<M, LIT>(sm, S, L, x2, tt, t, Prow, r, res, k == p.iters - 1);
+        }
+        cur2 ^= 1;
         __syncthreads();
         phase_dot(p, sm, S, tl);
         __syncthreads();
+    }
+    // Multipliers of the last iteration and the final per-trajectory results.
+    phase_xi1(p, sm, S, tl, cur, false, false, true, true, p.iters - 1);
+    cur ^= 1;
+    __syncthreads();
+    for (int i = threadIdx.x; i < Tn * STATE; i += blockDim.x) {
+        const int tq = i / STATE, e = i - STATE * tq;
+        float v;
+        if (e < 44) v = sm[S.xi1 + (cur * p.T + tq) * 48 + (e / NV) * 12 + e % NV];
+        else if (e < 55) v = sm[S.xi2 + (cur2 * p.T + tq) * 12 + (e - 44)];
+        else if (e < 99) v = sm[S.lam + (cur * p.T + tq) * 48 + ((e - 55) / NV) * 12 + (e - 55) % NV];
+        else v = sm[S.lps + tq * 12 + (e - 99)];
+        p.state[(size_t)tl.first * STATE + i] = v;
+    }
+    __syncthreads();
+}
 
-        for (int k = 0; k < p.iters; ++k) {
-            const bool res = (p.hist != nullptr) || (k == p.iters - 1);
-            const bool prev_res = (p.hist != nullptr) && k > 0;
-            phase_xi1(p, sm, S, tl, cur, k == 0, true, prev_res, false, k - 1);
-            cur ^= 1;
-            __syncthreads();
-            if (stepper) {
-                eval_xy(sm, S, L, sm + S.xi1 + (cur * p.T + tt) * 48, t, Prow, r);
-                // psi_t = psi + wrap(atan2(s, c) - psi), psi the previous heading;
-                // the heading step works on delta = psi_t - P xi2
-                r.psi_t = r.psi_prev + wrap_pi(atan2f(r.s, r.c) - r.psi_prev);
-                sm[S.PS + tt * L.qs + t] = r.psi_t - r.psi_cur;
-            }
-            prepare_accumulators(p, sm, S, tl, cur2);
-            __syncthreads();
-            phase_psi(p, sm, S, tl);
-            __syncthreads();
-            if (stepper) {
-                // xi2' = xi2 + (Mpsi lam_psi - Mpsi H xi2) + rho W^T delta
-                float x2[12], w[12], b[12];
-                load12(x2, sm + S.xi2 + (cur2 * p.T + tt) * 12);
-                load12(w, sm + S.wdt + tt * 12);
-                load12(b, sm + S.bas + tt * 12);
-                float d2[12];
-#pragma unroll
-                for (int c = 0; c < 12; ++c) {
-                    d2[c] = fmaf(L.rho, w[c], b[c]);
-                    x2[c] += d2[c];
-                }
-                if (t == 0) {
-#pragma unroll
-                    for (int c = 0; c < NV; ++c) {
-                        sm[S.xi2 + ((cur2 ^ 1) * p.T + tt) * 12 + c] = x2[c];
-                        sm[S.dx2 + tt * 12 + c] = d2[c];
-                    }
-                }
-                sweep_dispatch<M, LIT>(sm, S, L, x2, tt, t, Prow, r, res, k == p.iters - 1);
-            }
-            cur2 ^= 1;
-            __syncthreads();
-            phase_dot(p, sm, S, tl);
-            __syncthreads();
-        }
-        // Multipliers of the last iteration and the final per-trajectory results.
-        phase_xi1(p, sm, S, tl, cur, false, false, true, true, p.iters - 1);
-        cur ^= 1;
+template <int M, bool LIT>
+__global__ void __launch_bounds__(kMaxThreads, 1) am_fused_kernel(KParams p)
+{
+    extern __shared__ __align__(128) float sm[];
+    const Smem S = smem_layout(p.L, p.T);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + S.bar);
+    init_barrier(bar);
+    if (!stage_constants(p, sm, S, bar, 0)) {
+        if (threadIdx.x == 0) atomicExch(p.err, 1);
+        return;
+    }
+    for (int tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x)
+        run_tile<M, LIT>(p, sm, S, tile_of(tile, p.B, p.ntiles));
+}
+
+// Uneven batching: one persistent launch over the tiles of many problems of
+// different batch size, horizon, obstacle and circle counts.  CTAs take work
+// items (problem, tile) from a list in order, through one atomic counter; the
+// constants are re-staged whenever a CTA moves to another problem.
+__global__ void __launch_bounds__(kMaxThreads, 1)
+am_group_kernel(const KParams *probs, const int *items, int nitems, int *counter)
+{
+    extern __shared__ __align__(128) float sm[];
+    __shared__ KParams kp;
+    __shared__ int s_item;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm);  // fixed: the layout below starts past it
+    init_barrier(bar);
+    int cur = -1;
+    uint32_t parity = 0;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
         __syncthreads();
-        for (int i = threadIdx.x; i < Tn * STATE; i += blockDim.x) {
-            const int tq = i / STATE, e = i - STATE * tq;
-            float v;
-            if (e < 44) v = sm[S.xi1 + (cur * p.T + tq) * 48 + (e / NV) * 12 + e % NV];
-            else if (e < 55) v = sm[S.xi2 + (cur2 * p.T + tq) * 12 + (e - 44)];
-            else if (e < 99) v = sm[S.lam + (cur * p.T + tq) * 48 + ((e - 55) / NV) * 12 + (e - 55) % NV];
-            else v = sm[S.lps + tq * 12 + (e - 99)];
-            p.state[(size_t)tl.first * STATE + i] = v;
+        const int it = s_item;
+        if (it >= nitems) break;
+        const int2 item = make_int2(items[2 * it], items[2 * it + 1]);
+        if (item.x != cur) {
+            if (threadIdx.x == 0) kp = probs[item.x];
+            __syncthreads();
+            if (!stage_constants(kp, sm, smem_layout(kp.L, kp.T), bar, parity)) {
+                if (threadIdx.x == 0) atomicExch(kp.err, 1);
+                return;
+            }
+            parity ^= 1u;
+            cur = item.x;
+        }
+        const Smem S = smem_layout(kp.L, kp.T);
+        const Tile tl = tile_of(item.y, kp.B, kp.ntiles);
+        switch (kp.L.m * 2 + (kp.L.alpha_mode ? 1 : 0)) {
+        case 2: run_tile<1, false>(kp, sm, S, tl); break;
+        case 3: run_tile<1, true>(kp, sm, S, tl); break;
+        case 4: run_tile<2, false>(kp, sm, S, tl); break;
+        case 5: run_tile<2, true>(kp, sm, S, tl); break;
+        case 6: run_tile<3, false>(kp, sm, S, tl); break;
+        case 7: run_tile<3, true>(kp, sm, S, tl); break;
+        case 8: run_tile<4, false>(kp, sm, S, tl); break;
+        default: run_tile<4, true>(kp, sm, S, tl); break;
         }
         __syncthreads();
     }
 }
 
 }  // namespace
+
+// The group kernel's static shared memory (its problem descriptor) comes out
+// of the same 227 KB as the dynamic area.
+constexpr size_t kGroupSmemMax = 227 * 1024 - 512;
 
 size_t fused_smem_bytes(const ConstLayout &L, int tile)
 {
@@ -776,6 +838,29 @@ int fused_max_tile(const ConstLayout &L)
     if (tmax > kMaxTile) tmax = kMaxTile;
     while (tmax > 1 && fused_smem_bytes(L, tmax) > 227 * 1024) --tmax;
     return tmax < 1 ? 1 : tmax;
+}
+
+int fused_max_threads() { return kMaxThreads; }
+
+int group_tile(const ConstLayout &L, int threads)
+{
+    int t = threads / (L.q > 88 ? L.q : 88);
+    if (t > kMaxTile) t = kMaxTile;
+    while (t >= 1 && fused_smem_bytes(L, t) > kGroupSmemMax) --t;
+    return t < 1 ? 0 : t;
+}
+
+int launch_group(const GroupLaunch &g, void *stream, int *launches)
+{
+    if (g.threads < 32 || g.threads > kMaxThreads || g.smem > kGroupSmemMax || g.nitems < 1) return -1;
+    if (cudaFuncSetAttribute(am_group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(g.smem)) != cudaSuccess)
+        return -2;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(g.d_counter, 0, sizeof(int), st) != cudaSuccess) return -2;
+    am_group_kernel<<<g.grid, g.threads, g.smem, st>>>(g.d_probs, g.d_items, g.nitems, g.d_counter);
+    if (launches) ++*launches;
+    return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
 int fused_auto_tile(const ConstLayout &L, int B, int num_sms)

@@ -106,6 +106,32 @@ struct SolveArgs {
 
 // Fused persistent kernel: every iteration of the loop in one launch.
 int launch_fused(const SolveArgs &a, void *stream, int *launches);
+
+// One problem as the fused kernels see it (also the element of the work
+// descriptor array of a grouped launch).
+struct FusedProblem {
+    const float *cblob;
+    ConstLayout L;
+    int B, iters, T, ntiles;
+    float *state, *res, *res_psi, *cost, *mind, *hist;
+    int *err;
+};
+
+// Grouped launch: many problems' tiles in one persistent kernel.
+struct GroupLaunch {
+    const FusedProblem *d_probs;  // device array, one per problem
+    const int *d_items;           // device array of (problem, tile) pairs
+    int nitems;
+    int *d_counter;               // work counter, reset before each launch
+    int threads;
+    size_t smem;
+    int grid;
+};
+// Tile size (trajectories per CTA) of a problem in a grouped launch of the
+// given block size; 0 when the problem does not fit.
+int group_tile(const ConstLayout &L, int threads);
+int fused_max_threads();
+int launch_group(const GroupLaunch &g, void *stream, int *launches);
 // Unfused comparator: one launch per step, intermediates in global memory.
 int launch_plain(const SolveArgs &a, float *scratch, size_t scratch_floats, void *stream,
                  int *launches);

@@ -20,12 +20,15 @@ AM_HOST, AM_DEVICE = 0, 1
 AM_FP32, AM_TF32, AM_BF16 = 0, 1, 2
 AM_KERNEL_FUSED, AM_KERNEL_PLAIN = 0, 1
 AM_OPT_KERNEL, AM_OPT_TILE = 1, 2
+AM_GOPT_THREADS, AM_GOPT_GRAPH = 1, 2
 AM_NV, AM_STATE_FLOATS = 11, 110
 
 EXPORTS = ["am_init_problem", "am_set_obstacles", "am_set_boundary", "am_solve_batch",
            "am_get_results", "am_get_best", "am_get_state", "am_set_state", "am_set_history",
            "am_get_history", "am_set_option", "am_set_stream", "am_last_solve_stats",
-           "am_solve_batch_noalloc", "am_destroy", "am_last_error"]
+           "am_solve_batch_noalloc", "am_init_state", "am_group_create", "am_group_solve",
+           "am_group_autotune", "am_group_set_option", "am_group_stats", "am_group_destroy",
+           "am_destroy", "am_last_error"]
 
 
 class AmProblemDesc(C.Structure):
@@ -63,6 +66,13 @@ def _load():
         "am_set_stream": ([vp, vp], ip),
         "am_last_solve_stats": ([vp, C.POINTER(C.c_int)], ip),
         "am_solve_batch_noalloc": ([vp, ip, fp, fp, fp, fp, fp, ip, vp], ip),
+        "am_init_state": ([vp, ip, fp, fp, vp, ip], ip),
+        "am_group_create": ([C.POINTER(vp), ip, C.POINTER(vp)], ip),
+        "am_group_solve": ([vp, ip, vp], ip),
+        "am_group_autotune": ([vp, ip, vp, C.POINTER(C.c_int), C.POINTER(C.c_float)], ip),
+        "am_group_set_option": ([vp, ip, ip], ip),
+        "am_group_stats": ([vp, C.POINTER(C.c_int), C.POINTER(C.c_int)], ip),
+        "am_group_destroy": ([vp], None),
         "am_destroy": ([vp], None),
         "am_last_error": ([], C.c_char_p),
     }
@@ -209,6 +219,45 @@ def am_solve_batch_noalloc(h, B, state, res, res_psi, cost, mind, iters, stream=
                                        _stream_ptr(stream)))
 
 
+def am_init_state(h, B, init, warm_lambda=None, stream=None):
+    pi, mem, ki = _buf(init)
+    pw, memw, kw = _buf(warm_lambda)
+    if warm_lambda is not None and mem != memw:
+        raise ValueError("init and warm_lambda must both be host or both be device memory")
+    _check(_lib.am_init_state(h, int(B), pi, pw, _stream_ptr(stream), mem))
+
+
+def am_group_create(handles) -> int:
+    arr = (C.c_void_p * len(handles))(*handles)
+    g = C.c_void_p()
+    _check(_lib.am_group_create(arr, len(handles), C.byref(g)))
+    return g.value
+
+
+def am_group_solve(g, iters, stream=None):
+    _check(_lib.am_group_solve(g, int(iters), _stream_ptr(stream)))
+
+
+def am_group_autotune(g, iters, stream=None):
+    t, ms = C.c_int(), C.c_float()
+    _check(_lib.am_group_autotune(g, int(iters), _stream_ptr(stream), C.byref(t), C.byref(ms)))
+    return t.value, ms.value
+
+
+def am_group_set_option(g, option, value):
+    _check(_lib.am_group_set_option(g, int(option), int(value)))
+
+
+def am_group_stats(g):
+    n, k = C.c_int(), C.c_int()
+    _check(_lib.am_group_stats(g, C.byref(n), C.byref(k)))
+    return n.value, k.value
+
+
+def am_group_destroy(g):
+    _lib.am_group_destroy(g)
+
+
 def am_destroy(h):
     _lib.am_destroy(h)
 
@@ -236,6 +285,11 @@ class Problem:
 
     def set_obstacles(self, xo, yo, a, b):
         am_set_obstacles(self.h, len(a), xo, yo, a, b)
+
+    def init_state(self, init, warm_lambda=None, stream=None):
+        am_init_state(self.h, int(init.shape[0]), init, warm_lambda, stream)
+        self.B = int(init.shape[0])
+        return self
 
     def solve(self, init, iters, warm_lambda=None, stream=None, history=False):
         am_set_history(self.h, history)
@@ -266,6 +320,39 @@ class Problem:
         if self.h:
             am_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Group:
+    """Many Problems advanced by one persistent launch per solve."""
+
+    def __init__(self, problems, threads=0, graph=True):
+        self.problems = list(problems)   # keeps the handles alive
+        self.g = am_group_create([p.h for p in self.problems])
+        am_group_set_option(self.g, AM_GOPT_THREADS, threads)
+        am_group_set_option(self.g, AM_GOPT_GRAPH, int(bool(graph)))
+
+    def solve(self, iters, stream=None):
+        am_group_solve(self.g, iters, stream)
+        for p in self.problems:
+            p.iters = iters
+        return self
+
+    def autotune(self, iters, stream=None):
+        return am_group_autotune(self.g, iters, stream)
+
+    def stats(self):
+        return am_group_stats(self.g)
+
+    def close(self):
+        if self.g:
+            am_group_destroy(self.g)
+            self.g = None
 
     def __del__(self):
         try:
