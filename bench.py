@@ -149,6 +149,66 @@ def cpu_baseline(pb, sample_B: int, iters: int) -> dict:
             "sample": f"{sample_B} of the {pb['B']} trajectories x {iters} iterations, {dt:.1f} s wall"}
 
 
+def bench_uneven(TJ, W, torch, dev, flush, steps: int, iters: int = 100) -> dict:
+    """64 problems of mixed shape (B 128..2048, q in {50, 100, 150}, 2..32
+    moving ellipses, 2..4 circles), 100 iterations each: one grouped launch
+    (autotuned block size, replayed CUDA graph on a side stream) against one
+    fused launch per problem on the same stream."""
+    pbs = W.make_uneven(0, count=64)
+    side = torch.cuda.Stream(dev)
+    probs = [TJ.Problem(pb) for pb in pbs]
+    inits = [torch.tensor(pb["init"], dtype=torch.float32, device=dev) for pb in pbs]
+
+    def reset():
+        for P, x in zip(probs, inits):
+            P.init_state(x, stream=side)
+
+    reset()
+    G = TJ.Group(probs)
+    threads, _ = G.autotune(iters, stream=side)
+    for _ in range(2):
+        reset()
+        G.solve(iters, stream=side)
+    torch.cuda.synchronize()
+    launches0, items = G.stats()
+    ms = []
+    for i in range(steps):
+        flush.fill_(float(i))
+        reset()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(side)
+        G.solve(iters, stream=side)
+        e1.record(side)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    launches = (G.stats()[0] - launches0) / steps
+    seq = []
+    for i in range(steps):
+        flush.fill_(float(i))
+        reset()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(side)
+        for P in probs:
+            TJ.am_solve_batch(P.h, P.B, None, None, iters, side)
+        e1.record(side)
+        torch.cuda.synchronize()
+        seq.append(e0.elapsed_time(e1))
+    total = sum(pb["B"] for pb in pbs)
+    flops = sum(algorithmic_flops(pb["q"], pb["m"], pb["n"]) * pb["B"] for pb in pbs) * iters
+    g_ms, s_ms = statistics.mean(ms), statistics.mean(seq)
+    G.close()
+    for P in probs:
+        P.close()
+    return {"metric": "trajectory-AM-iterations/sec over 64 mixed problems", "value": total * iters / (g_ms / 1e3),
+            "unit": UNIT, "ms_per_solve": g_ms, "problems": len(pbs), "trajectories": total,
+            "iterations": iters, "work_items": items, "threads": threads, "launches_per_solve": launches,
+            "achieved_tflops": flops / (g_ms / 1e3) / 1e12,
+            "one_launch_per_problem": {"value": total * iters / (s_ms / 1e3), "unit": UNIT,
+                                       "ms_per_solve": s_ms, "launches_per_solve": len(pbs)},
+            "workload": "make_uneven(seed 0, 64 problems): B uniform over 128..2048, q in {50,100,150}, "
+                        "T=q/10 s, n 2..32 moving ellipses, m 2..4 circles over [-0.4, 0.4]"}
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -194,6 +254,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-steps", type=int, default=3)
+    ap.add_argument("--uneven-steps", type=int, default=3)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -211,22 +272,42 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    pb = W.make_problem(WORKLOAD, seed=rank)
+    # One planning problem; its samples are split into contiguous per-rank
+    # ranges of B trajectories (weak scaling), merged at the end of each step.
+    from paper_2109_13030_b300 import dist_best as D
+    pb_all = W.make_problem(WORKLOAD, seed=0, B=B * world)
+    lo, hi = D.shard_range(B * world, rank, world)
+    pb = dict(pb_all, init=pb_all["init"][lo:hi], B=hi - lo)
     P = TJ.Problem(pb)
     init_d = torch.tensor(pb["init"], dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    mind_d = torch.empty(B, dtype=torch.float32, device=dev)
 
-    def step():
-        P.solve(init_d, ITERS, stream=stream)
-        TJ.am_get_best(P.h)  # argmin on the device, 36 floats back
+    def merged_best():
+        best = TJ.am_get_best(P.h)  # argmin on the device, 36 floats back
+        if dist is None:
+            return best
+        TJ.am_get_results(P.h, mind=mind_d)
+        collides = bool(mind_d[best["index"]].item() < 0.99)
+        return D.merge_best(collides, best["cost"], lo + best["index"], best["coeffs"], dev)
+
+    def step(i=None):
+        TJ.am_init_state(P.h, B, init_d, None, stream)          # cold start from resident samples
+        if i is not None:
+            kstarts[i].record(stream)
+        TJ.am_solve_batch(P.h, B, None, None, ITERS, stream)     # the fused kernel
+        if i is not None:
+            kends[i].record(stream)
+        return merged_best()
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    launches_per_solve = TJ.am_last_solve_stats(P.h) + 1  # + argmin
+    launches_per_step = 1 + TJ.am_last_solve_stats(P.h) + 1  # init state, solve, argmin
 
-    # device-timed region: CUDA events around each solve on the solve's stream
+    # Timed region: CUDA events around each step on the solve's stream, and
+    # around the fused kernel inside it (its average launch duration).
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     kstarts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -238,13 +319,11 @@ def main():
         for i in range(args.steps):
             flush.fill_(float(i))
             starts[i].record(stream)
-            TJ.am_solve_batch(P.h, B, init_d, None, ITERS, stream)
-            kends[i].record(stream)
-            TJ.am_get_best(P.h)
+            step(i)
             ends[i].record(stream)
         torch.cuda.synchronize()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    solve_ms = [s.elapsed_time(e) for s, e in zip(starts, kends)]
+    kern_ms = [s.elapsed_time(e) for s, e in zip(kstarts, kends)]
     tot_ms = sum(step_ms)
     if dist:
         t = torch.tensor([tot_ms], device=dev)
@@ -252,19 +331,6 @@ def main():
         tot_ms = float(t.item())
         dist.barrier()
     value = world * B * ITERS * args.steps / (tot_ms / 1e3)
-
-    # fused kernel alone: events around the kernel launch itself
-    kern_ms = []
-    for i in range(args.steps):
-        flush.fill_(float(i))
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        # a fresh state, then time only the fused kernel (the init kernel stays outside)
-        TJ.am_solve_batch(P.h, B, init_d, None, 1, stream)
-        e0.record(stream)
-        TJ.am_solve_batch(P.h, B, None, None, ITERS, stream)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        kern_ms.append(e0.elapsed_time(e1))
     kern_avg = statistics.mean(kern_ms)
     q, m, n = pb["q"], pb["m"], pb["n"]
     flops = algorithmic_flops(q, m, n) * B * ITERS
@@ -286,7 +352,7 @@ def main():
         t0 = time.perf_counter()
         TJ.am_solve_batch(P.h, B, init_h.numpy(), None, ITERS, stream)
         TJ.am_get_results(P.h, *[o.numpy() for o in outs])
-        best = TJ.am_get_best(P.h)
+        best = merged_best()
         e2e_s.append(time.perf_counter() - t0)
     e2e_tot = sum(e2e_s)
     if dist:
@@ -319,10 +385,12 @@ def main():
             "config": {"workload": "paper-shaped: B=1000 per GPU, q=100 steps over 10 s, degree-10 Bernstein, "
                                    "m=3 circles (r=-0.4,0,0.4), 10 moving ellipses, 100 AM iterations, "
                                    "rho=1, then best-trajectory selection",
-                       "parallelism": f"replicas x{world} (independent batches, no collective)",
+                       "parallelism": (f"batch of {B * world} sharded x{world}: no exchange during the "
+                                       "iterations, one best-key all-gather + coefficient broadcast per step"
+                                       if world > 1 else "single GPU"),
                        "l2": "512 MiB buffer rewritten between timed steps",
                        "kernel": "fused persistent (1 launch per solve)"},
-            "gpu_launches": launches_per_solve * args.steps,
+            "gpu_launches": launches_per_step * args.steps,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": measured_traffic(),
                          "kernel": "am_fused_kernel",
@@ -336,6 +404,8 @@ def main():
                                                 "unit": UNIT, "ms_per_solve": statistics.mean(plain_ms),
                                                 "launches_per_solve": plain_launches}},
         }
+        if args.uneven_steps > 0:
+            line["uneven"] = bench_uneven(TJ, W, torch, dev, flush, args.uneven_steps)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(pb, 192, ITERS)
         print(json.dumps(line), flush=True)
