@@ -209,6 +209,70 @@ def bench_uneven(TJ, W, torch, dev, flush, steps: int, iters: int = 100) -> dict
                         "T=q/10 s, n 2..32 moving ellipses, m 2..4 circles over [-0.4, 0.4]"}
 
 
+def serve_run(TJ, W, pbs, mode, kernel, seconds, warmup_s=1.0, rate=400.0, iters=30, seed=7):
+    """One serving run: 64 resident scenes, Poisson arrivals at `rate`/s for
+    warmup_s + seconds; each request picks a scene uniformly, moves its
+    obstacles 0.1 s further along their (linear) tracks and starts the plan
+    from the scene's last best plan at t = 0.1 s.  Latency is the server's
+    submit-to-result time; requests arriving in the warm-up are not counted."""
+    S = TJ.Server(8 << 30, iters, mode=mode)
+    probs = []
+    for pb in pbs:
+        P = TJ.Problem(pb, kernel=kernel)
+        S.add_scene(P, pb["init"].astype(np.float32))
+        probs.append(P)
+    S.start()
+    rng = np.random.default_rng(seed)
+    total = warmup_s + seconds
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=int(total * rate * 1.5) + 16))
+    arrivals = arrivals[arrivals < total]
+    picks = rng.integers(0, len(pbs), size=len(arrivals))
+    vel = [((pb["xo"][:, -1] - pb["xo"][:, 0]) / pb["T"], (pb["yo"][:, -1] - pb["yo"][:, 0]) / pb["T"])
+           for pb in pbs]
+    clock = np.zeros(len(pbs))
+    tickets = []
+    t0 = time.perf_counter()
+    for a, k in zip(arrivals, picks):
+        while True:
+            dt = t0 + a - time.perf_counter()
+            if dt <= 0:
+                break
+            time.sleep(min(dt, 5e-4))
+        clock[k] += 0.1
+        pb = pbs[k]
+        xo = (pb["xo"] + clock[k] * vel[k][0][:, None]).astype(np.float32)
+        yo = (pb["yo"] + clock[k] * vel[k][1][:, None]).astype(np.float32)
+        tickets.append((a, S.submit(int(k), advance=0.1, xo=xo, yo=yo)))
+    res = [(a, S.wait(t, timeout_s=300.0)) for a, t in tickets]
+    stats = S.stats()
+    S.close()
+    for P in probs:
+        P.close()
+    bad = sum(1 for _, r in res if r["status"] != 0)
+    lat = np.array([r["t_done"] - r["t_submit"] for a, r in res if a >= warmup_s]) * 1e3
+    span = max(r["t_done"] for _, r in res) - min(r["t_submit"] for _, r in res)
+    return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "requests_measured": int(len(lat)), "requests": len(res),
+            "failed": bad, "offered_per_s": rate, "served_per_s": len(res) / span,
+            "rounds": stats["rounds"], "mean_batch": float(np.mean([r["batch"] for _, r in res])),
+            "seconds": seconds, "warmup_s": warmup_s}
+
+
+def bench_serving(TJ, W, seconds: float, plain_seconds: float) -> dict:
+    pbs = W.make_uneven(0, count=64)
+    out = {"metric": "re-plan latency (submit to result on the host)", "unit": "ms",
+           "workload": "64 resident scenes of the mixed workload (B 128..2048, q in {50,100,150}, "
+                       "n 2..32, m 2..4), Poisson arrivals at 400/s, 30 warm-started iterations per "
+                       "request, obstacles +0.1 s and start state from the last best plan at +0.1 s, "
+                       "8 GB budget",
+           "iterations_per_request": 30}
+    out["batched"] = serve_run(TJ, W, pbs, TJ.AM_SRV_BATCHED, TJ.AM_KERNEL_FUSED, seconds)
+    out["sequential_fused"] = serve_run(TJ, W, pbs, TJ.AM_SRV_SEQUENTIAL, TJ.AM_KERNEL_FUSED, seconds)
+    out["sequential_plain_fp32_loop"] = serve_run(TJ, W, pbs, TJ.AM_SRV_SEQUENTIAL, TJ.AM_KERNEL_PLAIN,
+                                                  plain_seconds)
+    return out
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -255,6 +319,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-steps", type=int, default=3)
     ap.add_argument("--uneven-steps", type=int, default=3)
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-plain-seconds", type=float, default=2.0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -406,6 +472,8 @@ def main():
         }
         if args.uneven_steps > 0:
             line["uneven"] = bench_uneven(TJ, W, torch, dev, flush, args.uneven_steps)
+        if args.serve_seconds > 0:
+            line["serving"] = bench_serving(TJ, W, args.serve_seconds, args.serve_plain_seconds)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(pb, 192, ITERS)
         print(json.dumps(line), flush=True)

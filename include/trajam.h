@@ -205,9 +205,93 @@ AM_API int am_group_autotune(am_group *g, int iters, void *stream, int *threads,
 #define AM_GOPT_THREADS 1
 #define AM_GOPT_GRAPH 2
 AM_API int am_group_set_option(am_group *g, int option, int value);
+/* Restricts the following solves (and am_group_get_best) to the listed
+ * problems, given by their position in am_group_create's array, each at most
+ * once, in any order; count = 0 selects every problem again.  A captured
+ * launch stays valid across changes of the list (the work list and its
+ * length are uploaded before each replay). */
+AM_API int am_group_set_active(am_group *g, const int *idx, int count);
+/* Best trajectory of every active problem (Fig. 1's selection, per problem):
+ * writes 36 floats per active problem, in the order of the active list:
+ * {index, cost, residual, 33 coefficients c_x, c_y, c_psi}.  With host
+ * memory the call waits (bounded) for the stream. */
+AM_API int am_group_get_best(am_group *g, float *out, int mem, void *stream);
 /* Launches issued by this group so far and work items of its last solve. */
 AM_API int am_group_stats(am_group *g, int *launches, int *items);
 AM_API void am_group_destroy(am_group *g);
+
+/* ------------------------------------------------------------- serving
+ * Re-planning service for the receding-horizon use of the method (Sec. IV:
+ * each new plan starts from the previous one, warm-started, with few
+ * iterations).  A scene is a problem whose state (xi, lambda) stays resident
+ * on the device between requests.  A worker thread serves requests in
+ * rounds: a round takes at most one pending request per scene (oldest
+ * first), applies each request's updates (start state, obstacle tracks),
+ * advances the scenes by `iters` iterations -- all of them in one grouped
+ * launch (AM_SRV_BATCHED; a round of one request uses the scene's own
+ * kernel), or one request per round with the scene's own kernel
+ * (AM_SRV_SEQUENTIAL, the comparator) -- selects each scene's best
+ * trajectory and completes the requests.  Requests that arrive during a
+ * round wait for the next one (continuous batching by rounds).
+ *
+ * Scenes are admitted while the device bytes they hold (am_scene_bytes)
+ * stay within the budget; am_server_add_scene returns AM_ERR_BUDGET beyond
+ * it, and am_server_submit returns AM_ERR_BUDGET when max_pending requests
+ * are queued.  The server uses the scenes' handles from its own thread
+ * between am_server_start and am_server_destroy: the caller must not use
+ * them meanwhile, and destroys them after the server. */
+#define AM_PENDING 1        /* am_server_poll: the request is not finished yet */
+#define AM_SRV_BATCHED 0
+#define AM_SRV_SEQUENTIAL 1
+
+typedef struct {
+    size_t budget_bytes;    /* device bytes all scenes together may hold      */
+    int iters;              /* AM iterations per request                       */
+    int mode;               /* AM_SRV_BATCHED | AM_SRV_SEQUENTIAL              */
+    int max_batch;          /* requests per round (0 = up to one per scene)    */
+    int max_pending;        /* queue bound (0 = 65536)                         */
+} am_server_desc;
+
+typedef struct {
+    int scene;              /* as returned by am_server_add_scene              */
+    double advance;         /* > 0: the start state becomes the scene's last
+                               best plan at t = advance s (position, velocity,
+                               acceleration of x, y and psi); goal unchanged   */
+    const float *xo, *yo;   /* nullable: new obstacle centre tracks, n x q
+                               each, host memory, copied by am_server_submit   */
+} am_request;
+
+typedef struct {
+    int status;             /* AM_OK or the error code of the request's round  */
+    int index;              /* best trajectory of the scene                    */
+    float cost, residual;
+    float coeffs[33];       /* c_x, c_y, c_psi of the best trajectory          */
+    double t_submit, t_start, t_done;  /* seconds, the server's steady clock  */
+    long long round;        /* round that served the request                   */
+    int batch;              /* requests in that round                          */
+} am_result;
+
+typedef struct am_server am_server;
+AM_API int am_server_create(const am_server_desc *desc, am_server **out);
+/* Admits a scene: loads its cold-start state (init: B x 3 x 11, as
+ * am_solve_batch) and returns its number.  Before am_server_start only. */
+AM_API int am_server_add_scene(am_server *s, am_problem *h, int B, const float *init, int mem,
+                               int *scene);
+/* Starts the worker thread (on the device current in the calling thread). */
+AM_API int am_server_start(am_server *s);
+/* Queues a request (thread-safe); returns its ticket.  Requests queued
+ * before am_server_start are served from the first round on. */
+AM_API int am_server_submit(am_server *s, const am_request *req, long long *ticket);
+/* Waits up to timeout_ms for a request; AM_OK with its result (the ticket is
+ * then forgotten), AM_PENDING if it is not finished, AM_ERR_ARG if unknown. */
+AM_API int am_server_poll(am_server *s, long long ticket, am_result *out, int timeout_ms);
+AM_API int am_server_stats(am_server *s, long long *rounds, long long *completed,
+                           size_t *device_bytes);
+/* Stops the worker after its current round; queued requests complete with
+ * AM_ERR_STATE.  Does not destroy the scenes' handles. */
+AM_API void am_server_destroy(am_server *s);
+/* Device bytes a scene of this shape and batch holds (host arithmetic only). */
+AM_API size_t am_scene_bytes(int q, int m, int n, int B);
 
 AM_API void am_destroy(am_problem *h);
 AM_API const char *am_last_error(void);

@@ -92,18 +92,25 @@ struct am_problem {
 
 namespace {
 
-int wait_stream(am_problem *h)
+// Waits (at most 60 s) for the work queued so far on a stream.
+int wait_event(cudaEvent_t ev, cudaStream_t st)
 {
-    CK(cudaEventRecord(h->ev, h->stream), "cudaEventRecord");
+    CK(cudaEventRecord(ev, st), "cudaEventRecord");
     const auto t0 = std::chrono::steady_clock::now();
     for (;;) {
-        const cudaError_t e = cudaEventQuery(h->ev);
-        if (e == cudaSuccess) break;
+        const cudaError_t e = cudaEventQuery(ev);
+        if (e == cudaSuccess) return AM_OK;
         if (e != cudaErrorNotReady) return cuda_fail(e, "stream wait");
         if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(60))
             return fail(AM_ERR_TIMEOUT, "stream did not finish within 60 s");
         std::this_thread::yield();
     }
+}
+
+int wait_stream(am_problem *h)
+{
+    int rc = wait_event(h->ev, h->stream);
+    if (rc) return rc;
     int err = 0;
     CK(cudaMemcpy(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost), "status read");
     if (err) return fail(AM_ERR_TIMEOUT, "a kernel gave up a bounded wait (status %d)", err);
@@ -231,7 +238,8 @@ int am_init_problem(const am_problem_desc *d, am_problem **out)
 void am_destroy(am_problem *h)
 {
     if (!h) return;
-    cudaStreamSynchronize(h->stream);
+    // No wait on h->stream: the caller may have destroyed that stream by now.
+    // cudaFree itself waits for the device work in flight.
     cudaFree(h->d_blob);
     cudaFree(h->d_raw);
     cudaFree(h->d_state);
@@ -477,22 +485,40 @@ int report_error(int code, const char *msg) { return fail(code, "%s", msg); }
 
 struct am_group {
     std::vector<am_problem *> probs;
-    int threads = 0;        // block size; 0 = tuned or the kernel maximum
+    std::vector<int> active;  // problems the next solve advances; empty = all
+    int threads = 0;          // block size; 0 = tuned or the kernel maximum
     bool use_graph = true;
-    FusedProblem *d_probs = nullptr;
-    size_t probs_cap = 0;
-    int *d_items = nullptr;
-    size_t items_cap = 0;
-    int *d_counter = nullptr;
-    size_t counter_cap = 0;
-    std::vector<FusedProblem> h_probs, up_probs;  // built, last uploaded
-    std::vector<int> h_items, up_items;
-    cudaGraphExec_t gexec = nullptr;
-    int g_iters = -1, g_threads = -1, g_nitems = -1;
-    size_t g_smem = 0;
-    cudaStream_t g_stream = nullptr;
-    const FusedProblem *g_probs = nullptr;
-    const int *g_items = nullptr;
+    // One upload region per solve, device and pinned host copies:
+    //   [count per variant (8), list offset per variant (8)] [descriptors]
+    //   [work items of every variant] [active list]
+    char *d_up = nullptr, *h_up = nullptr;
+    size_t up_cap = 0, h_up_cap = 0;
+    std::vector<char> last_up;        // what the device region holds
+    cudaEvent_t up_ev = nullptr;      // recorded after the last upload
+    bool up_pending = false;
+    FusedProblem *d_probs = nullptr;  // views into d_up
+    int *d_items = nullptr, *d_head = nullptr, *d_list = nullptr;
+    int *d_ctl = nullptr;     // {work counter, status} per variant
+    size_t ctl_cap = 0;
+    int *h_status = nullptr;  // pinned copy of the status words
+    cudaEvent_t ev = nullptr;
+    float *d_bests = nullptr; // 36 floats per active problem
+    size_t bests_cap = 0;
+    std::vector<FusedProblem> h_probs;
+    std::vector<int> h_items, solved_list;  // work lists; active list of the last solve
+    int count[kGroupVariants] = {}, offset[kGroupVariants] = {};
+    size_t vsmem[kGroupVariants] = {};      // shared memory per variant kernel
+    // concurrent variant kernels: a stream each, fork and join events
+    cudaStream_t vst[kGroupVariants] = {};
+    cudaEvent_t fork_ev = nullptr, join_ev[kGroupVariants] = {};
+    struct Captured {
+        int mask, threads;
+        cudaStream_t stream;
+        const char *up;
+        size_t smem[kGroupVariants];
+        cudaGraphExec_t exec;
+    };
+    std::vector<Captured> graphs;
     int launches = 0, nitems = 0;
     float *d_save = nullptr;  // state copies while tuning
     size_t save_cap = 0;
@@ -502,21 +528,30 @@ namespace {
 
 void drop_graph(am_group *g)
 {
-    if (g->gexec) cudaGraphExecDestroy(g->gexec);
-    g->gexec = nullptr;
-    g->g_iters = g->g_threads = g->g_nitems = -1;
+    for (auto &c : g->graphs) cudaGraphExecDestroy(c.exec);
+    g->graphs.clear();
 }
 
-// Work list: per problem its tile size for this block size and its tiles; the
-// problems with the costliest tiles first (longest-processing-time order), the
-// tiles of one problem together so a CTA rarely re-stages constants.
-int build_work(am_group *g, int threads, int iters, size_t *smem)
+std::vector<int> active_list(const am_group *g)
+{
+    if (!g->active.empty()) return g->active;
+    std::vector<int> all(g->probs.size());
+    for (size_t i = 0; i < all.size(); ++i) all[i] = int(i);
+    return all;
+}
+
+// Descriptors of every problem (tile size for this block size; shared memory
+// per variant as the largest of its problems, so a captured launch fits
+// whatever subset is active) and the work lists of the active ones, per
+// variant: the problems with the costliest tiles first (longest-processing-
+// time order), the tiles of one problem together so a CTA rarely re-stages
+// constants.
+int build_work(am_group *g, int threads, int iters, int sms)
 {
     const int np = int(g->probs.size());
     g->h_probs.resize(np);
     std::memset(static_cast<void *>(g->h_probs.data()), 0, sizeof(FusedProblem) * np);
-    std::vector<std::pair<double, int>> order;
-    *smem = 0;
+    for (int v = 0; v < kGroupVariants; ++v) g->vsmem[v] = 0;
     for (int i = 0; i < np; ++i) {
         am_problem *h = g->probs[i];
         const int T = group_tile(h->L, threads);
@@ -535,19 +570,135 @@ int build_work(am_group *g, int threads, int iters, size_t *smem)
         f.mind = h->d_out + 3 * size_t(h->B);
         f.hist = nullptr;
         f.err = h->d_err;  // a failed wait shows in the problem's own getters
+        const int v = group_variant(h->L);
         const size_t sm = fused_smem_bytes(h->L, T);
-        if (sm > *smem) *smem = sm;
-        const double tile_cost = double(T) * h->pp.q * (12.0 * h->pp.m * h->n + 250.0);
-        order.push_back({-tile_cost, i});
+        if (sm > g->vsmem[v]) g->vsmem[v] = sm;
     }
-    std::sort(order.begin(), order.end());
-    g->h_items.clear();
-    for (auto &o : order)
-        for (int t = 0; t < g->h_probs[o.second].ntiles; ++t) {
-            g->h_items.push_back(o.second);
-            g->h_items.push_back(t);
+    // Tiles of the active problems: each problem gets a share of the SMs in
+    // proportion to its work and tiles no larger than needed to cover that
+    // share, so that a few small problems still spread over the whole GPU
+    // (a lone problem gets the tile a single-problem solve would use).
+    const std::vector<int> act = active_list(g);
+    auto work = [&](int i) {
+        const am_problem *h = g->probs[i];
+        return double(h->B) * h->pp.q * (12.0 * h->pp.m * h->n + 250.0);
+    };
+    double total = 0;
+    for (int i : act) total += work(i);
+    for (int i : act) {
+        FusedProblem &f = g->h_probs[i];
+        double share = total > 0 ? sms * work(i) / total : 1.0;
+        if (share < 1) share = 1;
+        const int want = int(std::ceil(f.B / share));
+        if (want >= 1 && want < f.T) {
+            f.T = want;
+            f.ntiles = (f.B + f.T - 1) / f.T;
         }
+    }
+    std::vector<std::pair<double, int>> order[kGroupVariants];
+    for (int i : act) {
+        const am_problem *h = g->probs[i];
+        const double tile_cost = double(g->h_probs[i].T) * h->pp.q * (12.0 * h->pp.m * h->n + 250.0);
+        order[group_variant(h->L)].push_back({-tile_cost, i});
+    }
+    g->h_items.clear();
+    for (int v = 0; v < kGroupVariants; ++v) {
+        std::sort(order[v].begin(), order[v].end());
+        g->offset[v] = int(g->h_items.size() / 2);
+        for (auto &o : order[v])
+            for (int t = 0; t < g->h_probs[o.second].ntiles; ++t) {
+                g->h_items.push_back(o.second);
+                g->h_items.push_back(t);
+            }
+        g->count[v] = int(g->h_items.size() / 2) - g->offset[v];
+    }
     g->nitems = int(g->h_items.size() / 2);
+    return AM_OK;
+}
+
+// Packs the header, descriptors, work lists and active list into the pinned
+// staging area and uploads them with one copy, unless the device already
+// holds the same bytes.  The staging area is rewritten only after the
+// previous upload from it has completed (bounded wait).
+int upload_work(am_group *g, cudaStream_t st)
+{
+    const std::vector<int> act = active_list(g);
+    const size_t np = g->h_probs.size();
+    const size_t o_probs = 64, o_items = o_probs + ((sizeof(FusedProblem) * np + 15) & ~size_t(15));
+    const size_t o_list = o_items + sizeof(int) * g->h_items.size();
+    const size_t bytes = o_list + sizeof(int) * act.size();
+    std::vector<char> buf(bytes, 0);
+    std::memcpy(buf.data(), g->count, sizeof(g->count));
+    std::memcpy(buf.data() + 32, g->offset, sizeof(g->offset));
+    std::memcpy(buf.data() + o_probs, g->h_probs.data(), sizeof(FusedProblem) * np);
+    std::memcpy(buf.data() + o_items, g->h_items.data(), sizeof(int) * g->h_items.size());
+    std::memcpy(buf.data() + o_list, act.data(), sizeof(int) * act.size());
+    g->solved_list = act;
+    if (buf == g->last_up) return AM_OK;
+    if (g->up_pending) {
+        int rc = wait_event(g->up_ev, st);
+        if (rc) return rc;
+        g->up_pending = false;
+    }
+    if (bytes > g->up_cap) {
+        cudaFree(g->d_up);  // waits for the device: no kernel still reads it
+        g->d_up = nullptr;
+        g->up_cap = 0;
+        CK(cudaMalloc(&g->d_up, bytes * 2), "group upload region");
+        g->up_cap = bytes * 2;
+    }
+    if (bytes > g->h_up_cap) {
+        if (g->h_up) cudaFreeHost(g->h_up);
+        g->h_up = nullptr;
+        g->h_up_cap = 0;
+        CK(cudaMallocHost(&g->h_up, bytes * 2), "group staging area");
+        g->h_up_cap = bytes * 2;
+    }
+    std::memcpy(g->h_up, buf.data(), bytes);
+    CK(cudaMemcpyAsync(g->d_up, g->h_up, bytes, cudaMemcpyHostToDevice, st), "group upload");
+    CK(cudaEventRecord(g->up_ev, st), "event record");
+    g->up_pending = true;
+    g->last_up.swap(buf);
+    g->d_head = reinterpret_cast<int *>(g->d_up);
+    g->d_probs = reinterpret_cast<FusedProblem *>(g->d_up + o_probs);
+    g->d_items = reinterpret_cast<int *>(g->d_up + o_items);
+    g->d_list = reinterpret_cast<int *>(g->d_up + o_list);
+    return AM_OK;
+}
+
+// Issues the variant kernels of the mask: on the given stream when there is
+// one variant, else forked onto the group's streams and joined back.
+int issue_variants(am_group *g, int mask, int threads, int sms, bool fixed_grid, cudaStream_t st,
+                   int *launches)
+{
+    const int nv = __builtin_popcount(unsigned(mask));
+    GroupLaunch gl;
+    gl.d_probs = g->d_probs;
+    gl.d_items = g->d_items;
+    gl.d_head = g->d_head;
+    gl.d_ctl = g->d_ctl;
+    gl.threads = threads;
+    if (nv > 1) CK(cudaEventRecord(g->fork_ev, st), "fork");
+    for (int v = 0; v < kGroupVariants; ++v) {
+        if (!(mask >> v & 1)) continue;
+        gl.variant = v;
+        gl.smem = g->vsmem[v];
+        gl.grid = fixed_grid || g->count[v] > sms ? sms : g->count[v];
+        cudaStream_t s = st;
+        if (nv > 1) {
+            s = g->vst[v];
+            CK(cudaStreamWaitEvent(s, g->fork_ev, 0), "fork wait");
+        }
+        const char *why = nullptr;
+        const int rc = launch_group(gl, s, launches, &why);
+        if (rc == -1) return fail(AM_ERR_ARG, "group does not fit the kernel");
+        if (rc) return fail(AM_ERR_CUDA, "group launch failed (variant %d, %d threads, %zu B shared): %s", v,
+                            threads, gl.smem, why ? why : "?");
+        if (nv > 1) {
+            CK(cudaEventRecord(g->join_ev[v], s), "join");
+            CK(cudaStreamWaitEvent(st, g->join_ev[v], 0), "join wait");
+        }
+    }
     return AM_OK;
 }
 
@@ -557,62 +708,54 @@ int group_launch(am_group *g, int iters, cudaStream_t st)
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int threads = g->threads > 0 ? g->threads : fused_max_threads();
-    size_t smem = 0;
-    int rc = build_work(g, threads, iters, &smem);
+    int rc = build_work(g, threads, iters, sms);
     if (rc) return rc;
-    rc = ensure(g->d_probs, g->probs_cap, g->h_probs.size(), "group descriptors");
-    if (!rc) rc = ensure(g->d_items, g->items_cap, g->h_items.size(), "group work list");
+    rc = upload_work(g, st);
     if (rc) return rc;
-    // Upload only what changed since the last solve (descriptors are compared
-    // bytewise: they are zero-filled before their fields are set).  A copy from
-    // pageable memory has read its source when the call returns.
-    const size_t pb = sizeof(FusedProblem) * g->h_probs.size(), ib = sizeof(int) * g->h_items.size();
-    if (g->up_probs.size() != g->h_probs.size() || std::memcmp(g->up_probs.data(), g->h_probs.data(), pb)) {
-        CK(cudaMemcpyAsync(g->d_probs, g->h_probs.data(), pb, cudaMemcpyHostToDevice, st), "descriptor upload");
-        g->up_probs = g->h_probs;
+    int mask = 0;
+    for (int v = 0; v < kGroupVariants; ++v)
+        if (g->count[v] > 0) mask |= 1 << v;
+    if (!mask) return AM_OK;
+    if (__builtin_popcount(unsigned(mask)) > 1 && !g->vst[0]) {
+        for (int v = 0; v < kGroupVariants; ++v) {
+            CK(cudaStreamCreateWithFlags(&g->vst[v], cudaStreamNonBlocking), "stream creation");
+            CK(cudaEventCreateWithFlags(&g->join_ev[v], cudaEventDisableTiming), "event creation");
+        }
+        CK(cudaEventCreateWithFlags(&g->fork_ev, cudaEventDisableTiming), "event creation");
     }
-    if (g->up_items != g->h_items) {
-        CK(cudaMemcpyAsync(g->d_items, g->h_items.data(), ib, cudaMemcpyHostToDevice, st), "work list upload");
-        g->up_items = g->h_items;
-    }
-    GroupLaunch gl;
-    gl.d_probs = g->d_probs;
-    gl.d_items = g->d_items;
-    gl.nitems = g->nitems;
-    gl.d_counter = g->d_counter;
-    gl.threads = threads;
-    gl.smem = smem;
-    gl.grid = g->nitems < sms ? g->nitems : sms;
     const bool graph = g->use_graph && st != nullptr;
-    if (!graph) {
-        rc = launch_group(gl, st, &g->launches);
-        return rc == -1 ? fail(AM_ERR_ARG, "group does not fit the kernel")
-                        : rc ? fail(AM_ERR_CUDA, "group launch failed") : AM_OK;
-    }
-    if (!g->gexec || g->g_iters != iters || g->g_threads != threads || g->g_nitems != g->nitems ||
-        g->g_smem != smem || g->g_stream != st) {
-        drop_graph(g);
+    if (!graph) return issue_variants(g, mask, threads, sms, false, st, &g->launches);
+    // A captured launch keeps its grids: one CTA per SM for each variant;
+    // CTAs that find their list empty leave at once.
+    am_group::Captured *hit = nullptr;
+    for (auto &c : g->graphs)
+        if (c.mask == mask && c.threads == threads && c.stream == st && c.up == g->d_up &&
+            !std::memcmp(c.smem, g->vsmem, sizeof(c.smem)))
+            hit = &c;
+    if (!hit) {
+        if (g->graphs.size() >= 16) drop_graph(g);
         cudaGraph_t graph_obj = nullptr;
         CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
-        rc = launch_group(gl, st, nullptr);
+        rc = issue_variants(g, mask, threads, sms, true, st, nullptr);
         cudaError_t e = cudaStreamEndCapture(st, &graph_obj);
         if (rc || e != cudaSuccess) {
             if (graph_obj) cudaGraphDestroy(graph_obj);
-            return fail(AM_ERR_CUDA, "graph capture of the group launch failed");
+            return rc ? rc : cuda_fail(e, "graph capture of the group launch");
         }
-        e = cudaGraphInstantiate(&g->gexec, graph_obj, 0);
+        am_group::Captured c;
+        c.mask = mask;
+        c.threads = threads;
+        c.stream = st;
+        c.up = g->d_up;
+        std::memcpy(c.smem, g->vsmem, sizeof(c.smem));
+        e = cudaGraphInstantiate(&c.exec, graph_obj, 0);
         cudaGraphDestroy(graph_obj);
         if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
-        g->g_iters = iters;
-        g->g_threads = threads;
-        g->g_nitems = g->nitems;
-        g->g_smem = smem;
-        g->g_stream = st;
-        g->g_probs = g->d_probs;
-        g->g_items = g->d_items;
+        g->graphs.push_back(c);
+        hit = &g->graphs.back();
     }
-    CK(cudaGraphLaunch(g->gexec, st), "graph launch");
-    ++g->launches;
+    CK(cudaGraphLaunch(hit->exec, st), "graph launch");
+    g->launches += __builtin_popcount(unsigned(mask));
     return AM_OK;
 }
 
@@ -654,7 +797,15 @@ int am_group_create(am_problem *const *problems, int count, am_group **out)
     am_group *g = new (std::nothrow) am_group;
     if (!g) return fail(AM_ERR_ARG, "out of host memory");
     g->probs.assign(problems, problems + count);
-    const int rc = ensure(g->d_counter, g->counter_cap, 1, "work counter");
+    int rc = ensure(g->d_ctl, g->ctl_cap, 2 * kGroupVariants, "work counters");
+    if (!rc && cudaMemset(g->d_ctl, 0, 2 * kGroupVariants * sizeof(int)) != cudaSuccess)
+        rc = fail(AM_ERR_CUDA, "memset");
+    if (!rc && cudaEventCreateWithFlags(&g->up_ev, cudaEventDisableTiming) != cudaSuccess)
+        rc = fail(AM_ERR_CUDA, "event creation failed");
+    if (!rc && cudaMallocHost(&g->h_status, 2 * kGroupVariants * sizeof(int)) != cudaSuccess)
+        rc = fail(AM_ERR_CUDA, "pinned alloc");
+    if (!rc && cudaEventCreateWithFlags(&g->ev, cudaEventDisableTiming) != cudaSuccess)
+        rc = fail(AM_ERR_CUDA, "event creation failed");
     if (rc) {
         am_group_destroy(g);
         return rc;
@@ -667,9 +818,18 @@ void am_group_destroy(am_group *g)
 {
     if (!g) return;
     drop_graph(g);
-    cudaFree(g->d_probs);
-    cudaFree(g->d_items);
-    cudaFree(g->d_counter);
+    cudaFree(g->d_up);
+    if (g->h_up) cudaFreeHost(g->h_up);
+    cudaFree(g->d_ctl);
+    if (g->h_status) cudaFreeHost(g->h_status);
+    if (g->ev) cudaEventDestroy(g->ev);
+    if (g->up_ev) cudaEventDestroy(g->up_ev);
+    for (int v = 0; v < kGroupVariants; ++v) {
+        if (g->vst[v]) cudaStreamDestroy(g->vst[v]);
+        if (g->join_ev[v]) cudaEventDestroy(g->join_ev[v]);
+    }
+    if (g->fork_ev) cudaEventDestroy(g->fork_ev);
+    cudaFree(g->d_bests);
     cudaFree(g->d_save);
     delete g;
 }
@@ -691,20 +851,60 @@ int am_group_set_option(am_group *g, int option, int value)
     return fail(AM_ERR_ARG, "unknown group option %d", option);
 }
 
+int am_group_set_active(am_group *g, const int *idx, int count)
+{
+    if (!g) return fail(AM_ERR_ARG, "null group");
+    if (count < 0 || (count > 0 && !idx)) return fail(AM_ERR_ARG, "bad active list");
+    std::vector<char> seen(g->probs.size(), 0);
+    for (int k = 0; k < count; ++k) {
+        if (idx[k] < 0 || idx[k] >= int(g->probs.size())) return fail(AM_ERR_ARG, "problem index %d out of range", idx[k]);
+        if (seen[idx[k]]) return fail(AM_ERR_ARG, "problem %d listed twice", idx[k]);
+        seen[idx[k]] = 1;
+    }
+    g->active.assign(idx, idx + count);
+    return AM_OK;
+}
+
 int am_group_solve(am_group *g, int iters, void *stream)
 {
     if (!g) return fail(AM_ERR_ARG, "null group");
     if (iters < 1 || iters > 100000) return fail(AM_ERR_ARG, "iters must be in [1, 100000]");
-    for (size_t i = 0; i < g->probs.size(); ++i)
-        if (!g->probs[i]->solved) return fail(AM_ERR_STATE, "problem %zu has no state (am_init_state)", i);
+    const std::vector<int> act = active_list(g);
+    for (int i : act)
+        if (!g->probs[i]->solved) return fail(AM_ERR_STATE, "problem %d has no state (am_init_state)", i);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int before = g->launches;
     int rc = group_launch(g, iters, st);
     if (rc) return rc;
-    for (am_problem *h : g->probs) {
-        h->stream = st;
-        h->launches = g->launches - before;
+    for (int i : act) {
+        g->probs[i]->stream = st;
+        g->probs[i]->launches = g->launches - before;
     }
+    return AM_OK;
+}
+
+int am_group_get_best(am_group *g, float *out, int mem, void *stream)
+{
+    if (!g || !out) return fail(AM_ERR_ARG, "null argument");
+    if (mem != AM_HOST && mem != AM_DEVICE) return fail(AM_ERR_ARG, "bad mem flag");
+    const std::vector<int> act = active_list(g);
+    for (int i : act)
+        if (!g->probs[i]->solved) return fail(AM_ERR_STATE, "problem %d has no state", i);
+    if (!g->d_up) return fail(AM_ERR_STATE, "no group solve yet");
+    if (act != g->solved_list) return fail(AM_ERR_STATE, "the active list changed since the last solve");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = ensure(g->d_bests, g->bests_cap, 36 * act.size(), "best records");
+    if (rc) return rc;
+    if (launch_group_argmin(g->d_probs, g->d_list, int(act.size()), g->d_bests, st, &g->launches))
+        return fail(AM_ERR_CUDA, "best selection launch failed");
+    CK(cudaMemcpyAsync(out, g->d_bests, sizeof(float) * 36 * act.size(), kind_out(mem), st), "best copy");
+    if (mem == AM_DEVICE) return AM_OK;
+    CK(cudaMemcpyAsync(g->h_status, g->d_ctl, 2 * kGroupVariants * sizeof(int), cudaMemcpyDeviceToHost, st),
+       "status copy");
+    rc = wait_event(g->ev, st);
+    if (rc) return rc;
+    for (int v = 0; v < kGroupVariants; ++v)
+        if (g->h_status[2 * v + 1]) return fail(AM_ERR_TIMEOUT, "a kernel of the group gave up a bounded wait");
     return AM_OK;
 }
 
@@ -723,6 +923,9 @@ int am_group_autotune(am_group *g, int iters, void *stream, int *threads_out, fl
                            cudaMemcpyDeviceToDevice, st), "save state");
         o += size_t(h->B) * STATE;
     }
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -730,14 +933,13 @@ int am_group_autotune(am_group *g, int iters, void *stream, int *threads_out, fl
     int best = 0;
     float best_ms = 1e30f;
     for (int threads = 256; threads <= fused_max_threads(); threads += 64) {
-        size_t smem = 0;
         g->threads = threads;
-        if (build_work(g, threads, iters, &smem) != AM_OK) continue;
+        if (build_work(g, threads, iters, sms) != AM_OK) continue;
         if (am_group_solve(g, iters, stream) != AM_OK) continue;  // warm-up (and graph capture)
         cudaEventRecord(e0, st);
         for (int r = 0; r < 3; ++r) am_group_solve(g, iters, stream);
         cudaEventRecord(e1, st);
-        cudaEventSynchronize(e1);
+        if (wait_event(g->ev, st) != AM_OK) break;
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
         ms /= 3.f;
@@ -755,7 +957,8 @@ int am_group_autotune(am_group *g, int iters, void *stream, int *threads_out, fl
                            cudaMemcpyDeviceToDevice, st), "restore state");
         o += size_t(h->B) * STATE;
     }
-    CK(cudaStreamSynchronize(st), "sync");
+    rc = wait_event(g->ev, st);
+    if (rc) return rc;
     if (!best) return fail(AM_ERR_ARG, "no block size fits every problem of the group");
     if (threads_out) *threads_out = best;
     if (ms_out) *ms_out = best_ms;
@@ -771,3 +974,52 @@ int am_group_stats(am_group *g, int *launches, int *items)
 }
 
 }  // extern "C"
+
+namespace trajam {
+
+int problem_shape(const ::am_problem *h, int *q, int *m, int *n, int *B, double *T)
+{
+    *q = h->pp.q;
+    *m = h->pp.m;
+    *n = h->n;
+    *B = h->B;
+    *T = h->pp.T;
+    return h->solved ? 0 : -1;
+}
+
+void problem_boundary(const ::am_problem *h, double x[6], double y[6], double psi[6])
+{
+    std::memcpy(x, h->pp.x_bc, sizeof(h->pp.x_bc));
+    std::memcpy(y, h->pp.y_bc, sizeof(h->pp.y_bc));
+    std::memcpy(psi, h->pp.psi_bc, sizeof(h->pp.psi_bc));
+}
+
+int problem_update_tracks(::am_problem *h, const float *xo, const float *yo)
+{
+    const int n = h->n, q = h->pp.q;
+    if (n == 0) return AM_OK;
+    if (!h->d_raw) return fail(AM_ERR_STATE, "no obstacles set");
+    CK(cudaMemcpyAsync(h->d_raw, xo, sizeof(float) * n * q, cudaMemcpyHostToDevice, h->stream), "track copy");
+    CK(cudaMemcpyAsync(h->d_raw + n * q, yo, sizeof(float) * n * q, cudaMemcpyHostToDevice, h->stream),
+       "track copy");
+    if (launch_prep_obstacles(h->d_blob, h->L, h->d_raw, h->d_raw + n * q, h->d_raw + 2 * n * q,
+                              h->d_raw + 2 * n * q + n, float(h->pp.r_c), h->stream, nullptr))
+        return fail(AM_ERR_CUDA, "obstacle preparation launch failed");
+    return AM_OK;
+}
+
+size_t problem_device_bytes(const ::am_problem *h)
+{
+    return sizeof(float) * (h->blob_cap + h->raw_cap + h->state_cap + h->out_cap + h->best_cap +
+                            h->in_cap + h->hist_cap + h->scratch_cap) +
+           sizeof(int) * h->err_cap;
+}
+
+size_t scene_bytes(int q, int m, int n, int B)
+{
+    const ConstLayout L = make_layout(q, m, n);
+    const size_t floats = size_t(L.total) + size_t(2 * n * q + 2 * n) + size_t(B) * (STATE + 4 + 33 + 55) + 64;
+    return floats * sizeof(float) + sizeof(int);
+}
+
+}  // namespace trajam

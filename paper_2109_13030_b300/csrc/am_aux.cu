@@ -65,10 +65,11 @@ __device__ __forceinline__ bool better(const Key &a, const Key &b)
 // Lexicographic minimum over the batch of (collides, cost, index), where a
 // trajectory collides when its smallest ellipse distance is below 0.99; a
 // non-finite cost ranks last.  Writes {index, cost, residual, c_x, c_y, c_psi}.
-__global__ void argmin_kernel(const float *state, const float *cost, const float *res,
-                              const float *mind, int B, float *out)
+// Lexicographic best over B trajectories (collision-free first, then cost,
+// then index); the whole block takes part, out gets 36 floats.
+__device__ void select_best(const float *state, const float *cost, const float *res,
+                            const float *mind, int B, float *out, Key *sk)
 {
-    __shared__ Key sk[1024];
     Key best{2, FLT_MAX, 0x7fffffff};
     for (int l = threadIdx.x; l < B; l += blockDim.x) {
         float c = cost[l];
@@ -97,6 +98,20 @@ __global__ void argmin_kernel(const float *state, const float *cost, const float
     }
 }
 
+__global__ void argmin_kernel(const float *state, const float *cost, const float *res,
+                              const float *mind, int B, float *out)
+{
+    __shared__ Key sk[1024];
+    select_best(state, cost, res, mind, B, out, sk);
+}
+
+__global__ void group_argmin_kernel(const FusedProblem *probs, const int *list, float *out)
+{
+    __shared__ Key sk[1024];
+    const FusedProblem &p = probs[list[blockIdx.x]];
+    select_best(p.state, p.cost, p.res, p.mind, p.B, out + 36 * blockIdx.x, sk);
+}
+
 }  // namespace
 
 int launch_init_state(float *state, const float *init, const float *warm, int B, void *stream,
@@ -116,6 +131,15 @@ int launch_prep_obstacles(float *cblob, const ConstLayout &L, const float *xo, c
     if (n == 0) return 0;
     prep_obstacles_kernel<<<(n + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(
         cblob, L, xo, yo, a, b, r_c);
+    if (launches) ++*launches;
+    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
+int launch_group_argmin(const FusedProblem *d_probs, const int *d_list, int count, float *d_out,
+                        void *stream, int *launches)
+{
+    if (count < 1) return 0;
+    group_argmin_kernel<<<count, 1024, 0, static_cast<cudaStream_t>(stream)>>>(d_probs, d_list, d_out);
     if (launches) ++*launches;
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }

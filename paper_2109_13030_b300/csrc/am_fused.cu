@@ -775,13 +775,25 @@ __global__ void __launch_bounds__(kMaxThreads, 1) am_fused_kernel(KParams p)
         run_tile<M, LIT>(p, sm, S, tile_of(tile, p.B, p.ntiles));
 }
 
-// Uneven batching: one persistent launch over the tiles of many problems of
-// different batch size, horizon, obstacle and circle counts.  CTAs take work
-// items (problem, tile) from a list in order, through one atomic counter; the
-// constants are re-staged whenever a CTA moves to another problem.
+// Uneven batching: persistent launches over the tiles of many problems of
+// different batch size, horizon, obstacle and circle counts, one kernel per
+// variant (circle count M, alpha form LIT) so that each is compiled on its
+// own (the variants inlined into one kernel spill registers).  The variant
+// kernels of one solve run concurrently; CTAs take work items (problem,
+// tile) of their variant from a list in order, through one atomic counter
+// per variant, and re-stage constants whenever they move to another problem.
+// The lists, their lengths and offsets live in device memory, so a captured
+// launch stays valid when the set of problems it advances changes.
+//   head[v]: number of items of variant v; head[8 + v]: offset of its list
+//   ctl[2 v]: its work counter (zeroed before the launch); ctl[2 v + 1]: status
+template <int M, bool LIT>
 __global__ void __launch_bounds__(kMaxThreads, 1)
-am_group_kernel(const KParams *probs, const int *items, int nitems, int *counter)
+am_group_kernel(const KParams *probs, const int *items, const int *head, int *ctl)
 {
+    constexpr int v = M * 2 + (LIT ? 1 : 0) - 2;
+    int *counter = ctl + 2 * v;
+    const int nitems = head[v];
+    const int *list = items + 2 * head[8 + v];
     extern __shared__ __align__(128) float sm[];
     __shared__ KParams kp;
     __shared__ int s_item;
@@ -794,29 +806,21 @@ am_group_kernel(const KParams *probs, const int *items, int nitems, int *counter
         __syncthreads();
         const int it = s_item;
         if (it >= nitems) break;
-        const int2 item = make_int2(items[2 * it], items[2 * it + 1]);
+        const int2 item = make_int2(list[2 * it], list[2 * it + 1]);
         if (item.x != cur) {
             if (threadIdx.x == 0) kp = probs[item.x];
             __syncthreads();
             if (!stage_constants(kp, sm, smem_layout(kp.L, kp.T), bar, parity)) {
-                if (threadIdx.x == 0) atomicExch(kp.err, 1);
+                if (threadIdx.x == 0) {
+                    atomicExch(kp.err, 1);
+                    atomicExch(ctl + 2 * v + 1, 1);
+                }
                 return;
             }
             parity ^= 1u;
             cur = item.x;
         }
-        const Smem S = smem_layout(kp.L, kp.T);
-        const Tile tl = tile_of(item.y, kp.B, kp.ntiles);
-        switch (kp.L.m * 2 + (kp.L.alpha_mode ? 1 : 0)) {
-        case 2: run_tile<1, false>(kp, sm, S, tl); break;
-        case 3: run_tile<1, true>(kp, sm, S, tl); break;
-        case 4: run_tile<2, false>(kp, sm, S, tl); break;
-        case 5: run_tile<2, true>(kp, sm, S, tl); break;
-        case 6: run_tile<3, false>(kp, sm, S, tl); break;
-        case 7: run_tile<3, true>(kp, sm, S, tl); break;
-        case 8: run_tile<4, false>(kp, sm, S, tl); break;
-        default: run_tile<4, true>(kp, sm, S, tl); break;
-        }
+        run_tile<M, LIT>(kp, sm, smem_layout(kp.L, kp.T), tile_of(item.y, kp.B, kp.ntiles));
         __syncthreads();
     }
 }
@@ -850,18 +854,52 @@ int group_tile(const ConstLayout &L, int threads)
     return t < 1 ? 0 : t;
 }
 
-int launch_group(const GroupLaunch &g, void *stream, int *launches)
+int launch_group(const GroupLaunch &g, void *stream, int *launches, const char **why)
 {
-    if (g.threads < 32 || g.threads > kMaxThreads || g.smem > kGroupSmemMax || g.nitems < 1) return -1;
-    if (cudaFuncSetAttribute(am_group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             int(g.smem)) != cudaSuccess)
-        return -2;
+    *why = nullptr;
+    if (g.threads < 32 || g.threads > kMaxThreads || g.smem > kGroupSmemMax || g.grid < 1 ||
+        g.variant < 0 || g.variant >= kGroupVariants)
+        return -1;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (cudaMemsetAsync(g.d_counter, 0, sizeof(int), st) != cudaSuccess) return -2;
-    am_group_kernel<<<g.grid, g.threads, g.smem, st>>>(g.d_probs, g.d_items, g.nitems, g.d_counter);
+    cudaError_t e = cudaMemsetAsync(g.d_ctl + 2 * g.variant, 0, sizeof(int), st);
+    if (e != cudaSuccess) {
+        *why = cudaGetErrorString(e);
+        return -2;
+    }
+    switch (g.variant) {
+#define AM_GCASE(MM, LL)                                                                        \
+    case MM * 2 + LL - 2:                                                                       \
+        e = cudaFuncSetAttribute(am_group_kernel<MM, LL>,                                       \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, int(g.smem));     \
+        if (e != cudaSuccess) {                                                                 \
+            *why = cudaGetErrorString(e);                                                       \
+            return -2;                                                                          \
+        }                                                                                       \
+        am_group_kernel<MM, LL><<<g.grid, g.threads, g.smem, st>>>(g.d_probs, g.d_items, g.d_head, \
+                                                                   g.d_ctl);                   \
+        break;
+        AM_GCASE(1, 0)
+        AM_GCASE(1, 1)
+        AM_GCASE(2, 0)
+        AM_GCASE(2, 1)
+        AM_GCASE(3, 0)
+        AM_GCASE(3, 1)
+        AM_GCASE(4, 0)
+        AM_GCASE(4, 1)
+#undef AM_GCASE
+    default:
+        return -1;
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        *why = cudaGetErrorString(e);
+        return -2;
+    }
     if (launches) ++*launches;
-    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+    return 0;
 }
+
+int group_variant(const ConstLayout &L) { return L.m * 2 + (L.alpha_mode ? 1 : 0) - 2; }
 
 int fused_auto_tile(const ConstLayout &L, int B, int num_sms)
 {

@@ -117,21 +117,32 @@ struct FusedProblem {
     int *err;
 };
 
-// Grouped launch: many problems' tiles in one persistent kernel.
+// Grouped launch: many problems' tiles in persistent kernels, one kernel per
+// variant (circle count, alpha form) present; the variant kernels of one
+// solve run concurrently.
+constexpr int kGroupVariants = 8;
 struct GroupLaunch {
     const FusedProblem *d_probs;  // device array, one per problem
-    const int *d_items;           // device array of (problem, tile) pairs
-    int nitems;
-    int *d_counter;               // work counter, reset before each launch
+    const int *d_items;           // device array of (problem, tile) pairs, all variants
+    const int *d_head;            // device: item count per variant [8], list offset per variant [8]
+    int *d_ctl;                   // device {work counter, status} per variant; the
+                                  // variant's counter is zeroed by launch_group
+    int variant;                  // m * 2 + alpha_mode - 2
     int threads;
     size_t smem;
     int grid;
 };
+int group_variant(const ConstLayout &L);
 // Tile size (trajectories per CTA) of a problem in a grouped launch of the
 // given block size; 0 when the problem does not fit.
 int group_tile(const ConstLayout &L, int threads);
 int fused_max_threads();
-int launch_group(const GroupLaunch &g, void *stream, int *launches);
+// Returns 0, -1 (configuration out of range) or -2 (CUDA error, *why says which).
+int launch_group(const GroupLaunch &g, void *stream, int *launches, const char **why);
+// Best-trajectory selection for several problems in one launch: one block per
+// listed problem; writes 36 floats per entry ({index, cost, res, 33 coefficients}).
+int launch_group_argmin(const FusedProblem *d_probs, const int *d_list, int count, float *d_out,
+                        void *stream, int *launches);
 // Unfused comparator: one launch per step, intermediates in global memory.
 int launch_plain(const SolveArgs &a, float *scratch, size_t scratch_floats, void *stream,
                  int *launches);
@@ -149,6 +160,15 @@ int launch_init_state(float *state, const float *init, const float *warm, int B,
 // Handle accessors for entry points outside the C-ABI file.
 int handle_constants(const ::am_problem *h, const float **cblob, ConstLayout *L);
 int report_error(int code, const char *msg);
+// Scene accessors for the server.  problem_shape returns -1 when the handle
+// has no state yet.
+int problem_shape(const ::am_problem *h, int *q, int *m, int *n, int *B, double *T);
+void problem_boundary(const ::am_problem *h, double x[6], double y[6], double psi[6]);
+// New obstacle centre tracks (host, n x q each), semi-axes unchanged.
+int problem_update_tracks(::am_problem *h, const float *xo, const float *yo);
+size_t problem_device_bytes(const ::am_problem *h);
+// Device bytes a handle holds for a batch of B (no history, fused kernel).
+size_t scene_bytes(int q, int m, int n, int B);
 // Fused kernel tile selection, exposed for the autotuner.
 int fused_auto_tile(const ConstLayout &L, int B, int num_sms);
 size_t fused_smem_bytes(const ConstLayout &L, int tile);

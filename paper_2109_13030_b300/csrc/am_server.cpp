@@ -1,0 +1,365 @@
+// Re-planning server (include/trajam.h, "serving"): resident warm-started
+// scenes, HBM-budget admission, a worker thread that serves requests in
+// rounds of continuous batching through one grouped launch per round.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <unordered_set>
+#include <vector>
+
+#include "am_internal.h"
+#include "../../include/trajam.h"
+
+using namespace trajam;
+
+namespace {
+
+double now_s()
+{
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+struct Request {
+    long long ticket;
+    am_request r;
+    std::vector<float> xo, yo;
+    double t_submit;
+};
+
+struct Scene {
+    am_problem *h;
+    int q, m, n, B;
+    double T;
+    size_t bytes;
+    bool has_best = false;
+    float best[33];
+};
+
+double binom(int n, int k)
+{
+    double c = 1;
+    for (int i = 1; i <= k; ++i) c = c * (n - k + i) / i;
+    return c;
+}
+
+// Value, first and second time derivative at t of a degree-10 Bernstein
+// polynomial with control points c on [0, T] (derivatives through the
+// differences of the control points).
+void bernstein_eval(const float *c, double T, double t, double out[3])
+{
+    const int n = 10;
+    double tau = t / T;
+    tau = tau < 0 ? 0 : tau > 1 ? 1 : tau;
+    auto basis = [&](int k, int deg) { return binom(deg, k) * std::pow(tau, k) * std::pow(1 - tau, deg - k); };
+    double v = 0, d = 0, dd = 0;
+    for (int k = 0; k <= n; ++k) v += double(c[k]) * basis(k, n);
+    for (int k = 0; k < n; ++k) d += (double(c[k + 1]) - c[k]) * basis(k, n - 1);
+    for (int k = 0; k < n - 1; ++k) dd += (double(c[k + 2]) - 2.0 * c[k + 1] + c[k]) * basis(k, n - 2);
+    out[0] = v;
+    out[1] = d * n / T;
+    out[2] = dd * n * (n - 1) / (T * T);
+}
+
+}  // namespace
+
+struct am_server {
+    am_server_desc d;
+    int device = 0;
+    cudaStream_t st = nullptr;
+    std::vector<Scene> scenes;
+    size_t used = 0;
+    am_group *g = nullptr;
+    float *h_bests = nullptr;  // pinned, 36 floats per scene
+    std::thread worker;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Request> pending;
+    std::unordered_map<long long, am_result> done;
+    std::unordered_set<long long> outstanding;
+    long long next_ticket = 1, rounds = 0, completed = 0;
+    bool stop = false, started = false;
+};
+
+namespace {
+
+// Start state from the scene's last best plan at t = advance.
+int advance_start(Scene &sc, double advance)
+{
+    double x[6], y[6], psi[6], v[3];
+    problem_boundary(sc.h, x, y, psi);
+    bernstein_eval(sc.best, sc.T, advance, v);
+    std::memcpy(x, v, sizeof(v));
+    bernstein_eval(sc.best + 11, sc.T, advance, v);
+    std::memcpy(y, v, sizeof(v));
+    bernstein_eval(sc.best + 22, sc.T, advance, v);
+    std::memcpy(psi, v, sizeof(v));
+    return am_set_boundary(sc.h, x, y, psi);
+}
+
+// One round: updates, solve, best selection.  Fills best records (36 floats
+// per request, in batch order) or returns an error code.
+int serve_round(am_server *s, std::vector<Request> &batch)
+{
+    int rc = AM_OK;
+    for (auto &q : batch) {
+        Scene &sc = s->scenes[q.r.scene];
+        rc = am_set_stream(sc.h, s->st);
+        if (!rc && !q.xo.empty()) rc = problem_update_tracks(sc.h, q.xo.data(), q.yo.data());
+        if (!rc && q.r.advance > 0 && sc.has_best) rc = advance_start(sc, q.r.advance);
+        if (rc) return rc;
+    }
+    // A round of several requests goes through one grouped launch; a round of
+    // one takes the single-problem kernel, whose tile and block size are
+    // chosen for that problem alone (the per-tile code is the same).
+    if (s->d.mode == AM_SRV_BATCHED && batch.size() > 1) {
+        std::vector<int> act;
+        for (auto &q : batch) act.push_back(q.r.scene);
+        rc = am_group_set_active(s->g, act.data(), int(act.size()));
+        if (!rc) rc = am_group_solve(s->g, s->d.iters, s->st);
+        if (!rc) rc = am_group_get_best(s->g, s->h_bests, AM_HOST, s->st);
+        return rc;
+    }
+    for (size_t k = 0; k < batch.size() && !rc; ++k) {
+        Scene &sc = s->scenes[batch[k].r.scene];
+        float *o = s->h_bests + 36 * k;
+        int idx = 0;
+        rc = am_solve_batch(sc.h, sc.B, nullptr, nullptr, s->d.iters, s->st, AM_DEVICE);
+        if (!rc) rc = am_get_best(sc.h, o + 3, &o[1], &o[2], &idx);
+        o[0] = float(idx);
+    }
+    return rc;
+}
+
+void worker_main(am_server *s)
+{
+    cudaSetDevice(s->device);
+    const size_t nsc = s->scenes.size();
+    std::vector<Request> batch;
+    std::vector<char> taken(nsc);
+    for (;;) {
+        batch.clear();
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->cv_work.wait(lk, [&] { return s->stop || !s->pending.empty(); });
+            if (s->stop) break;
+            size_t limit = s->d.mode == AM_SRV_SEQUENTIAL ? 1 : nsc;
+            if (s->d.max_batch > 0 && size_t(s->d.max_batch) < limit) limit = size_t(s->d.max_batch);
+            std::fill(taken.begin(), taken.end(), 0);
+            for (auto it = s->pending.begin(); it != s->pending.end() && batch.size() < limit;) {
+                if (!taken[it->r.scene]) {
+                    taken[it->r.scene] = 1;
+                    batch.push_back(std::move(*it));
+                    it = s->pending.erase(it);
+                } else {
+                    ++it;
+                }
+            }
+        }
+        const double t_start = now_s();
+        const int rc = serve_round(s, batch);
+        const double t_done = now_s();
+        std::lock_guard<std::mutex> lk(s->mu);
+        for (size_t k = 0; k < batch.size(); ++k) {
+            Request &q = batch[k];
+            am_result r;
+            std::memset(&r, 0, sizeof(r));
+            r.status = rc;
+            r.t_submit = q.t_submit;
+            r.t_start = t_start;
+            r.t_done = t_done;
+            r.round = s->rounds;
+            r.batch = int(batch.size());
+            if (!rc) {
+                const float *o = s->h_bests + 36 * k;
+                r.index = int(o[0]);
+                r.cost = o[1];
+                r.residual = o[2];
+                std::memcpy(r.coeffs, o + 3, sizeof(r.coeffs));
+                Scene &sc = s->scenes[q.r.scene];
+                std::memcpy(sc.best, r.coeffs, sizeof(sc.best));
+                sc.has_best = true;
+            }
+            s->done[q.ticket] = r;
+            ++s->completed;
+        }
+        ++s->rounds;
+        s->cv_done.notify_all();
+    }
+    // Stopped: what is still queued completes with AM_ERR_STATE.
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (auto &q : s->pending) {
+        am_result r;
+        std::memset(&r, 0, sizeof(r));
+        r.status = AM_ERR_STATE;
+        r.t_submit = q.t_submit;
+        s->done[q.ticket] = r;
+    }
+    s->pending.clear();
+    s->cv_done.notify_all();
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t am_scene_bytes(int q, int m, int n, int B)
+{
+    if (q < 2 || q > AM_MAX_Q || m < 1 || m > AM_MAX_M || n < 0 || n > AM_MAX_N || B < 1) return 0;
+    return scene_bytes(q, m, n, B);
+}
+
+int am_server_create(const am_server_desc *d, am_server **out)
+{
+    if (!d || !out) return report_error(AM_ERR_ARG, "null argument");
+    *out = nullptr;
+    if (d->iters < 1 || d->iters > 100000) return report_error(AM_ERR_ARG, "iters must be in [1, 100000]");
+    if (d->mode != AM_SRV_BATCHED && d->mode != AM_SRV_SEQUENTIAL) return report_error(AM_ERR_ARG, "bad mode");
+    if (d->max_batch < 0 || d->max_pending < 0) return report_error(AM_ERR_ARG, "negative limit");
+    am_server *s = new (std::nothrow) am_server;
+    if (!s) return report_error(AM_ERR_ARG, "out of host memory");
+    s->d = *d;
+    if (s->d.max_pending == 0) s->d.max_pending = 65536;
+    cudaGetDevice(&s->device);
+    if (cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking) != cudaSuccess) {
+        delete s;
+        return report_error(AM_ERR_CUDA, "stream creation failed");
+    }
+    *out = s;
+    return AM_OK;
+}
+
+int am_server_add_scene(am_server *s, am_problem *h, int B, const float *init, int mem, int *scene)
+{
+    if (!s || !h || !init || !scene) return report_error(AM_ERR_ARG, "null argument");
+    if (s->started) return report_error(AM_ERR_STATE, "scenes are added before am_server_start");
+    Scene sc;
+    sc.h = h;
+    int b0;
+    problem_shape(h, &sc.q, &sc.m, &sc.n, &b0, &sc.T);
+    if (B < 1 || B > (1 << 24)) return report_error(AM_ERR_ARG, "B must be in [1, 2^24]");
+    for (const Scene &o : s->scenes)
+        if (o.h == h) return report_error(AM_ERR_ARG, "handle already added");
+    sc.B = B;
+    sc.bytes = scene_bytes(sc.q, sc.m, sc.n, B);
+    if (s->used + sc.bytes > s->d.budget_bytes) {
+        char msg[160];
+        snprintf(msg, sizeof(msg), "scene needs %zu bytes, %zu of the %zu-byte budget are in use", sc.bytes,
+                 s->used, s->d.budget_bytes);
+        return report_error(AM_ERR_BUDGET, msg);
+    }
+    int rc = am_init_state(h, B, init, nullptr, s->st, mem);
+    if (rc) return rc;
+    s->used += sc.bytes;
+    s->scenes.push_back(sc);
+    *scene = int(s->scenes.size()) - 1;
+    return AM_OK;
+}
+
+int am_server_start(am_server *s)
+{
+    if (!s) return report_error(AM_ERR_ARG, "null server");
+    if (s->started) return report_error(AM_ERR_STATE, "already started");
+    if (s->scenes.empty()) return report_error(AM_ERR_STATE, "no scenes");
+    if (cudaMallocHost(&s->h_bests, sizeof(float) * 36 * s->scenes.size()) != cudaSuccess)
+        return report_error(AM_ERR_CUDA, "pinned allocation failed");
+    if (s->d.mode == AM_SRV_BATCHED) {
+        std::vector<am_problem *> hs;
+        for (auto &sc : s->scenes) hs.push_back(sc.h);
+        int rc = am_group_create(hs.data(), int(hs.size()), &s->g);
+        if (rc) return rc;
+        int threads = 0;
+        float ms = 0;
+        rc = am_group_autotune(s->g, s->d.iters, s->st, &threads, &ms);
+        if (rc) return rc;
+    }
+    s->started = true;
+    s->worker = std::thread(worker_main, s);
+    return AM_OK;
+}
+
+int am_server_submit(am_server *s, const am_request *req, long long *ticket)
+{
+    if (!s || !req || !ticket) return report_error(AM_ERR_ARG, "null argument");
+    if (req->scene < 0 || req->scene >= int(s->scenes.size())) return report_error(AM_ERR_ARG, "unknown scene");
+    if (!(req->advance >= 0) || !std::isfinite(req->advance)) return report_error(AM_ERR_ARG, "bad advance");
+    if ((req->xo == nullptr) != (req->yo == nullptr)) return report_error(AM_ERR_ARG, "xo and yo go together");
+    const Scene &sc = s->scenes[req->scene];
+    Request q;
+    q.r = *req;
+    if (req->xo) {
+        q.xo.assign(req->xo, req->xo + size_t(sc.n) * sc.q);
+        q.yo.assign(req->yo, req->yo + size_t(sc.n) * sc.q);
+    }
+    q.r.xo = q.r.yo = nullptr;
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stop) return report_error(AM_ERR_STATE, "server stopping");
+    if (int(s->pending.size()) >= s->d.max_pending) return report_error(AM_ERR_BUDGET, "request queue full");
+    q.t_submit = now_s();
+    q.ticket = s->next_ticket++;
+    *ticket = q.ticket;
+    s->outstanding.insert(q.ticket);
+    s->pending.push_back(std::move(q));
+    s->cv_work.notify_one();
+    return AM_OK;
+}
+
+int am_server_poll(am_server *s, long long ticket, am_result *out, int timeout_ms)
+{
+    if (!s || !out) return report_error(AM_ERR_ARG, "null argument");
+    std::unique_lock<std::mutex> lk(s->mu);
+    if (!s->outstanding.count(ticket)) return report_error(AM_ERR_ARG, "unknown ticket");
+    const auto until = std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms);
+    while (!s->done.count(ticket))
+        if (s->cv_done.wait_until(lk, until) == std::cv_status::timeout && !s->done.count(ticket))
+            return AM_PENDING;
+    *out = s->done[ticket];
+    s->done.erase(ticket);
+    s->outstanding.erase(ticket);
+    return AM_OK;
+}
+
+int am_server_stats(am_server *s, long long *rounds, long long *completed, size_t *device_bytes)
+{
+    if (!s) return report_error(AM_ERR_ARG, "null server");
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (rounds) *rounds = s->rounds;
+    if (completed) *completed = s->completed;
+    if (device_bytes) *device_bytes = s->used;
+    return AM_OK;
+}
+
+void am_server_destroy(am_server *s)
+{
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+    // Let the server's stream drain (bounded), then hand the scenes back to
+    // the default stream: their handles must not keep the stream destroyed
+    // below.
+    if (s->st) {
+        const auto t0 = std::chrono::steady_clock::now();
+        while (cudaStreamQuery(s->st) == cudaErrorNotReady &&
+               std::chrono::steady_clock::now() - t0 < std::chrono::seconds(60))
+            std::this_thread::yield();
+    }
+    for (Scene &sc : s->scenes) am_set_stream(sc.h, nullptr);
+    if (s->g) am_group_destroy(s->g);
+    if (s->h_bests) cudaFreeHost(s->h_bests);
+    if (s->st) cudaStreamDestroy(s->st);
+    delete s;
+}
+
+}  // extern "C"

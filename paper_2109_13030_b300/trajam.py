@@ -21,14 +21,18 @@ AM_FP32, AM_TF32, AM_BF16 = 0, 1, 2
 AM_KERNEL_FUSED, AM_KERNEL_PLAIN = 0, 1
 AM_OPT_KERNEL, AM_OPT_TILE = 1, 2
 AM_GOPT_THREADS, AM_GOPT_GRAPH = 1, 2
+AM_PENDING = 1
+AM_SRV_BATCHED, AM_SRV_SEQUENTIAL = 0, 1
 AM_NV, AM_STATE_FLOATS = 11, 110
 
 EXPORTS = ["am_init_problem", "am_set_obstacles", "am_set_boundary", "am_solve_batch",
            "am_get_results", "am_get_best", "am_get_state", "am_set_state", "am_set_history",
            "am_get_history", "am_set_option", "am_set_stream", "am_last_solve_stats",
            "am_solve_batch_noalloc", "am_init_state", "am_group_create", "am_group_solve",
-           "am_group_autotune", "am_group_set_option", "am_group_stats", "am_group_destroy",
-           "am_destroy", "am_last_error"]
+           "am_group_autotune", "am_group_set_option", "am_group_set_active", "am_group_get_best",
+           "am_group_stats", "am_group_destroy", "am_server_create", "am_server_add_scene",
+           "am_server_start", "am_server_submit", "am_server_poll", "am_server_stats",
+           "am_server_destroy", "am_scene_bytes", "am_destroy", "am_last_error"]
 
 
 class AmProblemDesc(C.Structure):
@@ -38,6 +42,23 @@ class AmProblemDesc(C.Structure):
                 ("rho_psi", C.c_double), ("x_bc", C.c_double * 6), ("y_bc", C.c_double * 6),
                 ("psi_bc", C.c_double * 6), ("precision", C.c_int), ("alpha_mode", C.c_int),
                 ("psi_dual_sign", C.c_int), ("cs_boundary", C.c_int)]
+
+
+class AmServerDesc(C.Structure):
+    _fields_ = [("budget_bytes", C.c_size_t), ("iters", C.c_int), ("mode", C.c_int),
+                ("max_batch", C.c_int), ("max_pending", C.c_int)]
+
+
+class AmRequest(C.Structure):
+    _fields_ = [("scene", C.c_int), ("advance", C.c_double),
+                ("xo", C.c_void_p), ("yo", C.c_void_p)]
+
+
+class AmResult(C.Structure):
+    _fields_ = [("status", C.c_int), ("index", C.c_int), ("cost", C.c_float),
+                ("residual", C.c_float), ("coeffs", C.c_float * 33), ("t_submit", C.c_double),
+                ("t_start", C.c_double), ("t_done", C.c_double), ("round", C.c_longlong),
+                ("batch", C.c_int)]
 
 
 class TrajamError(RuntimeError):
@@ -72,6 +93,17 @@ def _load():
         "am_group_autotune": ([vp, ip, vp, C.POINTER(C.c_int), C.POINTER(C.c_float)], ip),
         "am_group_set_option": ([vp, ip, ip], ip),
         "am_group_stats": ([vp, C.POINTER(C.c_int), C.POINTER(C.c_int)], ip),
+        "am_group_set_active": ([vp, C.POINTER(C.c_int), ip], ip),
+        "am_group_get_best": ([vp, fp, ip, vp], ip),
+        "am_server_create": ([C.POINTER(AmServerDesc), C.POINTER(vp)], ip),
+        "am_server_add_scene": ([vp, vp, ip, fp, ip, C.POINTER(C.c_int)], ip),
+        "am_server_start": ([vp], ip),
+        "am_server_submit": ([vp, C.POINTER(AmRequest), C.POINTER(C.c_longlong)], ip),
+        "am_server_poll": ([vp, C.c_longlong, C.POINTER(AmResult), ip], ip),
+        "am_server_stats": ([vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
+                             C.POINTER(C.c_size_t)], ip),
+        "am_server_destroy": ([vp], None),
+        "am_scene_bytes": ([ip, ip, ip, ip], C.c_size_t),
         "am_group_destroy": ([vp], None),
         "am_destroy": ([vp], None),
         "am_last_error": ([], C.c_char_p),
@@ -254,8 +286,76 @@ def am_group_stats(g):
     return n.value, k.value
 
 
+def am_group_set_active(g, idx):
+    arr = (C.c_int * max(1, len(idx)))(*[int(i) for i in idx])
+    _check(_lib.am_group_set_active(g, arr if len(idx) else None, len(idx)))
+
+
+def am_group_get_best(g, count, stream=None):
+    out = np.zeros((count, 36), dtype=np.float32)
+    _check(_lib.am_group_get_best(g, out.ctypes.data, AM_HOST, _stream_ptr(stream)))
+    return out
+
+
 def am_group_destroy(g):
     _lib.am_group_destroy(g)
+
+
+def am_server_create(budget_bytes, iters, mode=AM_SRV_BATCHED, max_batch=0, max_pending=0) -> int:
+    d = AmServerDesc(int(budget_bytes), int(iters), int(mode), int(max_batch), int(max_pending))
+    s = C.c_void_p()
+    _check(_lib.am_server_create(C.byref(d), C.byref(s)))
+    return s.value
+
+
+def am_server_add_scene(s, h, B, init) -> int:
+    p, mem, k = _buf(init)
+    sc = C.c_int()
+    _check(_lib.am_server_add_scene(s, h, int(B), p, mem, C.byref(sc)))
+    return sc.value
+
+
+def am_server_start(s):
+    _check(_lib.am_server_start(s))
+
+
+def am_server_submit(s, scene, advance=0.0, xo=None, yo=None) -> int:
+    keep = []
+    r = AmRequest(int(scene), float(advance), None, None)
+    if xo is not None:
+        ax = np.ascontiguousarray(xo, dtype=np.float32)
+        ay = np.ascontiguousarray(yo, dtype=np.float32)
+        keep += [ax, ay]
+        r.xo, r.yo = ax.ctypes.data, ay.ctypes.data
+    t = C.c_longlong()
+    _check(_lib.am_server_submit(s, C.byref(r), C.byref(t)))
+    return t.value
+
+
+def am_server_poll(s, ticket, timeout_ms=0):
+    """dict of the result, or None while the request is pending."""
+    r = AmResult()
+    rc = _lib.am_server_poll(s, C.c_longlong(ticket), C.byref(r), int(timeout_ms))
+    if rc == AM_PENDING:
+        return None
+    _check(rc)
+    return dict(status=r.status, index=r.index, cost=r.cost, residual=r.residual,
+                coeffs=np.array(r.coeffs, dtype=np.float32).reshape(3, 11), t_submit=r.t_submit,
+                t_start=r.t_start, t_done=r.t_done, round=r.round, batch=r.batch)
+
+
+def am_server_stats(s):
+    r, c, b = C.c_longlong(), C.c_longlong(), C.c_size_t()
+    _check(_lib.am_server_stats(s, C.byref(r), C.byref(c), C.byref(b)))
+    return dict(rounds=r.value, completed=c.value, device_bytes=b.value)
+
+
+def am_server_destroy(s):
+    _lib.am_server_destroy(s)
+
+
+def am_scene_bytes(q, m, n, B) -> int:
+    return int(_lib.am_scene_bytes(int(q), int(m), int(n), int(B)))
 
 
 def am_destroy(h):
@@ -353,6 +453,50 @@ class Group:
         if self.g:
             am_group_destroy(self.g)
             self.g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Re-planning server over resident scenes (Problems), see am_server_*."""
+
+    def __init__(self, budget_bytes, iters, mode=AM_SRV_BATCHED, max_batch=0, max_pending=0):
+        self.s = am_server_create(budget_bytes, iters, mode, max_batch, max_pending)
+        self.scenes = []   # keeps the Problems alive while the server uses them
+
+    def add_scene(self, problem, init):
+        k = am_server_add_scene(self.s, problem.h, int(init.shape[0]), init)
+        problem.B = int(init.shape[0])
+        self.scenes.append(problem)
+        return k
+
+    def start(self):
+        am_server_start(self.s)
+        return self
+
+    def submit(self, scene, advance=0.0, xo=None, yo=None):
+        return am_server_submit(self.s, scene, advance, xo, yo)
+
+    def poll(self, ticket, timeout_ms=0):
+        return am_server_poll(self.s, ticket, timeout_ms)
+
+    def wait(self, ticket, timeout_s=60.0):
+        res = am_server_poll(self.s, ticket, int(timeout_s * 1000))
+        if res is None:
+            raise TimeoutError(f"request {ticket} not finished within {timeout_s} s")
+        return res
+
+    def stats(self):
+        return am_server_stats(self.s)
+
+    def close(self):
+        if self.s:
+            am_server_destroy(self.s)
+            self.s = None
 
     def __del__(self):
         try:

@@ -61,3 +61,37 @@ def test_null_and_bad_arguments_rejected_without_device(lib_path):
         h = ctypes.c_void_p()
         assert lib.am_init_problem(ctypes.byref(d), ctypes.byref(h)) == -1, field
         assert h.value is None
+
+
+def test_group_and_server_argument_checks_without_device(lib_path):
+    from paper_2109_13030_b300 import trajam as T
+    L = T._lib
+    g = ctypes.c_void_p()
+    assert L.am_group_create(None, 1, ctypes.byref(g)) == T.AM_ERR_ARG
+    assert L.am_group_solve(None, 10, None) == T.AM_ERR_ARG
+    assert L.am_group_set_active(None, None, 0) == T.AM_ERR_ARG
+    assert L.am_group_get_best(None, None, 0, None) == T.AM_ERR_ARG
+    assert L.am_init_state(None, 1, None, None, None, 0) == T.AM_ERR_ARG
+    s = ctypes.c_void_p()
+    for kw in (dict(iters=0), dict(mode=7), dict(max_batch=-1)):
+        d = T.AmServerDesc(1 << 30, kw.get("iters", 30), kw.get("mode", 0), kw.get("max_batch", 0), 0)
+        assert L.am_server_create(ctypes.byref(d), ctypes.byref(s)) == T.AM_ERR_ARG, kw
+        assert s.value is None
+    assert L.am_server_submit(None, None, None) == T.AM_ERR_ARG
+    assert L.am_server_poll(None, 1, None, 0) == T.AM_ERR_ARG
+
+
+def test_scene_bytes_accounting(lib_path):
+    """Admission arithmetic: the constant block, the obstacle tracks and the
+    per-trajectory buffers (state 110, results 4, staging 33 + 55 floats)."""
+    from paper_2109_13030_b300 import trajam as T
+    assert T.am_scene_bytes(1, 3, 10, 1000) == 0
+    assert T.am_scene_bytes(100, 5, 10, 1000) == 0
+    assert T.am_scene_bytes(100, 3, 10, 0) == 0
+    a = T.am_scene_bytes(100, 3, 10, 1000)
+    b = T.am_scene_bytes(100, 3, 10, 2000)
+    assert b - a == 1000 * (110 + 4 + 33 + 55) * 4
+    c = T.am_scene_bytes(100, 3, 11, 1000)
+    assert c - a >= (2 * 100 + 2) * 4   # one more obstacle track
+    # 64 scenes of the largest mixed shape fit an 8 GB budget many times over
+    assert 64 * T.am_scene_bytes(150, 4, 32, 2048) < 8 << 30

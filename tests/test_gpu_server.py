@@ -1,0 +1,202 @@
+"""Serving on the GPU: resident scenes, rounds of continuous batching.
+
+A request served in a round together with other scenes' requests must give
+the result it gives alone: every scene is advanced by the same per-tile code
+whatever else shares the launch.  Shared-memory sums are accumulated in a
+hardware-chosen order, so "the same" means within FP32 rounding (2e-4
+relative on coefficients, as between two solves of one problem).
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2109_13030_b300 import workload as W
+
+from test_gpu_parity import COEF_TOL, coef_err
+from test_gpu_group import coef_tolerance
+
+pytestmark = pytest.mark.gpu
+
+GB = 1 << 30
+
+
+def tj():
+    from paper_2109_13030_b300 import trajam
+    return trajam
+
+
+def scenes(count=4, seed=21, scale=1.0 / 64):
+    return W.make_uneven(seed, count=count, scale=scale)
+
+
+def make_server(pbs, iters, mode=0, budget=8 * GB, start=True, **kw):
+    T = tj()
+    S = T.Server(budget, iters, mode=mode, **kw)
+    probs = []
+    for pb in pbs:
+        P = T.Problem(pb)
+        S.add_scene(P, pb["init"].astype(np.float32))
+        probs.append(P)
+    return (S.start() if start else S), probs
+
+
+def close(S, probs):
+    S.close()
+    for P in probs:
+        P.close()
+
+
+def assert_same(a, b, tol=2 * COEF_TOL):
+    ca, cb = np.asarray(a["coeffs"], np.float64), np.asarray(b["coeffs"], np.float64)
+    err = np.max(np.abs(ca - cb)) / max(1.0, np.max(np.abs(cb)))
+    assert err <= tol, err
+    assert a["cost"] == pytest.approx(b["cost"], rel=1e-3)
+
+
+def test_result_alone_equals_result_in_mix():
+    pbs = scenes()
+    S, probs = make_server(pbs, 10)
+    alone = S.wait(S.submit(0))
+    close(S, probs)
+    assert alone["status"] == 0 and alone["batch"] == 1
+
+    S, probs = make_server(pbs, 10, start=False)
+    # queued before the start: the first round serves all four together
+    tickets = [S.submit(k) for k in range(len(pbs))]
+    S.start()
+    mixed = [S.wait(t) for t in tickets]
+    stats = S.stats()
+    close(S, probs)
+    assert all(r["status"] == 0 for r in mixed)
+    assert stats["completed"] == len(pbs)
+    assert all(r["batch"] == len(pbs) for r in mixed)
+    assert_same(mixed[0], alone)
+
+
+def test_batched_round_holds_many_scenes_and_matches_oracle():
+    """One round advances six scenes of different shapes; a second request for
+    a scene already in the round waits for the next round."""
+    pbs = scenes(count=6, seed=23)
+    S, probs = make_server(pbs, 10, start=False)
+    tickets = [S.submit(k) for k in range(len(pbs))]
+    extra = S.submit(2)
+    S.start()
+    results = [S.wait(t) for t in tickets]
+    again = S.wait(extra)
+    S.close()
+    states = [T_state(P) for P in probs]
+    close(S, probs)
+    assert all(r["batch"] == 6 and r["round"] == 0 for r in results)
+    assert again["round"] == 1 and again["batch"] == 1
+    for k, (pb, P, r) in enumerate(zip(pbs, probs, results)):
+        if k == 2:
+            continue   # advanced twice
+        st = states[k]
+        o, tol = coef_tolerance(pb, 10)
+        for key in ("xi1", "xi2"):
+            assert coef_err(st[key], o[key]).max() <= tol, key
+        i = r["index"]
+        assert np.allclose(r["coeffs"][0], st["xi1"][i, 0:11], atol=1e-6)
+
+
+def T_state(P):
+    T = tj()
+    return T.split_state(P.state())
+
+
+def test_warm_start_continues_the_iteration():
+    """Two requests on one scene (no updates) equal one 20-iteration solve: the
+    state (xi, lambda) stays resident between requests."""
+    T = tj()
+    pb = scenes(count=1, seed=25)[0]
+    S, probs = make_server([pb], 10)
+    S.wait(S.submit(0))
+    S.wait(S.submit(0))
+    S.close()
+    st = T.split_state(probs[0].state())
+    close(S, probs)
+    o, tol = coef_tolerance(pb, 20)
+    for key in ("xi1", "xi2"):
+        assert coef_err(st[key], o[key]).max() <= tol, key
+
+
+def test_sequential_mode_matches_batched():
+    pbs = scenes(count=3, seed=27)
+    S, probs = make_server(pbs, 10, mode=1)
+    seq = [S.wait(S.submit(k)) for k in range(3)]
+    close(S, probs)
+    S, probs = make_server(pbs, 10, mode=0)
+    bat = [S.wait(t) for t in [S.submit(k) for k in range(3)]]
+    close(S, probs)
+    assert all(r["batch"] == 1 for r in seq)
+    for a, b in zip(seq, bat):
+        assert_same(a, b)
+
+
+def test_advance_moves_the_start_to_the_previous_plan():
+    """advance = 0.1 s: the next plan starts at the previous best plan's
+    position, velocity and acceleration at t = 0.1 s (equality rows of the
+    position QP hold them exactly up to FP32 rounding)."""
+    pb = scenes(count=1, seed=29)[0]
+    S, probs = make_server([pb], 10)
+    r1 = S.wait(S.submit(0))
+    r2 = S.wait(S.submit(0, advance=0.1))
+    close(S, probs)
+    T = pb["T"]
+    tau = 0.1 / T
+    from math import comb
+    k = np.arange(11)
+    B = np.array([comb(10, i) for i in k]) * tau ** k * (1 - tau) ** (10 - k)
+    for blk in range(3):   # x, y, psi
+        c1 = r1["coeffs"][blk].astype(np.float64)
+        want = B @ c1
+        got = float(r2["coeffs"][blk][0])   # a Bernstein curve starts at its first control point
+        assert got == pytest.approx(want, abs=1e-4 * max(1.0, abs(want)))
+
+
+def test_obstacle_track_update_matches_oracle():
+    """A request carrying new obstacle tracks (shifted by 0.1 s along their
+    velocities) solves the scene with those tracks."""
+    pb = scenes(count=1, seed=31)[0]
+    xo, yo = pb["xo"], pb["yo"]
+    vx = (xo[:, -1] - xo[:, 0]) / pb["T"]
+    vy = (yo[:, -1] - yo[:, 0]) / pb["T"]
+    xo2 = (xo + 0.1 * vx[:, None]).astype(np.float32)
+    yo2 = (yo + 0.1 * vy[:, None]).astype(np.float32)
+    S, probs = make_server([pb], 10)
+    r = S.wait(S.submit(0, xo=xo2, yo=yo2))
+    S.close()
+    assert r["status"] == 0
+    st = T_state(probs[0])
+    close(S, probs)
+    pb2 = dict(pb, xo=xo2, yo=yo2)
+    o, tol = coef_tolerance(pb2, 10)
+    for key in ("xi1", "xi2"):
+        assert coef_err(st[key], o[key]).max() <= tol, key
+
+
+def test_budget_admission_and_errors():
+    T = tj()
+    pbs = scenes(count=2, seed=33)
+    need = [T.am_scene_bytes(pb["q"], pb["m"], pb["n"], pb["B"]) for pb in pbs]
+    S = T.Server(need[0] + need[1] // 2, 10)
+    P0, P1 = T.Problem(pbs[0]), T.Problem(pbs[1])
+    assert S.add_scene(P0, pbs[0]["init"].astype(np.float32)) == 0
+    with pytest.raises(T.TrajamError) as e:
+        S.add_scene(P1, pbs[1]["init"].astype(np.float32))
+    assert e.value.code == T.AM_ERR_BUDGET
+    assert "budget" in T.am_last_error()
+    assert S.stats()["device_bytes"] == need[0]
+    S.start()
+    with pytest.raises(T.TrajamError) as e:
+        S.add_scene(P1, pbs[1]["init"].astype(np.float32))   # after the start
+    assert e.value.code == T.AM_ERR_STATE
+    with pytest.raises(T.TrajamError):
+        S.submit(5)          # unknown scene
+    with pytest.raises(T.TrajamError):
+        S.poll(12345)        # unknown ticket
+    r = S.wait(S.submit(0))
+    assert r["status"] == 0
+    S.close()
+    P0.close()
+    P1.close()
