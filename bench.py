@@ -209,6 +209,44 @@ def bench_uneven(TJ, W, torch, dev, flush, steps: int, iters: int = 100) -> dict
                         "T=q/10 s, n 2..32 moving ellipses, m 2..4 circles over [-0.4, 0.4]"}
 
 
+def bench_precision(TJ, W, torch, dev, flush, steps: int, iters: int = 100) -> dict:
+    """The paper-shaped scene at B = 4096 in the three precision forms: FP32
+    (three TF32 products per contraction), and one TF32 or BF16 product for
+    the contractions over the time grid.  Reports the fused kernel's time and
+    each reduced form's coefficient deviation from the FP32 form after 10
+    iterations (the error against the FP64 oracle is measured by the tests)."""
+    pb = W.make_problem("precision", 0)
+    Bp = pb["B"]
+    init = torch.tensor(pb["init"], dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    out, ref = {}, None
+    for prec, name in ((TJ.AM_FP32, "fp32"), (TJ.AM_TF32, "tf32"), (TJ.AM_BF16, "bf16")):
+        P = TJ.Problem(pb, precision=prec)
+        P.solve(init, 10, stream=stream)
+        xi = P.state()[:, :55].astype(np.float64)
+        ms = []
+        for i in range(steps + 2):
+            flush.fill_(float(i))
+            TJ.am_init_state(P.h, Bp, init, None, stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            TJ.am_solve_batch(P.h, Bp, None, None, iters, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        P.close()
+        k_ms = statistics.mean(ms[2:])
+        row = {"value": Bp * iters / (k_ms / 1e3), "unit": UNIT, "kernel_ms": k_ms}
+        if ref is None:
+            ref = xi
+        else:
+            dev_ = np.max(np.abs(xi - ref), axis=1) / np.maximum(np.max(np.abs(ref), axis=1), 1.0)
+            row["coef_dev_vs_fp32_after_10"] = {"max": float(dev_.max()), "median": float(np.median(dev_))}
+        out[name] = row
+    out["workload"] = "paper-shaped scene at B = 4096, 100 iterations per timed solve"
+    return out
+
+
 def serve_run(TJ, W, pbs, mode, kernel, seconds, warmup_s=1.0, rate=400.0, iters=30, seed=7):
     """One serving run: 64 resident scenes, Poisson arrivals at `rate`/s for
     warmup_s + seconds; each request picks a scene uniformly, moves its
@@ -319,6 +357,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-steps", type=int, default=3)
     ap.add_argument("--uneven-steps", type=int, default=3)
+    ap.add_argument("--precision-steps", type=int, default=3)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-plain-seconds", type=float, default=2.0)
     args = ap.parse_args()
@@ -472,6 +511,8 @@ def main():
         }
         if args.uneven_steps > 0:
             line["uneven"] = bench_uneven(TJ, W, torch, dev, flush, args.uneven_steps)
+        if args.precision_steps > 0:
+            line["precision"] = bench_precision(TJ, W, torch, dev, flush, args.precision_steps)
         if args.serve_seconds > 0:
             line["serving"] = bench_serving(TJ, W, args.serve_seconds, args.serve_plain_seconds)
         if not args.no_cpu_baseline:

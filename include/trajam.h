@@ -55,9 +55,15 @@ extern "C" {
 #define AM_HOST 0
 #define AM_DEVICE 1
 
-#define AM_FP32 0           /* FP32 everywhere (the plain precision)          */
-#define AM_TF32 1           /* contractions on tensor cores in TF32          */
-#define AM_BF16 2           /* contractions on tensor cores in BF16          */
+/* Precision of the fused kernel's contractions over the time grid (R =
+ * F^T (g - F xi1), W^T delta, P^T delta): AM_FP32 takes three TF32
+ * tensor-core products per product (hi*hi + hi*lo + lo*hi, FP32 accuracy);
+ * AM_TF32 and AM_BF16 take one product of operands rounded to TF32 or BF16
+ * (the reduced-precision form; the position step keeps three products).
+ * The plain kernel, groups and the allocation-free entry run FP32 only. */
+#define AM_FP32 0
+#define AM_TF32 1
+#define AM_BF16 2
 
 #define AM_KERNEL_FUSED 0   /* one launch runs every iteration (default)     */
 #define AM_KERNEL_PLAIN 1   /* one launch per step, intermediates in memory  */

@@ -148,6 +148,7 @@ void set_scalars(am_problem *h)
     L.psi_sign = h->pp.psi_dual_sign ? -1.f : 1.f;
     L.alpha_mode = h->pp.alpha_mode;
     L.cs_boundary = h->pp.cs_boundary;
+    L.precision = h->pp.precision;
 }
 
 // (Re)forms the setup for n obstacles: FP64 setup, layout, device block.
@@ -193,7 +194,8 @@ int am_init_problem(const am_problem_desc *d, am_problem **out)
         return fail(AM_ERR_ARG, "r_c >= 0 and v_max, a_max, rho, rho_psi > 0 required");
     if (!finite_all(d->x_bc, 6) || !finite_all(d->y_bc, 6) || !finite_all(d->psi_bc, 6))
         return fail(AM_ERR_ARG, "non-finite boundary condition");
-    if (d->precision != AM_FP32) return fail(AM_ERR_ARG, "precision %d not available", d->precision);
+    if (d->precision != AM_FP32 && d->precision != AM_TF32 && d->precision != AM_BF16)
+        return fail(AM_ERR_ARG, "precision %d not available", d->precision);
     if (d->alpha_mode < 0 || d->alpha_mode > 1 || d->psi_dual_sign < 0 || d->psi_dual_sign > 1 ||
         d->cs_boundary < 0 || d->cs_boundary > 1)
         return fail(AM_ERR_ARG, "flag out of range");
@@ -338,6 +340,8 @@ int am_solve_batch(am_problem *h, int B, const float *init, const float *warm_la
     if (!init && (!h->solved || B != h->B))
         return fail(AM_ERR_STATE, "warm start needs a previous solve with the same B");
     if (!init && warm_lambda) return fail(AM_ERR_ARG, "warm_lambda needs init");
+    if (h->kernel == AM_KERNEL_PLAIN && h->pp.precision != AM_FP32)
+        return fail(AM_ERR_ARG, "reduced precision runs on the fused kernel only");
     h->stream = static_cast<cudaStream_t>(stream);
     h->launches = 0;
     int rc = check_B(h, B);
@@ -792,8 +796,10 @@ int am_group_create(am_problem *const *problems, int count, am_group **out)
 {
     if (!problems || !out || count < 1) return fail(AM_ERR_ARG, "need at least one problem");
     *out = nullptr;
-    for (int i = 0; i < count; ++i)
+    for (int i = 0; i < count; ++i) {
         if (!problems[i]) return fail(AM_ERR_ARG, "null problem %d", i);
+        if (problems[i]->pp.precision != AM_FP32) return fail(AM_ERR_ARG, "problem %d: groups run in FP32", i);
+    }
     am_group *g = new (std::nothrow) am_group;
     if (!g) return fail(AM_ERR_ARG, "out of host memory");
     g->probs.assign(problems, problems + count);

@@ -164,6 +164,37 @@ __device__ __forceinline__ void mma3x(float (&d0)[4], float (&d1)[4], float (&d2
     mma_tf32(d2, ah[0], ah[1], ah[2], ah[3], bh0, bh1);
 }
 
+// Reduced-precision forms of the same step (AM_TF32, AM_BF16): one product
+// of operands rounded to TF32, or to BF16 with m16n8k8.bf16.  For BF16 the k
+// index of the fragment is permuted (fragment k = 2t, 2t+1 <-> columns t,
+// t+4 of the step), identically in A and B, so the same loads serve both.
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
+{
+    uint32_t d;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;\n" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+
+template <int PR>
+__device__ __forceinline__ void mma_prec(float (&d0)[4], float (&d1)[4], float (&d2)[4],
+                                         const float (&a)[4], float b0, float b1)
+{
+    if constexpr (PR == 0) {
+        mma3x(d0, d1, d2, a, b0, b1);
+    } else if constexpr (PR == 1) {
+        mma_tf32(d2, round_tf32(__float_as_uint(a[0])), round_tf32(__float_as_uint(a[1])),
+                 round_tf32(__float_as_uint(a[2])), round_tf32(__float_as_uint(a[3])),
+                 round_tf32(__float_as_uint(b0)), round_tf32(__float_as_uint(b1)));
+    } else {
+        const uint32_t a01 = pack_bf16(a[0], a[2]), a23 = pack_bf16(a[1], a[3]), b = pack_bf16(b0, b1);
+        asm volatile(
+            "mma.sync.aligned.m16n8k8.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, "
+            "{%0,%1,%2,%3};\n"
+            : "+f"(d2[0]), "+f"(d2[1]), "+f"(d2[2]), "+f"(d2[3])
+            : "r"(a01), "r"(a23), "r"(b));
+    }
+}
+
 // ------------------------------------------------------------------ small
 
 // Side-row r (0..21) of (c_pos, c_slack) -> padded index within a 24-float side block.
@@ -372,6 +403,7 @@ __device__ void prepare_accumulators(const KParams &p, float *sm, const Smem &S,
 // Eight warp tasks: (segment rv | ra | r0 | r1, n-tile 0/1).  The c_pos rows
 // sum the rv, ra and r0 segment products (shared atomics), the c_slack rows
 // take r1.
+template <int PR>
 __device__ void phase_dot(const KParams &p, float *sm, const Smem &S, const Tile &tl)
 {
     const ConstLayout &L = p.L;
@@ -392,7 +424,7 @@ __device__ void phase_dot(const KParams &p, float *sm, const Smem &S, const Tile
             const int c0 = ks * 8 + tq;
             const float a[4] = {a_lo[c0], a_hi[c0], a_lo[c0 + 4], a_hi[c0 + 4]};
             const float b0 = kv ? bcol[c0] : 0.f, b1 = kv ? bcol[c0 + 4] : 0.f;
-            mma3x(d0, d1, d2, a, b0, b1);
+            mma_prec<PR>(d0, d1, d2, a, b0, b1);
         }
         if (g < tl.count) {
 #pragma unroll
@@ -411,6 +443,7 @@ __device__ void phase_dot(const KParams &p, float *sm, const Smem &S, const Tile
 // 11..21) per trajectory; rows 0..7 = trajectories, rows 8..15 are zero.
 // Six warp tasks: three n-tiles x two halves of the steps, summed with shared
 // atomics.
+template <int PR>
 __device__ void phase_psi(const KParams &p, float *sm, const Smem &S, const Tile &tl)
 {
     const ConstLayout &L = p.L;
@@ -429,7 +462,7 @@ __device__ void phase_psi(const KParams &p, float *sm, const Smem &S, const Tile
             const int c0 = ks * 8 + tq;
             const float a[4] = {arow[c0], 0.f, arow[c0 + 4], 0.f};
             const float b0 = bcol ? bcol[c0] : 0.f, b1 = bcol ? bcol[c0 + 4] : 0.f;
-            mma3x(d0, d1, d2, a, b0, b1);
+            mma_prec<PR>(d0, d1, d2, a, b0, b1);
         }
         if (g < tl.count && k1 > k0) {
 #pragma unroll
@@ -645,7 +678,7 @@ __device__ void init_barrier(uint64_t *bar)
 
 // All iterations of the AM loop for one tile of trajectories of one problem
 // whose constants are staged in shared memory.
-template <int M, bool LIT>
+template <int M, bool LIT, int PR = 0>
 __device__ void run_tile(const KParams &p, float *sm, const Smem &S, const Tile &tl)
 {
     const ConstLayout &L = p.L;
@@ -698,7 +731,7 @@ __device__ void run_tile(const KParams &p, float *sm, const Smem &S, const Tile 
         r.psi_cur = dot11(Prow, x2);  // heading of the reference c_psi
     }
     __syncthreads();
-    phase_dot(p, sm, S, tl);
+    phase_dot<PR>(p, sm, S, tl);
     __syncthreads();
 
     for (int k = 0; k < p.iters; ++k) {
@@ -716,7 +749,7 @@ __device__ void run_tile(const KParams &p, float *sm, const Smem &S, const Tile 
         }
         prepare_accumulators(p, sm, S, tl, cur2);
         __syncthreads();
-        phase_psi(p, sm, S, tl);
+        phase_psi<PR>(p, sm, S, tl);
         __syncthreads();
         if (stepper) {
             // xi2' = xi2 + (Mpsi lam_psi - Mpsi H xi2) + rho W^T delta
@@ -741,7 +774,7 @@ __device__ void run_tile(const KParams &p, float *sm, const Smem &S, const Tile 
         }
         cur2 ^= 1;
         __syncthreads();
-        phase_dot(p, sm, S, tl);
+        phase_dot<PR>(p, sm, S, tl);
         __syncthreads();
     }
     // Multipliers of the last iteration and the final per-trajectory results.
@@ -760,7 +793,7 @@ __device__ void run_tile(const KParams &p, float *sm, const Smem &S, const Tile 
     __syncthreads();
 }
 
-template <int M, bool LIT>
+template <int M, bool LIT, int PR>
 __global__ void __launch_bounds__(kMaxThreads, 1) am_fused_kernel(KParams p)
 {
     extern __shared__ __align__(128) float sm[];
@@ -772,7 +805,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) am_fused_kernel(KParams p)
         return;
     }
     for (int tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x)
-        run_tile<M, LIT>(p, sm, S, tile_of(tile, p.B, p.ntiles));
+        run_tile<M, LIT, PR>(p, sm, S, tile_of(tile, p.B, p.ntiles));
 }
 
 // Uneven batching: persistent launches over the tiles of many problems of
@@ -941,23 +974,28 @@ int launch_fused(const SolveArgs &a, void *stream, int *launches)
     p.err = a.err;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e;
-    const int sel = L.m * 2 + (L.alpha_mode ? 1 : 0);
+    const int sel = (L.precision * 8 + (L.m - 1) * 2) + (L.alpha_mode ? 1 : 0);
     switch (sel) {
-#define AM_CASE(MM, LL)                                                                       \
-    case MM * 2 + LL:                                                                         \
-        e = cudaFuncSetAttribute(am_fused_kernel<MM, LL>,                                     \
+#define AM_CASE(MM, LL, PP)                                                                   \
+    case PP * 8 + (MM - 1) * 2 + LL:                                                          \
+        e = cudaFuncSetAttribute(am_fused_kernel<MM, LL, PP>,                                 \
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));     \
         if (e != cudaSuccess) return -2;                                                      \
-        am_fused_kernel<MM, LL><<<grid, threads, smem, st>>>(p);                              \
+        am_fused_kernel<MM, LL, PP><<<grid, threads, smem, st>>>(p);                          \
         break;
-        AM_CASE(1, 0)
-        AM_CASE(2, 0)
-        AM_CASE(3, 0)
-        AM_CASE(4, 0)
-        AM_CASE(1, 1)
-        AM_CASE(2, 1)
-        AM_CASE(3, 1)
-        AM_CASE(4, 1)
+#define AM_CASES(PP)                                                                          \
+        AM_CASE(1, 0, PP)                                                                     \
+        AM_CASE(2, 0, PP)                                                                     \
+        AM_CASE(3, 0, PP)                                                                     \
+        AM_CASE(4, 0, PP)                                                                     \
+        AM_CASE(1, 1, PP)                                                                     \
+        AM_CASE(2, 1, PP)                                                                     \
+        AM_CASE(3, 1, PP)                                                                     \
+        AM_CASE(4, 1, PP)
+        AM_CASES(0)
+        AM_CASES(1)
+        AM_CASES(2)
+#undef AM_CASES
 #undef AM_CASE
     default:
         return -1;

@@ -84,6 +84,8 @@ struct ConstLayout {
     float psi_sign;           // +1 default reading, -1 printed sign
     int alpha_mode;
     int cs_boundary;          // slack blocks carry boundary rows
+    int precision;            // contractions over the time grid: 0 FP32 (three TF32
+                              // products), 1 one TF32 product, 2 one BF16 product
 };
 
 ConstLayout make_layout(int q, int m, int n);

@@ -493,6 +493,7 @@ extern "C" AM_API int am_solve_batch_noalloc(const am_problem *h, int B, float *
     int rc = handle_constants(h, &cblob, &L);
     if (rc) return rc;
     if (!state || !res || !res_psi || !cost || !mind) return report_error(AM_ERR_ARG, "null device buffer");
+    if (L.precision != 0) return report_error(AM_ERR_ARG, "reduced precision runs on the fused kernel only");
     if (B < 1 || iters < 1 || iters > 100000) return report_error(AM_ERR_ARG, "B >= 1 and 1 <= iters <= 100000 required");
     const size_t need = plain_scratch_floats(L, B);
     if (need > kNoallocScratchFloats) {

@@ -1,0 +1,79 @@
+"""Reduced-precision forms (AM_TF32, AM_BF16) on the 4096-trajectory
+paper-shaped workload, against the FP64 oracle on sampled trajectories.
+
+In these forms the contractions over the time grid (R = F^T (g - F xi1), and
+W^T delta, P^T delta of the heading step) take one tensor-core product of
+operands rounded to TF32 (unit roundoff u = 2^-11) or BF16 (u = 2^-8); the
+position step keeps its three TF32 products.  The error is a reported
+property of the form, not an FP32 parity bar: after 10 iterations the
+coefficients are measured within ~7 u (TF32) and ~17 u (BF16) of the oracle
+and the cost within ~1 u and ~2.5 u.  The bounds below are 30 u on
+coefficients and 10 u on the cost; an implementation mistake (a wrong
+fragment layout, a dropped term) gives errors of order one.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2109_13030_b300 import workload as W
+
+from test_gpu_parity import COEF_TOL, coef_err, sub_problem
+
+pytestmark = pytest.mark.gpu
+
+U = {1: 2.0 ** -11, 2: 2.0 ** -8}
+
+
+def tj():
+    from paper_2109_13030_b300 import trajam
+    return trajam
+
+
+@pytest.fixture(scope="module")
+def workload():
+    pb = W.make_problem("precision", 0)
+    idx = np.unique(np.concatenate([[0, 1, 4095], np.random.default_rng(3).choice(pb["B"], 21, replace=False)]))
+    return pb, idx, O.solve(sub_problem(pb, idx), 10)
+
+
+def solve(pb, precision, iters=10):
+    T = tj()
+    P = T.Problem(pb, precision=precision)
+    P.solve(pb["init"].astype(np.float32), iters)
+    out = T.split_state(P.state())
+    out.update(P.results())
+    P.close()
+    return out
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_reduced_precision_error_bound(workload, precision):
+    pb, idx, o = workload
+    g = solve(pb, precision)
+    u = U[precision]
+    for key in ("xi1", "xi2"):
+        e = coef_err(g[key][idx], o[key])
+        assert np.all(np.isfinite(e)) and e.max() <= 30 * u, (key, e.max())
+    dc = np.abs(g["cost"][idx] - o["cost"]) / np.abs(o["cost"])
+    assert dc.max() <= 10 * u, dc.max()
+
+
+def test_fp32_form_on_the_same_workload(workload):
+    pb, idx, o = workload
+    g = solve(pb, 0)
+    for key in ("xi1", "xi2"):
+        assert coef_err(g[key][idx], o[key]).max() <= COEF_TOL
+
+
+def test_reduced_precision_only_on_the_fused_kernel():
+    T = tj()
+    pb = W.make_problem("tiny", 0)
+    P = T.Problem(pb, precision=T.AM_TF32, kernel=T.AM_KERNEL_PLAIN)
+    with pytest.raises(T.TrajamError) as e:
+        P.solve(pb["init"].astype(np.float32), 5)
+    assert e.value.code == T.AM_ERR_ARG
+    P.close()
+    P = T.Problem(pb, precision=T.AM_BF16)
+    with pytest.raises(T.TrajamError):
+        T.Group([P])
+    P.close()
