@@ -46,6 +46,14 @@ __global__ void prep_obstacles_kernel(float *cblob, ConstLayout L, const float *
     if (i < L.n) {
         const float aj = a[i] + r_c, bj = b[i] + r_c;
         reinterpret_cast<float4 *>(cblob + L.off_obc)[i] = make_float4(1.f / aj, 1.f / bj, aj, bj);
+        // Every circle centre lies within r_max max(1/a, 1/b) of the robot
+        // centre in the ellipse-scaled frame; a centre at squared distance
+        // above this threshold (with a relative margin for rounding) has every
+        // circle outside the ellipse.
+        float rmax = 0.f;
+        for (int k = 0; k < L.m; ++k) rmax = fmaxf(rmax, fabsf(L.r[k]));
+        const float reach = fmaf(rmax, fmaxf(1.f / aj, 1.f / bj), 1.f);
+        cblob[L.off_obt + i] = reach * reach * (1.f + 1e-4f) + 1e-6f;
     }
 }
 

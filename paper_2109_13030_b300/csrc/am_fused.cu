@@ -547,10 +547,20 @@ __device__ __forceinline__ void sweep(float *sm, const Smem &S, const ConstLayou
     float dmin = 3.0e38f;
     const float2 *obs = reinterpret_cast<const float2 *>(cst + L.off_obs);
     const float4 *obc = reinterpret_cast<const float4 *>(cst + L.off_obc);
+    const float *obt = cst + L.off_obt;
     const int n = L.n;
     for (int j = 0; j < n; ++j) {
         const float2 o = obs[j * L.qs + t];   // (x_j(t)/a_j, y_j(t)/b_j)
         const float4 c = obc[j];              // (1/a_j, 1/b_j, a_j, b_j)
+        if (!LIT && !FIN) {
+            // In the default alpha form the row correction of a circle outside
+            // the ellipse is exactly zero (max(1, 1/d) - 1 = 0).  When the robot
+            // centre is far enough that every circle is outside, the warp skips
+            // obstacle j unless one of its steps is near it.
+            const float u0 = fmaf(r.x, c.x, -o.x), v0 = fmaf(r.y, c.y, -o.y);
+            const bool near = fmaf(u0, u0, v0 * v0) < obt[j];
+            if (!__any_sync(__activemask(), near)) continue;
+        }
 #pragma unroll
         for (int i = 0; i < M; ++i) {
             const float xh = fmaf(X[i], c.x, -o.x);   // (x + r_i cos psi - x_j) / a_j

@@ -78,6 +78,7 @@ struct ConstLayout {
     int off_kbpsi;            // [12]
     int off_obs;              // [n][qs][2]   (x_j(t)/a_j, y_j(t)/b_j) pairs
     int off_obc;              // [n][4]       1/a_j, 1/b_j, a_j, b_j (inflated)
+    int off_obt;              // [n]          near threshold (1 + r_max max(1/a_j, 1/b_j))^2
     int total;                // floats, multiple of 4
     float rho, rho_psi, v_max, a_max;
     float r[MAXM];

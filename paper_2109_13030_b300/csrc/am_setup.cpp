@@ -327,6 +327,7 @@ ConstLayout make_layout(int q, int m, int n)
     L.off_kbpsi = o; o = align4(o + 12);
     L.off_obs = o; o = align4(o + n * 2 * qs);
     L.off_obc = o; o = align4(o + n * 4);
+    L.off_obt = o; o = align4(o + n);
     L.total = o;
     return L;
 }
