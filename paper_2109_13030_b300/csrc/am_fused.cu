@@ -54,41 +54,56 @@ constexpr float kTwoPi = 6.28318530717958647692f;
 constexpr float kPi = 3.14159265358979323846f;
 
 struct Smem {
-    int cst, xi1, lam, rb, xi2, dx2, lps, ptp, wdt, bas, G2, RS, GX, PS, bar, total;
+    int cst, xi1, lam, rb, xi2, dx2, lps, ptp, wdt, bas, G2, RS, GX, PS, bar, total, T;
 };
 
 // Shared-memory layout (float offsets).
 //   xi1, lam  [2][T][48]   double-buffered, padded blocks of 12 per polynomial
-//   rb        [T][48]      R per side: c_pos rows 0..10, c_slack rows 12..22
+//   rb        [3][T][48]   partials of R per side (c_pos rows 0..10, c_slack rows
+//                          12..22): from the rv, ra and r0 segments, the c_slack
+//                          rows in the first (R is their sum)
 //   xi2       [2][T][12]   double-buffered c_psi;  dx2 [T][12] last increment
 //   lps       [T][12]      lambda_psi
-//   ptp, wdt, bas [8][12]  P^T delta, W^T delta, Mpsi lam_psi - Mpsi H xi2
-//   G2        [16][RS]     residual vectors, row = side*8 + trajectory,
-//                          segments rv | ra | r0 | r1 of qs steps each
+//   ptp, wdt  [2][8][12]   P^T delta, W^T delta: partials over two halves of the steps
+//   bas       [8][12]      Mpsi lam_psi - Mpsi H xi2
+//   G2        [2T][RS][2]  residual vectors as TF32 (hi, lo) pairs, row =
+//                          side*T + trajectory; segments rv | ra | r0 | r1 of qp steps
 //   GX        [T][4][qs]   per-step squared residual, heading residual, cost, distance
-//   PS        [8][qs]      delta = psi_t - P xi2 per trajectory
+//   PS        [T][qp][2]   delta = psi_t - P xi2 per trajectory as TF32 pairs
+// The constant block is staged from its offset off_fused on; cst is shifted so
+// that sm + cst + off_x addresses section x.
 __host__ __device__ inline Smem smem_layout(const ConstLayout &L, int T)
 {
     Smem s;
     int o = 0;
+    s.T = T;
     s.bar = o; o += 4;  // one 8-byte mbarrier at a fixed offset, 16-byte aligned
-    s.cst = o; o += L.total;
+    s.cst = o - L.off_fused; o += L.total - L.off_fused;
     s.xi1 = o; o += 2 * T * 48;
     s.lam = o; o += 2 * T * 48;
-    s.rb = o; o += T * 48;
+    s.rb = o; o += 3 * T * 48;
     s.xi2 = o; o += 2 * T * 12;
     s.dx2 = o; o += T * 12;
     s.lps = o; o += T * 12;
-    s.ptp = o; o += kMaxTile * 12;
-    s.wdt = o; o += kMaxTile * 12;
+    s.ptp = o; o += 2 * kMaxTile * 12;
+    s.wdt = o; o += 2 * kMaxTile * 12;
     s.bas = o; o += kMaxTile * 12;
-    s.RS = 4 * L.qs + 4;  // 4 mod 8 (qs is): eight rows at one offset hit distinct banks
-    s.G2 = o; o += 16 * s.RS;
+    // pairs per row; 2 RS words = 16 mod 32 (qp = 8 mod 16): the 128-bit
+    // fragment loads of two neighbouring rows fall on distinct banks
+    s.RS = 4 * L.qp + 8;
+    s.G2 = o; o += 2 * T * s.RS * 2;
     s.GX = o; o += T * 4 * L.qs;
-    s.PS = o; o += kMaxTile * L.qs;
+    s.PS = o; o += T * L.qp * 2;
     o = (o + 3) & ~3;
     s.total = o;
     return s;
+}
+
+// R of the position step: the sum of the three partials the DOT phase writes.
+__device__ __forceinline__ float rsum(const float *sm, const Smem &S, int i)
+{
+    const int n = S.T * 48;
+    return sm[S.rb + i] + sm[S.rb + n + i] + sm[S.rb + 2 * n + i];
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -195,6 +210,62 @@ __device__ __forceinline__ void mma_prec(float (&d0)[4], float (&d1)[4], float (
     }
 }
 
+// The same steps on operands split beforehand (TF32 (hi, lo) pairs: the
+// constants on the host, the residual rows and heading increments by the
+// phases that produce them), so the tensor-core phases only load.
+template <int PR>
+__device__ __forceinline__ void mma_pairs(float (&d0)[4], float (&d1)[4], float (&d2)[4],
+                                          const uint2 (&a)[4], uint2 b0, uint2 b1)
+{
+    if constexpr (PR == 0) {
+        mma_tf32(d0, a[0].y, a[1].y, a[2].y, a[3].y, b0.x, b1.x);
+        mma_tf32(d1, a[0].x, a[1].x, a[2].x, a[3].x, b0.y, b1.y);
+        mma_tf32(d2, a[0].x, a[1].x, a[2].x, a[3].x, b0.x, b1.x);
+    } else if constexpr (PR == 1) {
+        mma_tf32(d2, a[0].x, a[1].x, a[2].x, a[3].x, b0.x, b1.x);
+    } else {
+        const float f[4] = {__uint_as_float(a[0].x), __uint_as_float(a[1].x), __uint_as_float(a[2].x),
+                            __uint_as_float(a[3].x)};
+        mma_prec<2>(d0, d1, d2, f, __uint_as_float(b0.x), __uint_as_float(b1.x));
+    }
+}
+
+// A split here, B split beforehand.
+__device__ __forceinline__ void mma_asplit(float (&d0)[4], float (&d1)[4], float (&d2)[4],
+                                           const float (&a)[4], uint2 b0, uint2 b1)
+{
+    uint2 ap[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) split_tf32(a[i], ap[i].x, ap[i].y);
+    mma_pairs<0>(d0, d1, d2, ap, b0, b1);
+}
+
+__device__ __forceinline__ void st_split(uint2 *dst, float v)
+{
+    uint2 w;
+    split_tf32(v, w.x, w.y);
+    *dst = w;
+}
+
+// The columns of one k-step are permuted so that the two k elements a lane
+// holds (fragment k = t and t + 4) are the adjacent columns 2t, 2t + 1: one
+// 128-bit load brings both (hi, lo) pairs.  A and B use the same permutation,
+// so the product is unchanged.
+__device__ __forceinline__ void ld_pair2(const uint2 *p, uint2 &e0, uint2 &e1)
+{
+    const uint4 v = *reinterpret_cast<const uint4 *>(p);
+    e0 = make_uint2(v.x, v.y);
+    e1 = make_uint2(v.z, v.w);
+}
+
+// Row of a fragment lane: lanes past the tile read a row of the same parity
+// (their results are discarded; MMA rows are independent), keeping the
+// neighbouring-row bank pattern.
+__device__ __forceinline__ int frag_row(int g, int count)
+{
+    return g < count ? g : (count > 1 ? (g & 1) : 0);
+}
+
 // ------------------------------------------------------------------ small
 
 // Side-row r (0..21) of (c_pos, c_slack) -> padded index within a 24-float side block.
@@ -258,21 +329,23 @@ __device__ void xi1_mma(const KParams &p, float *sm, const Smem &S, const Tile &
     const int tt = valid ? g : 0;
     const float *lam = sm + S.lam + (cur * p.T + tt) * 48;
     const float *xi = sm + S.xi1 + (cur * p.T + tt) * 48;
-    const float *R = sm + S.rb + tt * 48;
+    const int rtt = tt * 48;
     for (int nt = warp; nt < 3; nt += blockDim.x >> 5) {
-        const float *brow = sm + S.cst + L.off_xib + (nt * 8 + g) * 52;
+        const uint2 *brow = reinterpret_cast<const uint2 *>(sm + S.cst + L.off_xib2) + (nt * 8 + g) * 56;
         float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f}, d2[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int ks = 0; ks < 6; ++ks) {
-            const int k0 = ks * 8 + tq, k1 = k0 + 4;
+            const int k0 = ks * 8 + 2 * tq, k1 = k0 + 1;  // permuted k-step columns
             float a[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int k = (e < 2) ? k0 : k1, side = e & 1;
                 const int o = side * 24 + (k < 24 ? k : k - 24);
-                a[e] = !valid ? 0.f : k < 24 ? fmaf(coef, R[o], lam[o]) : xi[o];
+                a[e] = !valid ? 0.f : k < 24 ? fmaf(coef, rsum(sm, S, rtt + o), lam[o]) : xi[o];
             }
-            mma3x(d0, d1, d2, a, brow[k0], brow[k1]);
+            uint2 b0, b1;
+            ld_pair2(brow + k0, b0, b1);
+            mma_asplit(d0, d1, d2, a, b0, b1);
         }
         if (valid) {
             float *lam_n = sm + S.lam + ((cur ^ 1) * p.T + tt) * 48;
@@ -283,7 +356,7 @@ __device__ void xi1_mma(const KParams &p, float *sm, const Smem &S, const Tile &
                 if (c == NV || c == 23) continue;  // pads stay zero
                 const int o = (e >> 1) * 24 + c;
                 xi_n[o] = xi[o] + (d0[e] + d1[e] + d2[e]);
-                lam_n[o] = first ? lam[o] : fmaf(rho, R[o], lam[o]);
+                lam_n[o] = first ? lam[o] : fmaf(rho, rsum(sm, S, rtt + o), lam[o]);
             }
         }
     }
@@ -311,7 +384,7 @@ __device__ void phase_xi1(const KParams &p, float *sm, const Smem &S, const Tile
             const int tt = task / 44, rem = task - 44 * tt, side = rem / NS, row = rem - NS * side;
             const float *lam = sm + S.lam + (cur * p.T + tt) * 48 + 24 * side;
             const float *xi = sm + S.xi1 + (cur * p.T + tt) * 48 + 24 * side;
-            const float *R = sm + S.rb + tt * 48 + 24 * side;
+            const int rbase = tt * 48 + 24 * side;
             float *lam_n = sm + S.lam + ((cur ^ 1) * p.T + tt) * 48 + 24 * side;
             float *xi_n = sm + S.xi1 + ((cur ^ 1) * p.T + tt) * 48 + 24 * side;
             const int rp = rowpad(row);
@@ -322,13 +395,13 @@ __device__ void phase_xi1(const KParams &p, float *sm, const Smem &S, const Tile
 #pragma unroll
                 for (int c = 0; c < NS; ++c) {
                     const int cp = rowpad(c);
-                    a0 = fmaf(cst[L.off_mt + c * 24 + row], fmaf(coef, R[cp], lam[cp]), a0);
+                    a0 = fmaf(cst[L.off_mt + c * 24 + row], fmaf(coef, rsum(sm, S, rbase + cp), lam[cp]), a0);
                     a1 = fmaf(cst[L.off_mq + c * 24 + row], xi[cp], a1);
                 }
                 xn += a0 - a1;
             }
             xi_n[rp] = xn;
-            lam_n[rp] = first ? lam[rp] : fmaf(rho, R[rp], lam[rp]);
+            lam_n[rp] = first ? lam[rp] : fmaf(rho, rsum(sm, S, rbase + rp), lam[rp]);
         } else if (task < n_xi + n_lp) {
             if (first) continue;
             // P^T (P xi2' - psi_t) = P^T P dxi2 - P^T delta, delta = psi_t - P xi2
@@ -338,7 +411,7 @@ __device__ void phase_xi1(const KParams &p, float *sm, const Smem &S, const Tile
 #pragma unroll
             for (int c = 0; c < NV; ++c) a = fmaf(cst[L.off_ptp + c * 12 + k], dx2[c], a);
             float *lp = sm + S.lps + tt * 12;
-            lp[k] -= L.psi_sign * L.rho_psi * (a - sm[S.ptp + tt * 12 + k]);
+            lp[k] -= L.psi_sign * L.rho_psi * (a - (sm[S.ptp + tt * 12 + k] + sm[S.ptp + 96 + tt * 12 + k]));
         } else {
             const int s = task - n_xi - n_lp, tt = s >> 2, w = s & 3;
             const float *gv = sm + S.GX + (tt * 4 + w) * L.qs;
@@ -378,31 +451,24 @@ __device__ void prepare_accumulators(const KParams &p, float *sm, const Smem &S,
     const ConstLayout &L = p.L;
     const float *cst = sm + S.cst;
     const int Tn = tl.count;
-    for (int i = threadIdx.x; i < Tn * 48; i += blockDim.x) sm[S.rb + i] = 0.f;
-    for (int i = threadIdx.x; i < Tn * 24; i += blockDim.x) {
-        const int tt = i / 24, j = i - 24 * tt;
-        if (j < 12) {
-            sm[S.ptp + tt * 12 + j] = 0.f;
-            sm[S.wdt + tt * 12 + j] = 0.f;
-        }
-        if (j < NV) {
-            const float *lp = sm + S.lps + tt * 12;
-            const float *x2 = sm + S.xi2 + (cur2 * p.T + tt) * 12;
-            float b0 = 0.f, b1 = 0.f;
+    for (int i = threadIdx.x; i < Tn * NV; i += blockDim.x) {
+        const int tt = i / NV, j = i - NV * tt;
+        const float *lp = sm + S.lps + tt * 12;
+        const float *x2 = sm + S.xi2 + (cur2 * p.T + tt) * 12;
+        float b0 = 0.f, b1 = 0.f;
 #pragma unroll
-            for (int c = 0; c < NV; ++c) {
-                b0 = fmaf(cst[L.off_mpsi + c * 12 + j], lp[c], b0);
-                b1 = fmaf(cst[L.off_mpsih + c * 12 + j], x2[c], b1);
-            }
-            sm[S.bas + tt * 12 + j] = b0 - b1;
+        for (int c = 0; c < NV; ++c) {
+            b0 = fmaf(cst[L.off_mpsi + c * 12 + j], lp[c], b0);
+            b1 = fmaf(cst[L.off_mpsih + c * 12 + j], x2[c], b1);
         }
+        sm[S.bas + tt * 12 + j] = b0 - b1;
     }
 }
 
 // DOT phase on the tensor cores.  One 16-row tile: row = side*8 + trajectory.
-// Eight warp tasks: (segment rv | ra | r0 | r1, n-tile 0/1).  The c_pos rows
-// sum the rv, ra and r0 segment products (shared atomics), the c_slack rows
-// take r1.
+// Eight warp tasks: (segment rv | ra | r0 | r1, n-tile 0/1).  Each segment's
+// product goes to its own partial of R (rv, ra, r0 -> c_pos rows of partials
+// 0, 1, 2; r1 -> c_slack rows of partial 0), so no two tasks write one word.
 template <int PR>
 __device__ void phase_dot(const KParams &p, float *sm, const Smem &S, const Tile &tl)
 {
@@ -410,30 +476,35 @@ __device__ void phase_dot(const KParams &p, float *sm, const Smem &S, const Tile
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane >> 2, tq = lane & 3;
     const int nks = (L.q + 7) >> 3;
+    const int row = frag_row(g, tl.count);
     for (int task = warp; task < 8; task += blockDim.x >> 5) {
         const int seg = task >> 1, nt = task & 1;
         const int bsel = seg == 0 ? 1 : seg == 1 ? 2 : 0;  // Pd, Pdd, P, P
         const int k = nt * 8 + g;
-        const bool kv = k < NV;
-        const float *bcol = sm + S.cst + L.off_pcol + (bsel * NV + (kv ? k : 0)) * L.qs;
-        const float *a_lo = sm + S.G2 + g * S.RS + seg * L.qs;
-        const float *a_hi = a_lo + 8 * S.RS;
+        // B columns past the 11 basis functions give discarded outputs: read
+        // a real column of the same parity instead of zeros
+        const uint2 *bcol = reinterpret_cast<const uint2 *>(sm + S.cst + L.off_pcol2) +
+                            (bsel * NV + (k < NV ? k : k - 8)) * L.qp;
+        const uint2 *G = reinterpret_cast<const uint2 *>(sm + S.G2);
+        const uint2 *a_lo = G + row * S.RS + seg * L.qp;
+        const uint2 *a_hi = G + (S.T + row) * S.RS + seg * L.qp;
         float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f}, d2[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 2
+#pragma unroll 1
         for (int ks = 0; ks < nks; ++ks) {
-            const int c0 = ks * 8 + tq;
-            const float a[4] = {a_lo[c0], a_hi[c0], a_lo[c0 + 4], a_hi[c0 + 4]};
-            const float b0 = kv ? bcol[c0] : 0.f, b1 = kv ? bcol[c0 + 4] : 0.f;
-            mma_prec<PR>(d0, d1, d2, a, b0, b1);
+            const int c0 = ks * 8 + 2 * tq;
+            uint2 a[4], b0, b1;
+            ld_pair2(a_lo + c0, a[0], a[2]);
+            ld_pair2(a_hi + c0, a[1], a[3]);
+            ld_pair2(bcol + c0, b0, b1);
+            mma_pairs<PR>(d0, d1, d2, a, b0, b1);
         }
         if (g < tl.count) {
+            float *R = sm + S.rb + (seg < 3 ? seg : 0) * S.T * 48 + g * 48;
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int side = e >> 1, col = nt * 8 + 2 * tq + (e & 1);
                 if (col >= NV) continue;
-                float *R = sm + S.rb + g * 48 + 24 * side;
-                if (seg < 3) atomicAdd(R + col, d0[e] + d1[e] + d2[e]);
-                else R[12 + col] = d0[e] + d1[e] + d2[e];
+                R[24 * side + (seg < 3 ? col : 12 + col)] = d0[e] + d1[e] + d2[e];
             }
         }
     }
@@ -441,8 +512,8 @@ __device__ void phase_dot(const KParams &p, float *sm, const Smem &S, const Tile
 
 // PSI phase on the tensor cores: W^T delta (cols 0..10) and P^T delta (cols
 // 11..21) per trajectory; rows 0..7 = trajectories, rows 8..15 are zero.
-// Six warp tasks: three n-tiles x two halves of the steps, summed with shared
-// atomics.
+// Six warp tasks: three n-tiles x two halves of the steps, each half into its
+// own partial.
 template <int PR>
 __device__ void phase_psi(const KParams &p, float *sm, const Smem &S, const Tile &tl)
 {
@@ -450,27 +521,33 @@ __device__ void phase_psi(const KParams &p, float *sm, const Smem &S, const Tile
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane >> 2, tq = lane & 3;
     const int nks = (L.q + 7) >> 3, quarter = (nks + 1) >> 1;
+    const uint2 *arow = reinterpret_cast<const uint2 *>(sm + S.PS) + frag_row(g, tl.count) * L.qp;
+    const uint2 z = make_uint2(0u, 0u);
     for (int task = warp; task < 6; task += blockDim.x >> 5) {
         const int nt = task % 3, part = task / 3;
         const int col = nt * 8 + g;
-        const float *bcol = col < NV ? sm + S.cst + L.off_wcol + col * L.qs
-                          : col < NS ? sm + S.cst + L.off_pcol + (col - NV) * L.qs : nullptr;
-        const float *arow = sm + S.PS + g * L.qs;
+        // columns 22, 23 give discarded outputs: read columns of the same parity
+        const uint2 *bcol = col < NV ? reinterpret_cast<const uint2 *>(sm + S.cst + L.off_wcol2) + col * L.qp
+                                     : reinterpret_cast<const uint2 *>(sm + S.cst + L.off_pcol2) +
+                                           (col < NS ? col - NV : col - NV - 8) * L.qp;
         float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f}, d2[4] = {0.f, 0.f, 0.f, 0.f};
         const int k0 = part * quarter, k1 = min(nks, k0 + quarter);
         for (int ks = k0; ks < k1; ++ks) {
-            const int c0 = ks * 8 + tq;
-            const float a[4] = {arow[c0], 0.f, arow[c0 + 4], 0.f};
-            const float b0 = bcol ? bcol[c0] : 0.f, b1 = bcol ? bcol[c0 + 4] : 0.f;
-            mma_prec<PR>(d0, d1, d2, a, b0, b1);
+            const int c0 = ks * 8 + 2 * tq;
+            uint2 a[4], b0, b1;
+            ld_pair2(arow + c0, a[0], a[2]);
+            a[1] = z;
+            a[3] = z;
+            ld_pair2(bcol + c0, b0, b1);
+            mma_pairs<PR>(d0, d1, d2, a, b0, b1);
         }
-        if (g < tl.count && k1 > k0) {
+        if (g < tl.count) {
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
                 const int c = nt * 8 + 2 * tq + e;
                 const float v = d0[e] + d1[e] + d2[e];
-                if (c < NV) atomicAdd(sm + S.wdt + g * 12 + c, v);
-                else if (c < NS) atomicAdd(sm + S.ptp + g * 12 + (c - NV), v);
+                if (c < NV) sm[S.wdt + part * 96 + g * 12 + c] = v;
+                else if (c < NS) sm[S.ptp + part * 96 + g * 12 + (c - NV)] = v;
             }
         }
     }
@@ -620,18 +697,19 @@ __device__ __forceinline__ void sweep(float *sm, const Smem &S, const ConstLayou
         }
     }
     const int qs = L.qs;
-    float *Gx = sm + S.G2 + tt * S.RS + t;        // side x: row tt
-    float *Gy = Gx + 8 * S.RS;                    // side y: row 8 + tt
+    uint2 *Gx = reinterpret_cast<uint2 *>(sm + S.G2) + tt * S.RS + t;   // side x: row tt
+    uint2 *Gy = Gx + S.T * S.RS;                                        // side y: row T + tt
     const float svm = sv - 1.f, sam = sa - 1.f;
     // v and a rows: projected value - F xi1 value
-    Gx[0] = PRO ? fmaf(r.xd, svm, r.xd - ref.xd) : r.xd * svm;
-    Gx[qs] = PRO ? fmaf(r.xdd, sam, r.xdd - ref.xdd) : r.xdd * sam;
-    Gx[2 * qs] = r0x;
-    Gx[3 * qs] = r1x + dcx;
-    Gy[0] = PRO ? fmaf(r.yd, svm, r.yd - ref.yd) : r.yd * svm;
-    Gy[qs] = PRO ? fmaf(r.ydd, sam, r.ydd - ref.ydd) : r.ydd * sam;
-    Gy[2 * qs] = r0y;
-    Gy[3 * qs] = r1y + dsy;
+    const int qp = L.qp;
+    st_split(Gx, PRO ? fmaf(r.xd, svm, r.xd - ref.xd) : r.xd * svm);
+    st_split(Gx + qp, PRO ? fmaf(r.xdd, sam, r.xdd - ref.xdd) : r.xdd * sam);
+    st_split(Gx + 2 * qp, r0x);
+    st_split(Gx + 3 * qp, r1x + dcx);
+    st_split(Gy, PRO ? fmaf(r.yd, svm, r.yd - ref.yd) : r.yd * svm);
+    st_split(Gy + qp, PRO ? fmaf(r.ydd, sam, r.ydd - ref.ydd) : r.ydd * sam);
+    st_split(Gy + 2 * qp, r0y);
+    st_split(Gy + 3 * qp, r1y + dsy);
     float *GX = sm + S.GX + tt * 4 * qs + t;
     if (RES) {
         GX[0] = v2 * svm * svm + a2 * sam * sam + rob + dcx * dcx + dsy * dsy;
@@ -663,13 +741,13 @@ __device__ bool stage_constants(const KParams &p, float *sm, const Smem &S, uint
                                 uint32_t parity)
 {
     if (threadIdx.x == 0) {
-        const uint32_t bytes = uint32_t(p.L.total) * 4u;
+        const uint32_t bytes = uint32_t(p.L.total - p.L.off_fused) * 4u;
         // order the block's earlier generic-proxy accesses of this area
         // before the asynchronous copy overwrites it
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n"
                      :: "r"(smem_u32(bar)), "r"(bytes) : "memory");
-        bulk_load(sm + S.cst, p.cblob, bytes, bar);
+        bulk_load(sm + S.cst + p.L.off_fused, p.cblob + p.L.off_fused, bytes, bar);
     }
     for (int i = S.xi1 + threadIdx.x; i < S.total; i += blockDim.x) sm[i] = 0.f;
     int ok = 0;
@@ -702,7 +780,7 @@ __device__ void run_tile(const KParams &p, float *sm, const Smem &S, const Tile 
         else if (e < 99) sm[S.lam + tt * 48 + ((e - 55) / NV) * 12 + (e - 55) % NV] = v;
         else sm[S.lps + tt * 12 + (e - 99)] = v;
     }
-    for (int i = threadIdx.x; i < Tn * 48; i += blockDim.x) sm[S.rb + i] = 0.f;
+    for (int i = threadIdx.x; i < 3 * p.T * 48; i += blockDim.x) sm[S.rb + i] = 0.f;
     __syncthreads();
     // Reference xi1, xi2 into buffer 0: boundary control points from the
     // boundary conditions on every block that has boundary rows, the rest as given.
@@ -755,7 +833,7 @@ __device__ void run_tile(const KParams &p, float *sm, const Smem &S, const Tile 
             // psi_t = psi + wrap(atan2(s, c) - psi), psi the previous heading;
             // the heading step works on delta = psi_t - P xi2
             r.psi_t = r.psi_prev + wrap_pi(atan2f(r.s, r.c) - r.psi_prev);
-            sm[S.PS + tt * L.qs + t] = r.psi_t - r.psi_cur;
+            st_split(reinterpret_cast<uint2 *>(sm + S.PS) + tt * L.qp + t, r.psi_t - r.psi_cur);
         }
         prepare_accumulators(p, sm, S, tl, cur2);
         __syncthreads();
@@ -766,6 +844,12 @@ __device__ void run_tile(const KParams &p, float *sm, const Smem &S, const Tile 
             float x2[12], w[12], b[12];
             load12(x2, sm + S.xi2 + (cur2 * p.T + tt) * 12);
             load12(w, sm + S.wdt + tt * 12);
+            {
+                float w1[12];
+                load12(w1, sm + S.wdt + 96 + tt * 12);
+#pragma unroll
+                for (int c = 0; c < 12; ++c) w[c] += w1[c];
+            }
             load12(b, sm + S.bas + tt * 12);
             float d2[12];
 #pragma unroll

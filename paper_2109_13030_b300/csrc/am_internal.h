@@ -64,12 +64,17 @@ int rebuild_boundary(const ProblemParams &pp, HostSetup &S);
 // into shared memory.  Every section starts on a 16-byte boundary.
 struct ConstLayout {
     int q, qs, m, n;          // qs: padded stride of per-step columns
+    int qp;                   // stride (in pairs) of the split per-step columns
+    int off_pcol;             // [3][NV][qs]  P, Pd, Pdd columns (FP32, plain loop)
+    int off_wcol;             // [NV][qs]     W = P Mpsi^T, columns (FP32, plain loop)
+    int off_fused;            // start of the part the fused kernel stages:
     int off_prow;             // [3][q][12]   P, Pd, Pdd rows (padded to 12)
-    int off_pcol;             // [3][NV][qs]  P, Pd, Pdd columns
-    int off_wcol;             // [NV][qs]     W = P Mpsi^T, columns
+    int off_pcol2;            // [3][NV][qp][2] P, Pd, Pdd columns as TF32 (hi, lo) pairs
+    int off_wcol2;            // [NV][qp][2]  W columns as TF32 (hi, lo) pairs
     int off_mt;               // [NS][24]     Minv^T
     int off_mq;               // [NS][24]     (Minv blockdiag(H, H))^T
-    int off_xib;              // [24][52]     [Minv | -Minv Q] on padded indices, row = output
+    int off_xib2;             // [24][56][2]  [Minv | -Minv Q] on padded indices, row = output,
+                              //              as TF32 (hi, lo) pairs
     int off_ends;             // [5][8]       boundary control points per block (xi1 blocks, c_psi)
     int off_kb;               // [2][24]      kb (x side, y side)
     int off_mpsi;             // [NV][12]     Mpsi^T

@@ -313,12 +313,21 @@ ConstLayout make_layout(int q, int m, int n)
     const int qs = ((q + 7) & ~7) + 4;
     L.qs = qs;
     int o = 0;
-    L.off_prow = o; o = align4(o + 3 * q * 12);
+    // FP32 columns for the plain loop, outside the part the fused kernel stages
     L.off_pcol = o; o = align4(o + 3 * NV * qs);
     L.off_wcol = o; o = align4(o + NV * qs);
+    // Split (hi, lo) columns: a stride of qp pairs = 16 mod 32 words, so the
+    // 128-bit fragment loads of two neighbouring rows fall on distinct banks.
+    int qp = (q + 7) & ~7;
+    if (qp % 16 == 0) qp += 8;
+    L.qp = qp;
+    L.off_fused = o;
+    L.off_prow = o; o = align4(o + 3 * q * 12);
+    L.off_pcol2 = o; o = align4(o + 3 * NV * 2 * qp);
+    L.off_wcol2 = o; o = align4(o + NV * 2 * qp);
     L.off_mt = o; o = align4(o + NS * 24);
     L.off_mq = o; o = align4(o + NS * 24);
-    L.off_xib = o; o = align4(o + 24 * 52);
+    L.off_xib2 = o; o = align4(o + 24 * 2 * 56);
     L.off_ends = o; o = align4(o + 5 * 8);
     L.off_kb = o; o = align4(o + 2 * 24);
     L.off_mpsi = o; o = align4(o + NV * 12);
@@ -332,6 +341,33 @@ ConstLayout make_layout(int q, int m, int n)
     return L;
 }
 
+namespace {
+
+// x = hi + lo with hi, lo both TF32 (round to nearest on the bit pattern:
+// add half a TF32 unit to the magnitude bits, clear the 13 low mantissa
+// bits), stored as FP32 values.  The fused kernel splits its run-time
+// operands the same way.
+void split_tf32(float x, float &hi, float &lo)
+{
+    auto round = [](float v) {
+        uint32_t b;
+        std::memcpy(&b, &v, 4);
+        b = (b + 0x1000u) & 0xFFFFE000u;
+        float r;
+        std::memcpy(&r, &b, 4);
+        return r;
+    };
+    hi = round(x);
+    lo = round(x - hi);
+}
+
+void put_split(std::vector<float> &blob, int off, float v)
+{
+    split_tf32(v, blob[off], blob[off + 1]);
+}
+
+}  // namespace
+
 void fill_constants(const HostSetup &S, const ProblemParams &pp, const ConstLayout &L,
                     std::vector<float> &blob)
 {
@@ -344,9 +380,14 @@ void fill_constants(const HostSetup &S, const ProblemParams &pp, const ConstLayo
                 const float v = float((*B3[b])[t * NV + k]);
                 blob[L.off_prow + (b * q + t) * 12 + k] = v;
                 blob[L.off_pcol + (b * NV + k) * qs + t] = v;
+                put_split(blob, L.off_pcol2 + 2 * ((b * NV + k) * L.qp + t), v);
             }
     for (int t = 0; t < q; ++t)
-        for (int k = 0; k < NV; ++k) blob[L.off_wcol + k * qs + t] = float(S.W[t * NV + k]);
+        for (int k = 0; k < NV; ++k) {
+            const float w = float(S.W[t * NV + k]);
+            blob[L.off_wcol + k * qs + t] = w;
+            put_split(blob, L.off_wcol2 + 2 * (k * L.qp + t), w);
+        }
     for (int a = 0; a < NS; ++a)
         for (int b = 0; b < NS; ++b) {
             blob[L.off_mt + b * 24 + a] = float(S.Minv[a][b]);
@@ -360,7 +401,7 @@ void fill_constants(const HostSetup &S, const ProblemParams &pp, const ConstLayo
         for (int kp = 0; kp < 48; ++kp) {
             const int a = unpad(np), b = unpad(kp % 24);
             if (a < 0 || b < 0) continue;
-            blob[L.off_xib + np * 52 + kp] = float(kp < 24 ? S.Minv[a][b] : -S.MQ[a][b]);
+            put_split(blob, L.off_xib2 + 2 * (np * 56 + kp), float(kp < 24 ? S.Minv[a][b] : -S.MQ[a][b]));
         }
     for (int blk = 0; blk < 5; ++blk)
         for (int e = 0; e < 6; ++e) blob[L.off_ends + blk * 8 + e] = float(S.ends[blk][e]);
