@@ -50,26 +50,30 @@ namespace {
 
 constexpr int kMaxThreads = 768;
 constexpr int kMaxTile = 8;     // rows (side, trajectory) of one 16-row MMA tile
+constexpr int kRParts = 12;     // partials of R: (rv | ra | r0 segment) x quarter of the steps
+constexpr int kPsiParts = 4;    // partials of W^T delta, P^T delta: quarters of the steps
 constexpr float kTwoPi = 6.28318530717958647692f;
 constexpr float kPi = 3.14159265358979323846f;
 
 struct Smem {
-    int cst, xi1, lam, rb, xi2, dx2, lps, ptp, wdt, bas, G2, RS, GX, PS, bar, total, T;
+    int cst, xi1, lam, rb, xi2, dx2, lps, ptp, wdt, bas, G2, RS, GX, PS, XA, bar, total, T;
 };
 
 // Shared-memory layout (float offsets).
 //   xi1, lam  [2][T][48]   double-buffered, padded blocks of 12 per polynomial
-//   rb        [3][T][48]   partials of R per side (c_pos rows 0..10, c_slack rows
-//                          12..22): from the rv, ra and r0 segments, the c_slack
-//                          rows in the first (R is their sum)
+//   rb        [12][T][48]  partials of R per side (c_pos rows 0..10, c_slack rows
+//                          12..22): (rv, ra, r0 segment) x quarter of the steps;
+//                          the c_slack rows in the first four (R is the sum of all)
 //   xi2       [2][T][12]   double-buffered c_psi;  dx2 [T][12] last increment
 //   lps       [T][12]      lambda_psi
-//   ptp, wdt  [2][8][12]   P^T delta, W^T delta: partials over two halves of the steps
+//   ptp, wdt  [4][8][12]   P^T delta, W^T delta: partials over four quarters of the steps
 //   bas       [8][12]      Mpsi lam_psi - Mpsi H xi2
-//   G2        [2T][RS][2]  residual vectors as TF32 (hi, lo) pairs, row =
-//                          side*T + trajectory; segments rv | ra | r0 | r1 of qp steps
+//   G2        [2T][RS]     residual vectors, row = side*T + trajectory; segments
+//                          rv | ra | r0 | r1 of qp steps
 //   GX        [T][4][qs]   per-step squared residual, heading residual, cost, distance
-//   PS        [T][qp][2]   delta = psi_t - P xi2 per trajectory as TF32 pairs
+//   PS        [T][qp]      delta = psi_t - P xi2 per trajectory
+//   XA        [2T][56][2]  A operand of the position step as TF32 pairs, row =
+//                          side*T + trajectory: lam + coef R (24) | xi1 (24)
 // The constant block is staged from its offset off_fused on; cst is shifted so
 // that sm + cst + off_x addresses section x.
 __host__ __device__ inline Smem smem_layout(const ConstLayout &L, int T)
@@ -81,29 +85,42 @@ __host__ __device__ inline Smem smem_layout(const ConstLayout &L, int T)
     s.cst = o - L.off_fused; o += L.total - L.off_fused;
     s.xi1 = o; o += 2 * T * 48;
     s.lam = o; o += 2 * T * 48;
-    s.rb = o; o += 3 * T * 48;
+    s.rb = o; o += kRParts * T * 48;
     s.xi2 = o; o += 2 * T * 12;
     s.dx2 = o; o += T * 12;
     s.lps = o; o += T * 12;
-    s.ptp = o; o += 2 * kMaxTile * 12;
-    s.wdt = o; o += 2 * kMaxTile * 12;
+    s.ptp = o; o += kPsiParts * kMaxTile * 12;
+    s.wdt = o; o += kPsiParts * kMaxTile * 12;
     s.bas = o; o += kMaxTile * 12;
-    // pairs per row; 2 RS words = 16 mod 32 (qp = 8 mod 16): the 128-bit
-    // fragment loads of two neighbouring rows fall on distinct banks
+    // RS = 8 mod 32 and qp = 8 mod 16: the 64-bit fragment loads of four
+    // neighbouring rows fall on distinct banks
     s.RS = 4 * L.qp + 8;
-    s.G2 = o; o += 2 * T * s.RS * 2;
+    s.G2 = o; o += 2 * T * s.RS;
     s.GX = o; o += T * 4 * L.qs;
-    s.PS = o; o += T * L.qp * 2;
+    s.PS = o; o += T * L.qp;
+    s.XA = o; o += 2 * T * 56 * 2;
     o = (o + 3) & ~3;
     s.total = o;
     return s;
 }
 
-// R of the position step: the sum of the three partials the DOT phase writes.
+// R of the position step: the sum of the partials the DOT phase writes.
 __device__ __forceinline__ float rsum(const float *sm, const Smem &S, int i)
 {
     const int n = S.T * 48;
-    return sm[S.rb + i] + sm[S.rb + n + i] + sm[S.rb + 2 * n + i];
+    float r = 0.f;
+#pragma unroll
+    for (int k = 0; k < kRParts; ++k) r += sm[S.rb + k * n + i];
+    return r;
+}
+
+// Sum of the kPsiParts partials of W^T delta or P^T delta, entry (tt, k).
+__device__ __forceinline__ float psisum(const float *sm, int base, int i)
+{
+    float r = 0.f;
+#pragma unroll
+    for (int k = 0; k < kPsiParts; ++k) r += sm[base + k * kMaxTile * 12 + i];
+    return r;
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -230,16 +247,6 @@ __device__ __forceinline__ void mma_pairs(float (&d0)[4], float (&d1)[4], float 
     }
 }
 
-// A split here, B split beforehand.
-__device__ __forceinline__ void mma_asplit(float (&d0)[4], float (&d1)[4], float (&d2)[4],
-                                           const float (&a)[4], uint2 b0, uint2 b1)
-{
-    uint2 ap[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) split_tf32(a[i], ap[i].x, ap[i].y);
-    mma_pairs<0>(d0, d1, d2, ap, b0, b1);
-}
-
 __device__ __forceinline__ void st_split(uint2 *dst, float v)
 {
     uint2 w;
@@ -264,6 +271,19 @@ __device__ __forceinline__ void ld_pair2(const uint2 *p, uint2 &e0, uint2 &e1)
 __device__ __forceinline__ int frag_row(int g, int count)
 {
     return g < count ? g : (count > 1 ? (g & 1) : 0);
+}
+
+// The same for 64-bit loads, whose 16-lane wavefronts hold four rows: a row
+// equal to the lane's modulo 4 where the tile has one.
+__device__ __forceinline__ int frag_row4(int g, int count)
+{
+    return g < count ? g : (g & 3) < count ? (g & 3) : 0;
+}
+
+__device__ __forceinline__ void split4(const float (&a)[4], uint2 (&ap)[4])
+{
+#pragma unroll
+    for (int i = 0; i < 4; ++i) split_tf32(a[i], ap[i].x, ap[i].y);
 }
 
 // ------------------------------------------------------------------ small
@@ -316,47 +336,60 @@ __device__ __forceinline__ Tile tile_of(int i, int B, int ntiles)
 // Position step on the tensor cores, one 16-row tile (row = side*8 + trajectory):
 //   D[row][np] = sum_k A[row][k] Bt[np][k],  A = [lam + coef R | xi1],  Bt = [Minv | -Minv Q]
 // on padded indices (k, np in 0..23 per side, 11 and 23 are zero pads), then
-// xi1' = xi1 + D and lam' = lam (first) or lam + rho R.  Three warp tasks, one
-// per n-tile of 8 output columns.
-__device__ void xi1_mma(const KParams &p, float *sm, const Smem &S, const Tile &tl, int cur,
-                        bool first)
+// xi1' = xi1 + D.  The whole block first forms A (split into TF32 pairs) and
+// lam' once; three warp tasks, one per n-tile of 8 output columns, then run
+// the products.
+__device__ void xi1_operand(const KParams &p, float *sm, const Smem &S, const Tile &tl, int cur,
+                            bool first)
+{
+    const float rho = p.L.rho, coef = first ? rho : 2.f * rho;
+    uint2 *XA = reinterpret_cast<uint2 *>(sm + S.XA);
+    for (int i = threadIdx.x; i < tl.count * 96; i += blockDim.x) {
+        const int tt = i / 96, e = i - 96 * tt, side = e / 48, k = e - 48 * side;
+        const int o = side * 24 + (k < 24 ? k : k - 24);
+        const int src = (cur * p.T + tt) * 48 + o;
+        float v;
+        if (k < 24) {
+            const float lam = sm[S.lam + src], R = rsum(sm, S, tt * 48 + o);
+            v = fmaf(coef, R, lam);
+            sm[S.lam + ((cur ^ 1) * p.T + tt) * 48 + o] = first ? lam : fmaf(rho, R, lam);
+        } else {
+            v = sm[S.xi1 + src];
+        }
+        st_split(XA + (side * S.T + tt) * 56 + k, v);
+    }
+}
+
+__device__ void xi1_mma(const KParams &p, float *sm, const Smem &S, const Tile &tl, int cur)
 {
     const ConstLayout &L = p.L;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane >> 2, tq = lane & 3;
-    const float rho = L.rho, coef = first ? rho : 2.f * rho;
     const bool valid = g < tl.count;
-    const int tt = valid ? g : 0;
-    const float *lam = sm + S.lam + (cur * p.T + tt) * 48;
-    const float *xi = sm + S.xi1 + (cur * p.T + tt) * 48;
-    const int rtt = tt * 48;
+    const int row = frag_row(g, tl.count);
+    const uint2 *XA = reinterpret_cast<const uint2 *>(sm + S.XA);
+    const uint2 *a_lo = XA + row * 56, *a_hi = XA + (S.T + row) * 56;
     for (int nt = warp; nt < 3; nt += blockDim.x >> 5) {
         const uint2 *brow = reinterpret_cast<const uint2 *>(sm + S.cst + L.off_xib2) + (nt * 8 + g) * 56;
         float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f}, d2[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int ks = 0; ks < 6; ++ks) {
-            const int k0 = ks * 8 + 2 * tq, k1 = k0 + 1;  // permuted k-step columns
-            float a[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int k = (e < 2) ? k0 : k1, side = e & 1;
-                const int o = side * 24 + (k < 24 ? k : k - 24);
-                a[e] = !valid ? 0.f : k < 24 ? fmaf(coef, rsum(sm, S, rtt + o), lam[o]) : xi[o];
-            }
-            uint2 b0, b1;
-            ld_pair2(brow + k0, b0, b1);
-            mma_asplit(d0, d1, d2, a, b0, b1);
+            const int c0 = ks * 8 + 2 * tq;  // permuted k-step columns
+            uint2 a[4], b0, b1;
+            ld_pair2(a_lo + c0, a[0], a[2]);
+            ld_pair2(a_hi + c0, a[1], a[3]);
+            ld_pair2(brow + c0, b0, b1);
+            mma_pairs<0>(d0, d1, d2, a, b0, b1);
         }
         if (valid) {
-            float *lam_n = sm + S.lam + ((cur ^ 1) * p.T + tt) * 48;
-            float *xi_n = sm + S.xi1 + ((cur ^ 1) * p.T + tt) * 48;
+            const float *xi = sm + S.xi1 + (cur * p.T + g) * 48;
+            float *xi_n = sm + S.xi1 + ((cur ^ 1) * p.T + g) * 48;
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int c = nt * 8 + 2 * tq + (e & 1);
                 if (c == NV || c == 23) continue;  // pads stay zero
                 const int o = (e >> 1) * 24 + c;
                 xi_n[o] = xi[o] + (d0[e] + d1[e] + d2[e]);
-                lam_n[o] = first ? lam[o] : fmaf(rho, rsum(sm, S, rtt + o), lam[o]);
             }
         }
     }
@@ -375,7 +408,9 @@ __device__ void phase_xi1(const KParams &p, float *sm, const Smem &S, const Tile
     const int ntask = n_xi + n_lp + n_sc;
     int base = 0;
     if (solve) {
-        xi1_mma(p, sm, S, tl, cur, first);
+        xi1_operand(p, sm, S, tl, cur, first);
+        __syncthreads();
+        xi1_mma(p, sm, S, tl, cur);
         if (int(blockDim.x) >= 96 + ntask) base = 96;
     }
     const int stride = int(blockDim.x) - base;
@@ -411,7 +446,7 @@ __device__ void phase_xi1(const KParams &p, float *sm, const Smem &S, const Tile
 #pragma unroll
             for (int c = 0; c < NV; ++c) a = fmaf(cst[L.off_ptp + c * 12 + k], dx2[c], a);
             float *lp = sm + S.lps + tt * 12;
-            lp[k] -= L.psi_sign * L.rho_psi * (a - (sm[S.ptp + tt * 12 + k] + sm[S.ptp + 96 + tt * 12 + k]));
+            lp[k] -= L.psi_sign * L.rho_psi * (a - psisum(sm, S.ptp, tt * 12 + k));
         } else {
             const int s = task - n_xi - n_lp, tt = s >> 2, w = s & 3;
             const float *gv = sm + S.GX + (tt * 4 + w) * L.qs;
@@ -466,45 +501,51 @@ __device__ void prepare_accumulators(const KParams &p, float *sm, const Smem &S,
 }
 
 // DOT phase on the tensor cores.  One 16-row tile: row = side*8 + trajectory.
-// Eight warp tasks: (segment rv | ra | r0 | r1, n-tile 0/1).  Each segment's
-// product goes to its own partial of R (rv, ra, r0 -> c_pos rows of partials
-// 0, 1, 2; r1 -> c_slack rows of partial 0), so no two tasks write one word.
+// Sixteen warp tasks: (segment rv | ra | r0 | r1, quarter of the steps), each
+// for both n-tiles of 8 output columns, so a task loads its A fragment once
+// (FP32, split here) for two products.  Each task writes its own partial of R
+// (rv, ra, r0 -> c_pos rows of partial 4 seg + quarter; r1 -> c_slack rows of
+// partial quarter), so no two tasks write one word.
 template <int PR>
 __device__ void phase_dot(const KParams &p, float *sm, const Smem &S, const Tile &tl)
 {
     const ConstLayout &L = p.L;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane >> 2, tq = lane & 3;
-    const int nks = (L.q + 7) >> 3;
-    const int row = frag_row(g, tl.count);
-    for (int task = warp; task < 8; task += blockDim.x >> 5) {
-        const int seg = task >> 1, nt = task & 1;
+    const int nks = (L.q + 7) >> 3, quarter = (nks + 3) >> 2;
+    const int row = frag_row4(g, tl.count);
+    for (int task = warp; task < 16; task += blockDim.x >> 5) {
+        const int seg = task >> 2, part = task & 3;
         const int bsel = seg == 0 ? 1 : seg == 1 ? 2 : 0;  // Pd, Pdd, P, P
-        const int k = nt * 8 + g;
-        // B columns past the 11 basis functions give discarded outputs: read
-        // a real column of the same parity instead of zeros
-        const uint2 *bcol = reinterpret_cast<const uint2 *>(sm + S.cst + L.off_pcol2) +
-                            (bsel * NV + (k < NV ? k : k - 8)) * L.qp;
-        const uint2 *G = reinterpret_cast<const uint2 *>(sm + S.G2);
-        const uint2 *a_lo = G + row * S.RS + seg * L.qp;
-        const uint2 *a_hi = G + (S.T + row) * S.RS + seg * L.qp;
+        const uint2 *B = reinterpret_cast<const uint2 *>(sm + S.cst + L.off_pcol2) + bsel * NV * L.qp;
+        // n-tile 1 holds columns 8..10; its other lanes give discarded
+        // outputs and read real columns of the same parity
+        const uint2 *bc0 = B + g * L.qp, *bc1 = B + (g < 3 ? 8 + g : g) * L.qp;
+        const float *a_lo = sm + S.G2 + row * S.RS + seg * L.qp;
+        const float *a_hi = sm + S.G2 + (S.T + row) * S.RS + seg * L.qp;
         float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f}, d2[4] = {0.f, 0.f, 0.f, 0.f};
+        float e0[4] = {0.f, 0.f, 0.f, 0.f}, e1[4] = {0.f, 0.f, 0.f, 0.f}, e2[4] = {0.f, 0.f, 0.f, 0.f};
+        const int k0 = part * quarter, k1 = min(nks, k0 + quarter);
 #pragma unroll 1
-        for (int ks = 0; ks < nks; ++ks) {
+        for (int ks = k0; ks < k1; ++ks) {
             const int c0 = ks * 8 + 2 * tq;
-            uint2 a[4], b0, b1;
-            ld_pair2(a_lo + c0, a[0], a[2]);
-            ld_pair2(a_hi + c0, a[1], a[3]);
-            ld_pair2(bcol + c0, b0, b1);
-            mma_pairs<PR>(d0, d1, d2, a, b0, b1);
+            const float2 lo = *reinterpret_cast<const float2 *>(a_lo + c0);
+            const float2 hi = *reinterpret_cast<const float2 *>(a_hi + c0);
+            const float a[4] = {lo.x, hi.x, lo.y, hi.y};
+            uint2 ap[4], b0, b1, b2, b3;
+            split4(a, ap);
+            ld_pair2(bc0 + c0, b0, b1);
+            ld_pair2(bc1 + c0, b2, b3);
+            mma_pairs<PR>(d0, d1, d2, ap, b0, b1);
+            mma_pairs<PR>(e0, e1, e2, ap, b2, b3);
         }
         if (g < tl.count) {
-            float *R = sm + S.rb + (seg < 3 ? seg : 0) * S.T * 48 + g * 48;
+            float *R = sm + S.rb + (seg < 3 ? 4 * seg + part : part) * S.T * 48 + g * 48;
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const int side = e >> 1, col = nt * 8 + 2 * tq + (e & 1);
-                if (col >= NV) continue;
-                R[24 * side + (seg < 3 ? col : 12 + col)] = d0[e] + d1[e] + d2[e];
+                const int side = e >> 1, c = 2 * tq + (e & 1);
+                R[24 * side + (seg < 3 ? c : 12 + c)] = d0[e] + d1[e] + d2[e];
+                if (c < 3) R[24 * side + (seg < 3 ? 8 + c : 20 + c)] = e0[e] + e1[e] + e2[e];
             }
         }
     }
@@ -512,18 +553,18 @@ __device__ void phase_dot(const KParams &p, float *sm, const Smem &S, const Tile
 
 // PSI phase on the tensor cores: W^T delta (cols 0..10) and P^T delta (cols
 // 11..21) per trajectory; rows 0..7 = trajectories, rows 8..15 are zero.
-// Six warp tasks: three n-tiles x two halves of the steps, each half into its
-// own partial.
+// Twelve warp tasks: three n-tiles x four quarters of the steps, each quarter
+// into its own partial.
 template <int PR>
 __device__ void phase_psi(const KParams &p, float *sm, const Smem &S, const Tile &tl)
 {
     const ConstLayout &L = p.L;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane >> 2, tq = lane & 3;
-    const int nks = (L.q + 7) >> 3, quarter = (nks + 1) >> 1;
-    const uint2 *arow = reinterpret_cast<const uint2 *>(sm + S.PS) + frag_row(g, tl.count) * L.qp;
+    const int nks = (L.q + 7) >> 3, quarter = (nks + kPsiParts - 1) / kPsiParts;
+    const float *arow = sm + S.PS + frag_row4(g, tl.count) * L.qp;
     const uint2 z = make_uint2(0u, 0u);
-    for (int task = warp; task < 6; task += blockDim.x >> 5) {
+    for (int task = warp; task < 3 * kPsiParts; task += blockDim.x >> 5) {
         const int nt = task % 3, part = task / 3;
         const int col = nt * 8 + g;
         // columns 22, 23 give discarded outputs: read columns of the same parity
@@ -534,8 +575,10 @@ __device__ void phase_psi(const KParams &p, float *sm, const Smem &S, const Tile
         const int k0 = part * quarter, k1 = min(nks, k0 + quarter);
         for (int ks = k0; ks < k1; ++ks) {
             const int c0 = ks * 8 + 2 * tq;
+            const float2 av = *reinterpret_cast<const float2 *>(arow + c0);
             uint2 a[4], b0, b1;
-            ld_pair2(arow + c0, a[0], a[2]);
+            split_tf32(av.x, a[0].x, a[0].y);
+            split_tf32(av.y, a[2].x, a[2].y);
             a[1] = z;
             a[3] = z;
             ld_pair2(bcol + c0, b0, b1);
@@ -697,19 +740,19 @@ __device__ __forceinline__ void sweep(float *sm, const Smem &S, const ConstLayou
         }
     }
     const int qs = L.qs;
-    uint2 *Gx = reinterpret_cast<uint2 *>(sm + S.G2) + tt * S.RS + t;   // side x: row tt
-    uint2 *Gy = Gx + S.T * S.RS;                                        // side y: row T + tt
+    float *Gx = sm + S.G2 + tt * S.RS + t;   // side x: row tt
+    float *Gy = Gx + S.T * S.RS;             // side y: row T + tt
     const float svm = sv - 1.f, sam = sa - 1.f;
     // v and a rows: projected value - F xi1 value
     const int qp = L.qp;
-    st_split(Gx, PRO ? fmaf(r.xd, svm, r.xd - ref.xd) : r.xd * svm);
-    st_split(Gx + qp, PRO ? fmaf(r.xdd, sam, r.xdd - ref.xdd) : r.xdd * sam);
-    st_split(Gx + 2 * qp, r0x);
-    st_split(Gx + 3 * qp, r1x + dcx);
-    st_split(Gy, PRO ? fmaf(r.yd, svm, r.yd - ref.yd) : r.yd * svm);
-    st_split(Gy + qp, PRO ? fmaf(r.ydd, sam, r.ydd - ref.ydd) : r.ydd * sam);
-    st_split(Gy + 2 * qp, r0y);
-    st_split(Gy + 3 * qp, r1y + dsy);
+    Gx[0] = PRO ? fmaf(r.xd, svm, r.xd - ref.xd) : r.xd * svm;
+    Gx[qp] = PRO ? fmaf(r.xdd, sam, r.xdd - ref.xdd) : r.xdd * sam;
+    Gx[2 * qp] = r0x;
+    Gx[3 * qp] = r1x + dcx;
+    Gy[0] = PRO ? fmaf(r.yd, svm, r.yd - ref.yd) : r.yd * svm;
+    Gy[qp] = PRO ? fmaf(r.ydd, sam, r.ydd - ref.ydd) : r.ydd * sam;
+    Gy[2 * qp] = r0y;
+    Gy[3 * qp] = r1y + dsy;
     float *GX = sm + S.GX + tt * 4 * qs + t;
     if (RES) {
         GX[0] = v2 * svm * svm + a2 * sam * sam + rob + dcx * dcx + dsy * dsy;
@@ -780,7 +823,7 @@ __device__ void run_tile(const KParams &p, float *sm, const Smem &S, const Tile 
         else if (e < 99) sm[S.lam + tt * 48 + ((e - 55) / NV) * 12 + (e - 55) % NV] = v;
         else sm[S.lps + tt * 12 + (e - 99)] = v;
     }
-    for (int i = threadIdx.x; i < 3 * p.T * 48; i += blockDim.x) sm[S.rb + i] = 0.f;
+    for (int i = threadIdx.x; i < kRParts * p.T * 48; i += blockDim.x) sm[S.rb + i] = 0.f;
     __syncthreads();
     // Reference xi1, xi2 into buffer 0: boundary control points from the
     // boundary conditions on every block that has boundary rows, the rest as given.
@@ -800,8 +843,9 @@ __device__ void run_tile(const KParams &p, float *sm, const Smem &S, const Tile 
     const bool stepper = tid < Tn * L.q;
     const int tt = stepper ? tid / L.q : 0;
     const int t = stepper ? tid - tt * L.q : 0;
-    float Prow[12];
-    load12(Prow, sm + S.cst + L.off_prow + t * 12);
+    // The thread's basis row P[t, :] is reloaded where it is used, so it does
+    // not occupy registers through the tensor-core phases.
+    const float *prow = sm + S.cst + L.off_prow + t * 12;
     StepRegs r;
     r.psi_t = 0.f;
     int cur = 0, cur2 = 0;
@@ -810,7 +854,8 @@ __device__ void run_tile(const KParams &p, float *sm, const Smem &S, const Tile 
     // residual against the reference.
     if (stepper) {
         StepRegs ref;
-        float x2[12];
+        float x2[12], Prow[12];
+        load12(Prow, prow);
         eval_xy(sm, S, L, sm + S.xi1 + (p.T + tt) * 48, t, Prow, r);
         eval_xy(sm, S, L, sm + S.xi1 + tt * 48, t, Prow, ref);
         load12(x2, sm + S.xi2 + (p.T + tt) * 12);
@@ -829,11 +874,13 @@ __device__ void run_tile(const KParams &p, float *sm, const Smem &S, const Tile 
         cur ^= 1;
         __syncthreads();
         if (stepper) {
+            float Prow[12];
+            load12(Prow, prow);
             eval_xy(sm, S, L, sm + S.xi1 + (cur * p.T + tt) * 48, t, Prow, r);
             // psi_t = psi + wrap(atan2(s, c) - psi), psi the previous heading;
             // the heading step works on delta = psi_t - P xi2
             r.psi_t = r.psi_prev + wrap_pi(atan2f(r.s, r.c) - r.psi_prev);
-            st_split(reinterpret_cast<uint2 *>(sm + S.PS) + tt * L.qp + t, r.psi_t - r.psi_cur);
+            sm[S.PS + tt * L.qp + t] = r.psi_t - r.psi_cur;
         }
         prepare_accumulators(p, sm, S, tl, cur2);
         __syncthreads();
@@ -844,9 +891,10 @@ __device__ void run_tile(const KParams &p, float *sm, const Smem &S, const Tile 
             float x2[12], w[12], b[12];
             load12(x2, sm + S.xi2 + (cur2 * p.T + tt) * 12);
             load12(w, sm + S.wdt + tt * 12);
-            {
+#pragma unroll
+            for (int part = 1; part < kPsiParts; ++part) {
                 float w1[12];
-                load12(w1, sm + S.wdt + 96 + tt * 12);
+                load12(w1, sm + S.wdt + part * kMaxTile * 12 + tt * 12);
 #pragma unroll
                 for (int c = 0; c < 12; ++c) w[c] += w1[c];
             }
@@ -864,6 +912,8 @@ __device__ void run_tile(const KParams &p, float *sm, const Smem &S, const Tile 
                     sm[S.dx2 + tt * 12 + c] = d2[c];
                 }
             }
+            float Prow[12];
+            load12(Prow, prow);
             sweep_dispatch<M, LIT>(sm, S, L, x2, tt, t, Prow, r, res, k == p.iters - 1);
         }
         cur2 ^= 1;
