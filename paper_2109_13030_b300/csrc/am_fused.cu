@@ -669,18 +669,10 @@ __device__ __forceinline__ void sweep(float *sm, const Smem &S, const ConstLayou
     const float4 *obc = reinterpret_cast<const float4 *>(cst + L.off_obc);
     const float *obt = cst + L.off_obt;
     const int n = L.n;
-    for (int j = 0; j < n; ++j) {
+    // One (circle, obstacle) pair of this step.
+    auto pair = [&](int j) {
         const float2 o = obs[j * L.qs + t];   // (x_j(t)/a_j, y_j(t)/b_j)
         const float4 c = obc[j];              // (1/a_j, 1/b_j, a_j, b_j)
-        if (!LIT && !FIN) {
-            // In the default alpha form the row correction of a circle outside
-            // the ellipse is exactly zero (max(1, 1/d) - 1 = 0).  When the robot
-            // centre is far enough that every circle is outside, the warp skips
-            // obstacle j unless one of its steps is near it.
-            const float u0 = fmaf(r.x, c.x, -o.x), v0 = fmaf(r.y, c.y, -o.y);
-            const bool near = fmaf(u0, u0, v0 * v0) < obt[j];
-            if (!__any_sync(__activemask(), near)) continue;
-        }
 #pragma unroll
         for (int i = 0; i < M; ++i) {
             const float xh = fmaf(X[i], c.x, -o.x);   // (x + r_i cos psi - x_j) / a_j
@@ -719,6 +711,34 @@ __device__ __forceinline__ void sweep(float *sm, const Smem &S, const ConstLayou
             }
             if (FIN) dmin = fminf(dmin, D);
         }
+    };
+    if (!LIT && !FIN) {
+        // In the default alpha form the row correction of a circle outside
+        // the ellipse is exactly zero (max(1, 1/d) - 1 = 0).  Every circle
+        // lies within r_max max(1/a, 1/b) of the robot centre in the
+        // ellipse-scaled frame, so obstacle j matters only when the centre is
+        // near it.  First pass: the obstacles near any step of the warp (one
+        // bit each); second pass: the pairs of those obstacles only.
+        const unsigned act = __activemask();
+        for (int j0 = 0; j0 < n; j0 += 32) {
+            const int jn = min(32, n - j0);
+            unsigned near = 0u;
+            for (int jj = 0; jj < jn; ++jj) {
+                const int j = j0 + jj;
+                const float2 o = obs[j * L.qs + t];
+                const float4 c = obc[j];
+                const float u0 = fmaf(r.x, c.x, -o.x), v0 = fmaf(r.y, c.y, -o.y);
+                near |= (fmaf(u0, u0, v0 * v0) < obt[j] ? 1u : 0u) << jj;
+            }
+            near = __reduce_or_sync(act, near);
+            while (near) {
+                const int jj = __ffs(near) - 1;
+                near &= near - 1u;
+                pair(j0 + jj);
+            }
+        }
+    } else {
+        for (int j = 0; j < n; ++j) pair(j);
     }
     // Obstacle rows: g_ij - (x + r_i c) = r_i (cos psi - c) + e_ij (+ x - x_ref in PRO)
     const float fn = float(n);
@@ -1100,8 +1120,6 @@ int launch_fused(const SolveArgs &a, void *stream, int *launches)
     if (smem > 227 * 1024) return -1;
     const int threads = (tq + 31) & ~31;
     const int ntiles = (a.B + T - 1) / T;
-    const int grid = ntiles < sms ? ntiles : sms;
-
     KParams p;
     p.cblob = a.cblob;
     p.L = L;
@@ -1118,6 +1136,9 @@ int launch_fused(const SolveArgs &a, void *stream, int *launches)
     p.err = a.err;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e;
+    // Persistent CTAs: as many as can be resident at once (one per SM for the
+    // large tiles; more when a smaller tile lets several share an SM).
+    int per_sm = 1, grid = 1;
     const int sel = (L.precision * 8 + (L.m - 1) * 2) + (L.alpha_mode ? 1 : 0);
     switch (sel) {
 #define AM_CASE(MM, LL, PP)                                                                   \
@@ -1125,6 +1146,10 @@ int launch_fused(const SolveArgs &a, void *stream, int *launches)
         e = cudaFuncSetAttribute(am_fused_kernel<MM, LL, PP>,                                 \
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));     \
         if (e != cudaSuccess) return -2;                                                      \
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, am_fused_kernel<MM, LL, PP>, \
+                                                          threads, smem);                     \
+        if (e != cudaSuccess || per_sm < 1) return -2;                                        \
+        grid = ntiles < sms * per_sm ? ntiles : sms * per_sm;                                 \
         am_fused_kernel<MM, LL, PP><<<grid, threads, smem, st>>>(p);                          \
         break;
 #define AM_CASES(PP)                                                                          \
