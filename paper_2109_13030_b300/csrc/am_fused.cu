@@ -51,12 +51,12 @@ namespace {
 constexpr int kMaxThreads = 768;
 constexpr int kMaxTile = 8;     // rows (side, trajectory) of one 16-row MMA tile
 constexpr int kRParts = 12;     // partials of R: (rv | ra | r0 segment) x quarter of the steps
-constexpr int kPsiParts = 4;    // partials of W^T delta, P^T delta: quarters of the steps
+
 constexpr float kTwoPi = 6.28318530717958647692f;
 constexpr float kPi = 3.14159265358979323846f;
 
 struct Smem {
-    int cst, xi1, lam, rb, xi2, dx2, lps, ptp, wdt, bas, G2, RS, GX, PS, XA, bar, total, T;
+    int cst, xi1, lam, rb, xi2, dx2, lps, ptp, bas, G2, RS, GX, PS, XA, bar, total, T;
 };
 
 // Shared-memory layout (float offsets).
@@ -66,7 +66,7 @@ struct Smem {
 //                          the c_slack rows in the first four (R is the sum of all)
 //   xi2       [2][T][12]   double-buffered c_psi;  dx2 [T][12] last increment
 //   lps       [T][12]      lambda_psi
-//   ptp, wdt  [4][8][12]   P^T delta, W^T delta: partials over four quarters of the steps
+//   ptp       [8][12]      P^T delta
 //   bas       [8][12]      Mpsi lam_psi - Mpsi H xi2
 //   G2        [2T][RS]     residual vectors, row = side*T + trajectory; segments
 //                          rv | ra | r0 | r1 of qp steps
@@ -89,8 +89,7 @@ __host__ __device__ inline Smem smem_layout(const ConstLayout &L, int T)
     s.xi2 = o; o += 2 * T * 12;
     s.dx2 = o; o += T * 12;
     s.lps = o; o += T * 12;
-    s.ptp = o; o += kPsiParts * kMaxTile * 12;
-    s.wdt = o; o += kPsiParts * kMaxTile * 12;
+    s.ptp = o; o += kMaxTile * 12;
     s.bas = o; o += kMaxTile * 12;
     // RS = 8 mod 32 and qp = 8 mod 16: the 64-bit fragment loads of four
     // neighbouring rows fall on distinct banks
@@ -114,14 +113,7 @@ __device__ __forceinline__ float rsum(const float *sm, const Smem &S, int i)
     return r;
 }
 
-// Sum of the kPsiParts partials of W^T delta or P^T delta, entry (tt, k).
-__device__ __forceinline__ float psisum(const float *sm, int base, int i)
-{
-    float r = 0.f;
-#pragma unroll
-    for (int k = 0; k < kPsiParts; ++k) r += sm[base + k * kMaxTile * 12 + i];
-    return r;
-}
+
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -446,7 +438,7 @@ __device__ void phase_xi1(const KParams &p, float *sm, const Smem &S, const Tile
 #pragma unroll
             for (int c = 0; c < NV; ++c) a = fmaf(cst[L.off_ptp + c * 12 + k], dx2[c], a);
             float *lp = sm + S.lps + tt * 12;
-            lp[k] -= L.psi_sign * L.rho_psi * (a - psisum(sm, S.ptp, tt * 12 + k));
+            lp[k] -= L.psi_sign * L.rho_psi * (a - sm[S.ptp + tt * 12 + k]);
         } else {
             const int s = task - n_xi - n_lp, tt = s >> 2, w = s & 3;
             const float *gv = sm + S.GX + (tt * 4 + w) * L.qs;
@@ -553,27 +545,28 @@ __device__ void phase_dot(const KParams &p, float *sm, const Smem &S, const Tile
 
 // PSI phase on the tensor cores: W^T delta (cols 0..10) and P^T delta (cols
 // 11..21) per trajectory; rows 0..7 = trajectories, rows 8..15 are zero.
-// Twelve warp tasks: three n-tiles x four quarters of the steps, each quarter
-// into its own partial.
+// Three warp tasks, one per n-tile, over all steps, so each output comes from
+// one lane, which also applies the heading step to its coefficient:
+//   xi2' = xi2 + (Mpsi lam_psi - Mpsi H xi2) + rho W^T delta
+// (the first bracket formed in the EVAL phase), writing xi2' and the increment.
 template <int PR>
-__device__ void phase_psi(const KParams &p, float *sm, const Smem &S, const Tile &tl)
+__device__ void phase_psi(const KParams &p, float *sm, const Smem &S, const Tile &tl, int cur2)
 {
     const ConstLayout &L = p.L;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane >> 2, tq = lane & 3;
-    const int nks = (L.q + 7) >> 3, quarter = (nks + kPsiParts - 1) / kPsiParts;
+    const int nks = (L.q + 7) >> 3;
     const float *arow = sm + S.PS + frag_row4(g, tl.count) * L.qp;
     const uint2 z = make_uint2(0u, 0u);
-    for (int task = warp; task < 3 * kPsiParts; task += blockDim.x >> 5) {
-        const int nt = task % 3, part = task / 3;
+    for (int nt = warp; nt < 3; nt += blockDim.x >> 5) {
         const int col = nt * 8 + g;
         // columns 22, 23 give discarded outputs: read columns of the same parity
         const uint2 *bcol = col < NV ? reinterpret_cast<const uint2 *>(sm + S.cst + L.off_wcol2) + col * L.qp
                                      : reinterpret_cast<const uint2 *>(sm + S.cst + L.off_pcol2) +
                                            (col < NS ? col - NV : col - NV - 8) * L.qp;
         float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f}, d2[4] = {0.f, 0.f, 0.f, 0.f};
-        const int k0 = part * quarter, k1 = min(nks, k0 + quarter);
-        for (int ks = k0; ks < k1; ++ks) {
+#pragma unroll 1
+        for (int ks = 0; ks < nks; ++ks) {
             const int c0 = ks * 8 + 2 * tq;
             const float2 av = *reinterpret_cast<const float2 *>(arow + c0);
             uint2 a[4], b0, b1;
@@ -589,8 +582,13 @@ __device__ void phase_psi(const KParams &p, float *sm, const Smem &S, const Tile
             for (int e = 0; e < 2; ++e) {
                 const int c = nt * 8 + 2 * tq + e;
                 const float v = d0[e] + d1[e] + d2[e];
-                if (c < NV) sm[S.wdt + part * 96 + g * 12 + c] = v;
-                else if (c < NS) sm[S.ptp + part * 96 + g * 12 + (c - NV)] = v;
+                if (c < NV) {
+                    const float d = fmaf(L.rho, v, sm[S.bas + g * 12 + c]);
+                    sm[S.xi2 + ((cur2 ^ 1) * p.T + g) * 12 + c] = sm[S.xi2 + (cur2 * p.T + g) * 12 + c] + d;
+                    sm[S.dx2 + g * 12 + c] = d;
+                } else if (c < NS) {
+                    sm[S.ptp + g * 12 + (c - NV)] = v;
+                }
             }
         }
     }
@@ -904,34 +902,11 @@ __device__ void run_tile(const KParams &p, float *sm, const Smem &S, const Tile 
         }
         prepare_accumulators(p, sm, S, tl, cur2);
         __syncthreads();
-        phase_psi<PR>(p, sm, S, tl);
+        phase_psi<PR>(p, sm, S, tl, cur2);
         __syncthreads();
         if (stepper) {
-            // xi2' = xi2 + (Mpsi lam_psi - Mpsi H xi2) + rho W^T delta
-            float x2[12], w[12], b[12];
-            load12(x2, sm + S.xi2 + (cur2 * p.T + tt) * 12);
-            load12(w, sm + S.wdt + tt * 12);
-#pragma unroll
-            for (int part = 1; part < kPsiParts; ++part) {
-                float w1[12];
-                load12(w1, sm + S.wdt + part * kMaxTile * 12 + tt * 12);
-#pragma unroll
-                for (int c = 0; c < 12; ++c) w[c] += w1[c];
-            }
-            load12(b, sm + S.bas + tt * 12);
-            float d2[12];
-#pragma unroll
-            for (int c = 0; c < 12; ++c) {
-                d2[c] = fmaf(L.rho, w[c], b[c]);
-                x2[c] += d2[c];
-            }
-            if (t == 0) {
-#pragma unroll
-                for (int c = 0; c < NV; ++c) {
-                    sm[S.xi2 + ((cur2 ^ 1) * p.T + tt) * 12 + c] = x2[c];
-                    sm[S.dx2 + tt * 12 + c] = d2[c];
-                }
-            }
+            float x2[12];
+            load12(x2, sm + S.xi2 + ((cur2 ^ 1) * p.T + tt) * 12);  // xi2' from the PSI phase
             float Prow[12];
             load12(Prow, prow);
             sweep_dispatch<M, LIT>(sm, S, L, x2, tt, t, Prow, r, res, k == p.iters - 1);
