@@ -387,7 +387,11 @@ int am_solve_batch(am_problem *h, int B, const float *init, const float *warm_la
         if (rc) return rc;
         rc = launch_plain(a, h->d_scratch, h->scratch_cap, h->stream, &h->launches);
     }
-    if (rc == -1) return fail(AM_ERR_ARG, "problem shape does not fit the kernel (tile %d)", h->tile);
+    if (rc == -1)
+        return fail(AM_ERR_ARG,
+                    "problem shape (q=%d, m=%d, n=%d, tile %d) does not fit the fused kernel's shared memory; "
+                    "the plain kernel (AM_OPT_KERNEL = AM_KERNEL_PLAIN) runs any shape",
+                    h->pp.q, h->pp.m, h->n, h->tile);
     if (rc) return fail(AM_ERR_CUDA, "solve launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     h->solved = true;
     return AM_OK;

@@ -190,6 +190,23 @@ def make_uneven(seed: int = 0, count: int = 64, scale: float = 1.0) -> list[dict
     return out
 
 
+def make_shape(seed: int, B: int, q: int, n: int, m: int) -> dict:
+    """A problem of an arbitrary shape (for edge cases: the largest horizons and
+    obstacle counts, single steps of the size range): q steps over q/10 s, n
+    moving ellipses as in ``paper``, m circles evenly spaced over
+    [-0.4, 0.4] m (0 m for m = 1), B initial samples as in ``paper``."""
+    rng = np.random.default_rng(seed)
+    T = q / 10.0
+    r = np.linspace(-0.4, 0.4, m) if m > 1 else np.zeros(1)
+    xo, yo, ao, bo = _moving_ellipses(rng, n, q, T)
+    x_bc, y_bc, psi_bc = _boundary()
+    init = _init_gaussian(rng, B, sigma_iid=None)
+    return dict(name=f"shape_q{q}_n{n}_m{m}", seed=seed, q=q, T=T, degree=DEGREE, m=m,
+                r=_f32(r), r_c=0.35, n=n, xo=xo, yo=yo, ao=ao, bo=bo,
+                v_max=2.0, a_max=2.0, rho=1.0, rho_psi=1.0,
+                x_bc=x_bc, y_bc=y_bc, psi_bc=psi_bc, B=B, init=init, iters=100)
+
+
 def with_obstacles_removed(pb: dict, v_max: float = 1e6, a_max: float = 1e6) -> dict:
     """Copy of a problem with no obstacles and (by default) inactive bounds."""
     out = dict(pb)
