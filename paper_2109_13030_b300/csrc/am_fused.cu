@@ -51,12 +51,13 @@ namespace {
 constexpr int kMaxThreads = 768;
 constexpr int kMaxTile = 8;     // rows (side, trajectory) of one 16-row MMA tile
 constexpr int kRParts = 12;     // partials of R: (rv | ra | r0 segment) x quarter of the steps
+constexpr int kPsiParts = 4;    // partials of W^T delta, P^T delta: quarters of the steps
 
 constexpr float kTwoPi = 6.28318530717958647692f;
 constexpr float kPi = 3.14159265358979323846f;
 
 struct Smem {
-    int cst, xi1, lam, rb, xi2, dx2, lps, ptp, bas, G2, RS, GX, PS, XA, bar, total, T;
+    int cst, xi1, lam, rb, xi2, dx2, lps, ptp, psp, bas, G2, RS, GX, PS, XA, bar, total, T;
 };
 
 // Shared-memory layout (float offsets).
@@ -67,6 +68,7 @@ struct Smem {
 //   xi2       [2][T][12]   double-buffered c_psi;  dx2 [T][12] last increment
 //   lps       [T][12]      lambda_psi
 //   ptp       [8][12]      P^T delta
+//   psp       [4][8][24]   partials of W^T delta (0..10) and P^T delta (12..22) per quarter
 //   bas       [8][12]      Mpsi lam_psi - Mpsi H xi2
 //   G2        [2T][RS]     residual vectors, row = side*T + trajectory; segments
 //                          rv | ra | r0 | r1 of qp steps
@@ -90,6 +92,7 @@ __host__ __device__ inline Smem smem_layout(const ConstLayout &L, int T)
     s.dx2 = o; o += T * 12;
     s.lps = o; o += T * 12;
     s.ptp = o; o += kMaxTile * 12;
+    s.psp = o; o += kPsiParts * kMaxTile * 24;
     s.bas = o; o += kMaxTile * 12;
     // RS = 8 mod 32 and qp = 8 mod 16: the 64-bit fragment loads of four
     // neighbouring rows fall on distinct banks
@@ -544,11 +547,27 @@ __device__ void phase_dot(const KParams &p, float *sm, const Smem &S, const Tile
 }
 
 // PSI phase on the tensor cores: W^T delta (cols 0..10) and P^T delta (cols
-// 11..21) per trajectory; rows 0..7 = trajectories, rows 8..15 are zero.
-// Three warp tasks, one per n-tile, over all steps, so each output comes from
-// one lane, which also applies the heading step to its coefficient:
+// 11..21) per trajectory; rows 0..7 = trajectories, rows 8..15 are zero.  The
+// heading step is then applied once per coefficient:
 //   xi2' = xi2 + (Mpsi lam_psi - Mpsi H xi2) + rho W^T delta
 // (the first bracket formed in the EVAL phase), writing xi2' and the increment.
+// With twelve or more warps: twelve tasks (three n-tiles x four quarters of
+// the steps) write partials, meet at a named barrier of those twelve warps,
+// and the first of them sum the partials and apply the step.  Smaller blocks:
+// three tasks (one per n-tile) over all steps, each applying the step to its
+// own outputs.
+__device__ __forceinline__ void psi_apply(const KParams &p, float *sm, const Smem &S, int g, int c,
+                                          float v, int cur2)
+{
+    if (c < NV) {
+        const float d = fmaf(p.L.rho, v, sm[S.bas + g * 12 + c]);
+        sm[S.xi2 + ((cur2 ^ 1) * p.T + g) * 12 + c] = sm[S.xi2 + (cur2 * p.T + g) * 12 + c] + d;
+        sm[S.dx2 + g * 12 + c] = d;
+    } else if (c < NS) {
+        sm[S.ptp + g * 12 + (c - NV)] = v;
+    }
+}
+
 template <int PR>
 __device__ void phase_psi(const KParams &p, float *sm, const Smem &S, const Tile &tl, int cur2)
 {
@@ -556,17 +575,21 @@ __device__ void phase_psi(const KParams &p, float *sm, const Smem &S, const Tile
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane >> 2, tq = lane & 3;
     const int nks = (L.q + 7) >> 3;
+    const bool split = (blockDim.x >> 5) >= 3 * kPsiParts;
+    const int ntask = split ? 3 * kPsiParts : 3, per = split ? (nks + kPsiParts - 1) / kPsiParts : nks;
     const float *arow = sm + S.PS + frag_row4(g, tl.count) * L.qp;
     const uint2 z = make_uint2(0u, 0u);
-    for (int nt = warp; nt < 3; nt += blockDim.x >> 5) {
+    if (warp < ntask) {
+        const int nt = warp % 3, part = warp / 3;
         const int col = nt * 8 + g;
         // columns 22, 23 give discarded outputs: read columns of the same parity
         const uint2 *bcol = col < NV ? reinterpret_cast<const uint2 *>(sm + S.cst + L.off_wcol2) + col * L.qp
                                      : reinterpret_cast<const uint2 *>(sm + S.cst + L.off_pcol2) +
                                            (col < NS ? col - NV : col - NV - 8) * L.qp;
         float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f}, d2[4] = {0.f, 0.f, 0.f, 0.f};
+        const int k0 = part * per, k1 = min(nks, k0 + per);
 #pragma unroll 1
-        for (int ks = 0; ks < nks; ++ks) {
+        for (int ks = k0; ks < k1; ++ks) {
             const int c0 = ks * 8 + 2 * tq;
             const float2 av = *reinterpret_cast<const float2 *>(arow + c0);
             uint2 a[4], b0, b1;
@@ -582,13 +605,22 @@ __device__ void phase_psi(const KParams &p, float *sm, const Smem &S, const Tile
             for (int e = 0; e < 2; ++e) {
                 const int c = nt * 8 + 2 * tq + e;
                 const float v = d0[e] + d1[e] + d2[e];
-                if (c < NV) {
-                    const float d = fmaf(L.rho, v, sm[S.bas + g * 12 + c]);
-                    sm[S.xi2 + ((cur2 ^ 1) * p.T + g) * 12 + c] = sm[S.xi2 + (cur2 * p.T + g) * 12 + c] + d;
-                    sm[S.dx2 + g * 12 + c] = d;
-                } else if (c < NS) {
-                    sm[S.ptp + g * 12 + (c - NV)] = v;
+                if (split) {
+                    if (c < NS) sm[S.psp + (part * kMaxTile + g) * 24 + (c < NV ? c : c + 1)] = v;
+                } else {
+                    psi_apply(p, sm, S, g, c, v, cur2);
                 }
+            }
+        }
+        if (split) {
+            // the twelve task warps only (barrier 0 is the block's)
+            asm volatile("bar.sync 1, %0;\n" :: "r"(32 * 3 * kPsiParts) : "memory");
+            for (int i = threadIdx.x; i < tl.count * NS; i += 32 * 3 * kPsiParts) {
+                const int tt = i / NS, c = i - NS * tt, o = c < NV ? c : c + 1;
+                float v = 0.f;
+#pragma unroll
+                for (int k = 0; k < kPsiParts; ++k) v += sm[S.psp + (k * kMaxTile + tt) * 24 + o];
+                psi_apply(p, sm, S, tt, c, v, cur2);
             }
         }
     }
