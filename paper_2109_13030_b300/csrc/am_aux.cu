@@ -49,10 +49,11 @@ __global__ void prep_obstacles_kernel(float *cblob, ConstLayout L, const float *
         // Every circle centre lies within r_max max(1/a, 1/b) of the robot
         // centre in the ellipse-scaled frame; a centre at squared distance
         // above this threshold (with a relative margin for rounding) has every
-        // circle outside the ellipse.
+        // circle outside the ellipse, and keeps that property while it moves
+        // by at most kNearMargin (m).
         float rmax = 0.f;
         for (int k = 0; k < L.m; ++k) rmax = fmaxf(rmax, fabsf(L.r[k]));
-        const float reach = fmaf(rmax, fmaxf(1.f / aj, 1.f / bj), 1.f);
+        const float reach = fmaf(rmax + kNearMargin, fmaxf(1.f / aj, 1.f / bj), 1.f);
         cblob[L.off_obt + i] = reach * reach * (1.f + 1e-4f) + 1e-6f;
     }
 }

@@ -57,7 +57,7 @@ constexpr float kTwoPi = 6.28318530717958647692f;
 constexpr float kPi = 3.14159265358979323846f;
 
 struct Smem {
-    int cst, xi1, lam, rb, xi2, dx2, lps, ptp, psp, bas, G2, RS, GX, PS, XA, bar, total, T;
+    int cst, xi1, lam, rb, xi2, dx2, lps, ptp, psp, bas, G2, RS, GX, PS, XA, NR, NM, bar, total, T;
 };
 
 // Shared-memory layout (float offsets).
@@ -76,6 +76,8 @@ struct Smem {
 //   PS        [T][qp]      delta = psi_t - P xi2 per trajectory
 //   XA        [2T][56][2]  A operand of the position step as TF32 pairs, row =
 //                          side*T + trajectory: lam + coef R (24) | xi1 (24)
+//   NR        [T*q][2]     robot centre of each step when its warp's near list was formed
+//   NM        [24][2]      near-obstacle bit lists per warp (obstacles 0..31, 32..63)
 // The constant block is staged from its offset off_fused on; cst is shifted so
 // that sm + cst + off_x addresses section x.
 __host__ __device__ inline Smem smem_layout(const ConstLayout &L, int T)
@@ -101,6 +103,8 @@ __host__ __device__ inline Smem smem_layout(const ConstLayout &L, int T)
     s.GX = o; o += T * 4 * L.qs;
     s.PS = o; o += T * L.qp;
     s.XA = o; o += 2 * T * 56 * 2;
+    s.NR = o; o += 2 * T * L.q;
+    s.NM = o; o += 24 * 2;
     o = (o + 3) & ~3;
     s.total = o;
     return s;
@@ -747,20 +751,34 @@ __device__ __forceinline__ void sweep(float *sm, const Smem &S, const ConstLayou
         // the ellipse is exactly zero (max(1, 1/d) - 1 = 0).  Every circle
         // lies within r_max max(1/a, 1/b) of the robot centre in the
         // ellipse-scaled frame, so obstacle j matters only when the centre is
-        // near it.  First pass: the obstacles near any step of the warp (one
-        // bit each); second pass: the pairs of those obstacles only.
+        // near it.  The warp keeps the list of obstacles near any of its steps
+        // (formed with a threshold widened by kNearMargin) and forms it again
+        // only when one of its centres has moved farther than the margin;
+        // then only the pairs of listed obstacles are visited.
         const unsigned act = __activemask();
-        for (int j0 = 0; j0 < n; j0 += 32) {
-            const int jn = min(32, n - j0);
-            unsigned near = 0u;
-            for (int jj = 0; jj < jn; ++jj) {
-                const int j = j0 + jj;
-                const float2 o = obs[j * L.qs + t];
-                const float4 c = obc[j];
-                const float u0 = fmaf(r.x, c.x, -o.x), v0 = fmaf(r.y, c.y, -o.y);
-                near |= (fmaf(u0, u0, v0 * v0) < obt[j] ? 1u : 0u) << jj;
+        float2 *ref = reinterpret_cast<float2 *>(sm + S.NR) + tt * L.q + t;
+        unsigned *list = reinterpret_cast<unsigned *>(sm + S.NM) + 2 * (threadIdx.x >> 5);
+        const float2 c0 = *ref;
+        const float mx = r.x - c0.x, my = r.y - c0.y;
+        if (__any_sync(act, fmaf(mx, mx, my * my) > kNearMargin * kNearMargin)) {
+            for (int j0 = 0; j0 < n; j0 += 32) {
+                const int jn = min(32, n - j0);
+                unsigned near = 0u;
+                for (int jj = 0; jj < jn; ++jj) {
+                    const int j = j0 + jj;
+                    const float2 o = obs[j * L.qs + t];
+                    const float4 c = obc[j];
+                    const float u0 = fmaf(r.x, c.x, -o.x), v0 = fmaf(r.y, c.y, -o.y);
+                    near |= (fmaf(u0, u0, v0 * v0) < obt[j] ? 1u : 0u) << jj;
+                }
+                near = __reduce_or_sync(act, near);
+                if ((threadIdx.x & 31) == 0) list[j0 >> 5] = near;
             }
-            near = __reduce_or_sync(act, near);
+            *ref = make_float2(r.x, r.y);
+            __syncwarp(act);
+        }
+        for (int j0 = 0; j0 < n; j0 += 32) {
+            unsigned near = list[j0 >> 5];
             while (near) {
                 const int jj = __ffs(near) - 1;
                 near &= near - 1u;
@@ -874,6 +892,8 @@ __device__ void run_tile(const KParams &p, float *sm, const Smem &S, const Tile 
         else sm[S.lps + tt * 12 + (e - 99)] = v;
     }
     for (int i = threadIdx.x; i < kRParts * p.T * 48; i += blockDim.x) sm[S.rb + i] = 0.f;
+    // no near lists yet: a reference far away makes every warp form its list
+    for (int i = threadIdx.x; i < 2 * p.T * L.q; i += blockDim.x) sm[S.NR + i] = 3.0e18f;
     __syncthreads();
     // Reference xi1, xi2 into buffer 0: boundary control points from the
     // boundary conditions on every block that has boundary rows, the rest as given.

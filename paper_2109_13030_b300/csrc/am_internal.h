@@ -83,7 +83,7 @@ struct ConstLayout {
     int off_kbpsi;            // [12]
     int off_obs;              // [n][qs][2]   (x_j(t)/a_j, y_j(t)/b_j) pairs
     int off_obc;              // [n][4]       1/a_j, 1/b_j, a_j, b_j (inflated)
-    int off_obt;              // [n]          near threshold (1 + r_max max(1/a_j, 1/b_j))^2
+    int off_obt;              // [n]          near threshold (1 + (r_max + margin) max(1/a_j, 1/b_j))^2
     int total;                // floats, multiple of 4
     float rho, rho_psi, v_max, a_max;
     float r[MAXM];
@@ -124,6 +124,11 @@ struct FusedProblem {
     float *state, *res, *res_psi, *cost, *mind, *hist;
     int *err;
 };
+
+// World-space margin (m) of the near-obstacle test: a warp's list of
+// obstacles near its steps stays valid until one of its robot centres has
+// moved farther than this since the list was formed.
+constexpr float kNearMargin = 0.25f;
 
 // Grouped launch: many problems' tiles in persistent kernels, one kernel per
 // variant (circle count, alpha form) present; the variant kernels of one
