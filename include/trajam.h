@@ -128,7 +128,11 @@ AM_API int am_get_results(am_problem *h, float *res, float *res_psi, float *cost
 /* The best trajectory of the last solve: lowest cost among those whose
  * smallest ellipse distance is >= 0.99, else lowest cost overall; ties go to
  * the lower index (Fig. 1's best-cost trajectory).  coeffs gets c_x, c_y,
- * c_psi (33 floats, host memory). */
+ * c_psi (33 floats, host memory).  Trajectories with a non-finite cost rank
+ * last; when every one is non-finite the outputs are filled and the call
+ * returns AM_ERR_NAN.  (Host inputs with a non-finite value are refused with
+ * AM_ERR_ARG by am_set_obstacles and am_solve_batch; device inputs are not
+ * scanned.) */
 AM_API int am_get_best(am_problem *h, float coeffs[33], float *cost, float *residual, int *index);
 
 /* Copy the B x AM_STATE_FLOATS state out of / into the handle. */
@@ -141,9 +145,16 @@ AM_API int am_set_history(am_problem *h, int enable);
 AM_API int am_get_history(am_problem *h, float *out, int mem);
 
 /* Options.  AM_OPT_KERNEL: AM_KERNEL_FUSED or AM_KERNEL_PLAIN.
- * AM_OPT_TILE: trajectories per CTA of the fused kernel (0 = automatic). */
+ * AM_OPT_TILE: trajectories per CTA of the fused kernel (0 = automatic).
+ * AM_OPT_DIAG_STALL: diagnostic for failure-detection tests (no counterpart
+ * in the paper).  While set, the fused kernel stages its constants without
+ * issuing the copy, so its bounded device-side wait (about one second) runs
+ * out; the kernel then records the failure in the handle's status word and
+ * returns, the getters report AM_ERR_TIMEOUT, and the results are undefined.
+ * The next solve after clearing it resets the status word. */
 #define AM_OPT_KERNEL 1
 #define AM_OPT_TILE 2
+#define AM_OPT_DIAG_STALL 3
 AM_API int am_set_option(am_problem *h, int option, int value);
 
 /* Stream used by calls that take none (am_set_obstacles, am_set_boundary,

@@ -87,6 +87,7 @@ struct am_problem {
     cudaEvent_t ev = nullptr;
     int launches = 0;
     bool solved = false;
+    int diag_stall = 0;
     float *h_best = nullptr;  // pinned
 };
 
@@ -127,6 +128,13 @@ bool finite_all(const double *v, int n)
     return true;
 }
 
+bool finite_floats(const float *v, size_t n)
+{
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
 // Uploads the non-obstacle sections of the constant block.
 int upload_shape_sections(am_problem *h)
 {
@@ -140,6 +148,7 @@ int upload_shape_sections(am_problem *h)
 void set_scalars(am_problem *h)
 {
     ConstLayout &L = h->L;
+    L.diag_stall = h->diag_stall;
     L.rho = float(h->pp.rho);
     L.rho_psi = float(h->pp.rho_psi);
     L.v_max = float(h->pp.v_max);
@@ -271,10 +280,13 @@ int am_set_obstacles(am_problem *h, int n, const float *xo, const float *yo, con
     if (n > 0 && (!xo || !yo || !a || !b)) return fail(AM_ERR_ARG, "null obstacle array");
     if (mem != AM_HOST && mem != AM_DEVICE) return fail(AM_ERR_ARG, "bad mem flag");
     const int q = h->pp.q;
-    if (mem == AM_HOST)
+    if (mem == AM_HOST) {
         for (int j = 0; j < n; ++j)
             if (!(a[j] > 0) || !(b[j] > 0) || !std::isfinite(a[j]) || !std::isfinite(b[j]))
                 return fail(AM_ERR_ARG, "semi-axes must be finite and > 0");
+        if (n > 0 && (!finite_floats(xo, size_t(n) * q) || !finite_floats(yo, size_t(n) * q)))
+            return fail(AM_ERR_ARG, "non-finite obstacle track");
+    }
     int rc;
     if (n != h->n) {
         rc = reshape(h, n);
@@ -320,6 +332,11 @@ int am_set_option(am_problem *h, int option, int value)
         h->tile = value;
         return AM_OK;
     }
+    if (option == AM_OPT_DIAG_STALL) {
+        h->diag_stall = value != 0;
+        h->L.diag_stall = h->diag_stall;
+        return AM_OK;
+    }
     return fail(AM_ERR_ARG, "unknown option %d", option);
 }
 
@@ -333,6 +350,7 @@ int am_set_history(am_problem *h, int enable)
 int am_solve_batch(am_problem *h, int B, const float *init, const float *warm_lambda, int iters,
                    void *stream, int mem)
 {
+    NvtxRange range("am_solve_batch");
     if (!h) return fail(AM_ERR_ARG, "null handle");
     if (B < 1 || B > (1 << 24)) return fail(AM_ERR_ARG, "B must be in [1, 2^24]");
     if (iters < 1 || iters > 100000) return fail(AM_ERR_ARG, "iters must be in [1, 100000]");
@@ -342,10 +360,15 @@ int am_solve_batch(am_problem *h, int B, const float *init, const float *warm_la
     if (!init && warm_lambda) return fail(AM_ERR_ARG, "warm_lambda needs init");
     if (h->kernel == AM_KERNEL_PLAIN && h->pp.precision != AM_FP32)
         return fail(AM_ERR_ARG, "reduced precision runs on the fused kernel only");
+    if (mem == AM_HOST) {
+        if (init && !finite_floats(init, size_t(B) * 33)) return fail(AM_ERR_ARG, "non-finite initial coefficients");
+        if (warm_lambda && !finite_floats(warm_lambda, size_t(B) * 55)) return fail(AM_ERR_ARG, "non-finite warm multipliers");
+    }
     h->stream = static_cast<cudaStream_t>(stream);
     h->launches = 0;
     int rc = check_B(h, B);
     if (rc) return rc;
+    CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream), "status reset");
     if (init) {
         CK(cudaMemcpyAsync(h->d_in, init, sizeof(float) * 33 * B, kind_in(mem), h->stream), "init copy");
         const float *warm = nullptr;
@@ -426,6 +449,8 @@ int am_get_best(am_problem *h, float coeffs[33], float *cost, float *residual, i
     if (cost) *cost = h->h_best[1];
     if (residual) *residual = h->h_best[2];
     if (coeffs) std::memcpy(coeffs, h->h_best + 3, 33 * sizeof(float));
+    // non-finite trajectories rank last, so a non-finite best means all are
+    if (!std::isfinite(h->h_best[1])) return fail(AM_ERR_NAN, "every trajectory of the batch is non-finite");
     return AM_OK;
 }
 
@@ -791,6 +816,7 @@ int am_init_state(am_problem *h, int B, const float *init, const float *warm_lam
     if (launch_init_state(h->d_state, h->d_in, warm, B, h->stream, nullptr))
         return fail(AM_ERR_CUDA, "init launch failed");
     CK(cudaMemsetAsync(h->d_out, 0, sizeof(float) * 4 * B, h->stream), "memset");
+    CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream), "status reset");
     h->B = B;
     h->solved = true;
     return AM_OK;
@@ -877,6 +903,7 @@ int am_group_set_active(am_group *g, const int *idx, int count)
 
 int am_group_solve(am_group *g, int iters, void *stream)
 {
+    NvtxRange range("am_group_solve");
     if (!g) return fail(AM_ERR_ARG, "null group");
     if (iters < 1 || iters > 100000) return fail(AM_ERR_ARG, "iters must be in [1, 100000]");
     const std::vector<int> act = active_list(g);

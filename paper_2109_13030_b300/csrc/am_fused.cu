@@ -136,6 +136,17 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
         : "memory");
 }
 
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Limit of the device-side wait for the constant copy: about a second of
+// the global timer (and an iteration cap behind it).
+constexpr uint64_t kWaitLimitNs = 1000000000ull;
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 {
     uint32_t ok;
@@ -882,11 +893,15 @@ __device__ bool stage_constants(const KParams &p, float *sm, const Smem &S, uint
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n"
                      :: "r"(smem_u32(bar)), "r"(bytes) : "memory");
-        bulk_load(sm + S.cst + p.L.off_fused, p.cblob + p.L.off_fused, bytes, bar);
+        if (!p.L.diag_stall) bulk_load(sm + S.cst + p.L.off_fused, p.cblob + p.L.off_fused, bytes, bar);
     }
     for (int i = S.xi1 + threadIdx.x; i < S.total; i += blockDim.x) sm[i] = 0.f;
     int ok = 0;
-    for (int spin = 0; spin < (1 << 24) && !ok; ++spin) ok = mbar_try_wait(bar, parity) ? 1 : 0;
+    const uint64_t t0 = global_ns();
+    for (int spin = 0; spin < (1 << 26) && !ok; ++spin) {
+        ok = mbar_try_wait(bar, parity) ? 1 : 0;
+        if (!ok && global_ns() - t0 > kWaitLimitNs) break;
+    }
     return __syncthreads_and(ok) != 0;
 }
 
@@ -1109,7 +1124,8 @@ int launch_group(const GroupLaunch &g, void *stream, int *launches, const char *
         g.variant < 0 || g.variant >= kGroupVariants)
         return -1;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    cudaError_t e = cudaMemsetAsync(g.d_ctl + 2 * g.variant, 0, sizeof(int), st);
+    // the variant's work counter and status word start at zero every solve
+    cudaError_t e = cudaMemsetAsync(g.d_ctl + 2 * g.variant, 0, 2 * sizeof(int), st);
     if (e != cudaSuccess) {
         *why = cudaGetErrorString(e);
         return -2;

@@ -5,9 +5,20 @@
 #include <cstdint>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 struct am_problem;
 
 namespace trajam {
+
+// NVTX range for the duration of a scope (solves, group solves, server
+// rounds); free unless a profiler attaches.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 constexpr int NV = 11;        // coefficients per polynomial (degree 10)
 constexpr int NS = 22;        // unknowns per side: (c_pos, c_slack)
@@ -92,6 +103,8 @@ struct ConstLayout {
     int cs_boundary;          // slack blocks carry boundary rows
     int precision;            // contractions over the time grid: 0 FP32 (three TF32
                               // products), 1 one TF32 product, 2 one BF16 product
+    int diag_stall;           // diagnostic: stage without the copy, so the bounded
+                              // wait on it runs out (failure-detection tests)
 };
 
 ConstLayout make_layout(int q, int m, int n);

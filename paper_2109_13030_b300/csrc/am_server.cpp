@@ -165,7 +165,11 @@ void worker_main(am_server *s)
             }
         }
         const double t_start = now_s();
-        const int rc = serve_round(s, batch);
+        int rc;
+        {
+            NvtxRange range("am_server round");
+            rc = serve_round(s, batch);
+        }
         const double t_done = now_s();
         std::lock_guard<std::mutex> lk(s->mu);
         for (size_t k = 0; k < batch.size(); ++k) {

@@ -19,7 +19,7 @@ AM_OK, AM_ERR_ARG, AM_ERR_CUDA, AM_ERR_BUDGET, AM_ERR_TIMEOUT, AM_ERR_NAN, AM_ER
 AM_HOST, AM_DEVICE = 0, 1
 AM_FP32, AM_TF32, AM_BF16 = 0, 1, 2
 AM_KERNEL_FUSED, AM_KERNEL_PLAIN = 0, 1
-AM_OPT_KERNEL, AM_OPT_TILE = 1, 2
+AM_OPT_KERNEL, AM_OPT_TILE, AM_OPT_DIAG_STALL = 1, 2, 3
 AM_GOPT_THREADS, AM_GOPT_GRAPH = 1, 2
 AM_PENDING = 1
 AM_SRV_BATCHED, AM_SRV_SEQUENTIAL = 0, 1
