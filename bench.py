@@ -27,7 +27,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "trajectory-AM-iterations/sec at batch 1000"
+METRIC = "trajectory-AM-iterations/sec at batch 1000; p50/p99 re-plan latency vs plain GPU"
 UNIT = "trajectory-iterations/s"
 WORKLOAD = "paper"
 B, ITERS = 1000, 100
@@ -363,6 +363,9 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=3)
     ap.add_argument("--uneven-steps", type=int, default=3)
     ap.add_argument("--precision-steps", type=int, default=3)
+    ap.add_argument("--profile-plain", type=int, default=0, metavar="B",
+                    help="profiling aid: solve 2 iterations of the paper-shaped scene at batch B with the "
+                         "plain loop and exit (no JSON line)")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-plain-seconds", type=float, default=2.0)
     args = ap.parse_args()
@@ -373,6 +376,15 @@ def main():
 
     import torch
     from paper_2109_13030_b300 import trajam as TJ, workload as W
+
+    if args.profile_plain > 0:
+        pb = W.make_problem(WORKLOAD, 0, B=args.profile_plain)
+        P = TJ.Problem(pb, kernel=TJ.AM_KERNEL_PLAIN)
+        P.solve(torch.tensor(pb["init"], dtype=torch.float32, device="cuda"), 2,
+                stream=torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        P.close()
+        return 0
 
     rank, world, local = dist_env()
     dist = None

@@ -486,15 +486,15 @@ __device__ void phase_xi1(const KParams &p, float *sm, const Smem &S, const Tile
             const float *gv = sm + S.GX + (tt * 4 + w) * L.qs;
             float v;
             if (w < 3) {
+                // the reductions over the steps of the residuals and the cost
+                // accumulate in FP64 (q terms of similar size each)
                 const float4 *g = reinterpret_cast<const float4 *>(gv);
-                float a0 = 0.f, a1 = 0.f;
+                double acc = 0.0;
                 for (int i = 0; i < L.qs / 4; ++i) {  // padding past q is zero
                     const float4 x = g[i];
-                    a0 += x.x + x.y;
-                    a1 += x.z + x.w;
+                    acc += (double(x.x) + double(x.y)) + (double(x.z) + double(x.w));
                 }
-                v = a0 + a1;
-                if (w < 2) v = sqrtf(v);
+                v = float(w < 2 ? sqrt(acc) : acc);
             } else {
                 if (!final_out) continue;
                 float mn = 3.0e38f;

@@ -353,15 +353,16 @@ __global__ void k_scalars(ConstLayout L, PlainBufs b, int B, float *res, float *
     if (l >= B) return;
     const int q = L.q;
     const float *G = b.gv + size_t(l) * 12 * q;
-    float r = 0, rp = 0, c = 0, dm = 3.0e38f;
+    // reductions over the steps in FP64, as in the fused kernel
+    double r2 = 0, rp2 = 0, c2 = 0;
+    float dm = 3.0e38f;
     for (int t = 0; t < q; ++t) {
-        r += G[8 * q + t];
-        rp += G[9 * q + t];
-        c += G[10 * q + t];
+        r2 += G[8 * q + t];
+        rp2 += G[9 * q + t];
+        c2 += G[10 * q + t];
         dm = fminf(dm, G[11 * q + t]);
     }
-    r = sqrtf(r);
-    rp = sqrtf(rp);
+    const float r = float(sqrt(r2)), rp = float(sqrt(rp2)), c = float(c2);
     if (hist) {
         hist[(size_t(l) * iters + k) * 3 + 0] = r;
         hist[(size_t(l) * iters + k) * 3 + 1] = rp;

@@ -338,7 +338,7 @@ def test_errors_are_reported():
     with pytest.raises(T.TrajamError) as e:
         T.am_set_obstacles(P.h, 65, np.zeros((65, 50)), np.zeros((65, 50)), np.ones(65), np.ones(65))
     assert e.value.code == T.AM_ERR_ARG
-    big = dict(pb, q=256, T=25.6)
+    big = dict(pb, q=256, T=25.6, n=0)   # tracks set below, at the new horizon
     Q = T.Problem(big)
     Q.set_obstacles(np.zeros((64, 256)), np.zeros((64, 256)), np.ones(64), np.ones(64))
     with pytest.raises(T.TrajamError) as e:
