@@ -497,7 +497,9 @@ def main():
         torch.cuda.synchronize()
         plain_ms.append(e0.elapsed_time(e1))
     plain_launches = TJ.am_last_solve_stats(Pp.h)
+    plain_res = float(np.median(Pp.results()["res"]))
     Pp.close()
+    fused_res = float(np.median(outs[0].numpy()))
 
     if rank == 0:
         line = {
@@ -524,7 +526,9 @@ def main():
             "clocks": clocks,
             "comparators": {"plain_fp32_loop": {"value": B * ITERS / (statistics.mean(plain_ms) / 1e3),
                                                 "unit": UNIT, "ms_per_solve": statistics.mean(plain_ms),
-                                                "launches_per_solve": plain_launches}},
+                                                "launches_per_solve": plain_launches,
+                                                "final_residual_median": plain_res}},
+            "final_residual_median": fused_res,
         }
         if args.uneven_steps > 0:
             line["uneven"] = bench_uneven(TJ, W, torch, dev, flush, args.uneven_steps)
