@@ -313,6 +313,16 @@ def bench_serving(TJ, W, seconds: float, plain_seconds: float) -> dict:
     out["sequential_fused"] = serve_run(TJ, W, pbs, TJ.AM_SRV_SEQUENTIAL, TJ.AM_KERNEL_FUSED, seconds)
     out["sequential_plain_fp32_loop"] = serve_run(TJ, W, pbs, TJ.AM_SRV_SEQUENTIAL, TJ.AM_KERNEL_PLAIN,
                                                   plain_seconds)
+    # a heavier load, where requests arrive while others are on the GPU and
+    # rounds of continuous batching hold several of them
+    hi_rate = 2500.0
+    out["high_load"] = {
+        "offered_per_s": hi_rate,
+        "batched": serve_run(TJ, W, pbs, TJ.AM_SRV_BATCHED, TJ.AM_KERNEL_FUSED, plain_seconds * 1.5,
+                             warmup_s=0.5, rate=hi_rate),
+        "sequential_fused": serve_run(TJ, W, pbs, TJ.AM_SRV_SEQUENTIAL, TJ.AM_KERNEL_FUSED,
+                                      plain_seconds * 1.5, warmup_s=0.5, rate=hi_rate),
+    }
     return out
 
 
