@@ -373,6 +373,7 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=3)
     ap.add_argument("--uneven-steps", type=int, default=3)
     ap.add_argument("--precision-steps", type=int, default=3)
+    ap.add_argument("--jsonl", default=None, help="also append the JSON line to this file")
     ap.add_argument("--profile-plain", type=int, default=0, metavar="B",
                     help="profiling aid: solve 2 iterations of the paper-shaped scene at batch B with the "
                          "plain loop and exit (no JSON line)")
@@ -549,6 +550,9 @@ def main():
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(pb, B, ITERS)
         print(json.dumps(line), flush=True)
+        if args.jsonl:
+            with open(args.jsonl, "a") as f:
+                f.write(json.dumps(dict(line, seed=0, when=time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime()))) + "\n")
     P.close()
     if dist:
         dist.destroy_process_group()

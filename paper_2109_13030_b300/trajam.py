@@ -375,7 +375,8 @@ class Problem:
                  kernel=AM_KERNEL_FUSED, tile=0):
         self.desc = make_desc(pb, precision, alpha_mode, psi_dual_sign, cs_boundary)
         self.h = am_init_problem(self.desc)
-        self.q = int(pb["q"])
+        self.q, self.m, self.n = int(pb["q"]), int(pb["m"]), int(pb["n"])
+        self.precision = int(precision)
         self.B = 0
         self.iters = 0
         am_set_option(self.h, AM_OPT_KERNEL, kernel)
@@ -443,8 +444,22 @@ class Group:
             p.iters = iters
         return self
 
-    def autotune(self, iters, stream=None):
-        return am_group_autotune(self.g, iters, stream)
+    def autotune(self, iters, stream=None, cache=None, sms=0):
+        """Time the block sizes and keep the fastest; with cache (a JSON path),
+        reuse a choice stored for the same shapes, precision, SM count and
+        iterations (sms: the device's SM count, part of the key)."""
+        if cache is None:
+            return am_group_autotune(self.g, iters, stream)
+        from . import tune_cache
+        k = tune_cache.key([(p.q, p.m, p.n, p.B) for p in self.problems],
+                           self.problems[0].precision, sms, iters)
+        hit = tune_cache.lookup(cache, k)
+        if hit is not None:
+            am_group_set_option(self.g, AM_GOPT_THREADS, hit[0])
+            return hit
+        threads, ms = am_group_autotune(self.g, iters, stream)
+        tune_cache.store(cache, k, threads, ms)
+        return threads, ms
 
     def stats(self):
         return am_group_stats(self.g)

@@ -164,6 +164,29 @@ def test_group_autotune_restores_state():
         P.close()
 
 
+def test_group_autotune_cache(tmp_path):
+    """A stored choice is reused for a group of the same key without timing."""
+    T = tj()
+    pbs = mix(count=3, seed=19)
+    cache = str(tmp_path / "tune.json")
+    probs = [T.Problem(pb).init_state(pb["init"].astype(np.float32)) for pb in pbs]
+    G = T.Group(probs)
+    threads, ms = G.autotune(10, cache=cache, sms=148)
+    G.close()
+    from paper_2109_13030_b300 import tune_cache
+    k = tune_cache.key([(pb["q"], pb["m"], pb["n"], pb["B"]) for pb in pbs], 0, 148, 10)
+    assert tune_cache.lookup(cache, k) == (threads, ms)
+    tune_cache.store(cache, k, 512, 0.5)
+    G = T.Group(probs)
+    assert G.autotune(10, cache=cache, sms=148) == (512, 0.5)
+    G.solve(10)
+    for pb, P in zip(pbs, probs):
+        check_oracle(pb, split_all(P))
+    G.close()
+    for P in probs:
+        P.close()
+
+
 def test_group_best_and_results_per_problem():
     pbs = mix(count=3, seed=17)
     T = tj()
