@@ -326,6 +326,34 @@ def bench_serving(TJ, W, seconds: float, plain_seconds: float) -> dict:
     return out
 
 
+def bench_closed_loop(episodes: int, batches=(1, 200, 1000)) -> dict:
+    """Closed-loop MPC on the crowd benchmarks of Sec. IV (Table III's
+    metrics against batch size): `episodes` scenes per benchmark (static,
+    same-direction, opposite flow), 20 s at 10 Hz, 10 iterations per re-plan,
+    all episodes served together by one re-planning server."""
+    from paper_2109_13030_b300 import mpc as M
+    from paper_2109_13030_b300 import workload as W
+    crowds = [W.make_crowd(k, s) for k in W.CROWD_KINDS for s in range(episodes)]
+    cfg = M.MPCConfig()
+    out = {"workload": f"{len(crowds)} synthetic crowd episodes ({episodes} per benchmark: static, same-direction "
+                       "flow <= 0.3 m/s, opposite flow <= 1.0 m/s; 30 people of radius 0.3 m in a 10 m band), "
+                       "robot of 3 circles tracking (t m/s, 0), 20 s at 10 Hz",
+           "config": {"iters_per_replan": cfg.iters, "horizon_s": cfg.horizon, "q": cfg.q,
+                      "planning_margin_m": cfg.margin, "warm_start": "xi and lambda kept between steps",
+                      "fallback": "most clearance"},
+           "by_batch": {}}
+    for batch in batches:
+        r = M.run(crowds, M.MPCConfig(batch=batch))
+        row = M.summarize(r["episodes"])
+        row["by_benchmark_success"] = {k: M.summarize([e for e in r["episodes"] if e["kind"] == k])["success_rate"]
+                                       for k in W.CROWD_KINDS}
+        row["replan_ms"] = r["replan_ms"]
+        row["control_steps"] = r["steps"]
+        row["loop_wall_s"] = r["wall_s"]
+        out["by_batch"][str(batch)] = row
+    return out
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -374,6 +402,7 @@ def main():
     ap.add_argument("--uneven-steps", type=int, default=3)
     ap.add_argument("--precision-steps", type=int, default=3)
     ap.add_argument("--jsonl", default=None, help="also append the JSON line to this file")
+    ap.add_argument("--mpc-episodes", type=int, default=20, help="closed-loop episodes per crowd benchmark (0: skip)")
     ap.add_argument("--profile-plain", type=int, default=0, metavar="B",
                     help="profiling aid: solve 2 iterations of the paper-shaped scene at batch B with the "
                          "plain loop and exit (no JSON line)")
@@ -547,6 +576,8 @@ def main():
             line["precision"] = bench_precision(TJ, W, torch, dev, flush, args.precision_steps)
         if args.serve_seconds > 0:
             line["serving"] = bench_serving(TJ, W, args.serve_seconds, args.serve_plain_seconds)
+        if args.mpc_episodes > 0:
+            line["closed_loop"] = bench_closed_loop(args.mpc_episodes)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(pb, B, ITERS)
         print(json.dumps(line), flush=True)

@@ -135,6 +135,30 @@ AM_API int am_get_results(am_problem *h, float *res, float *res_psi, float *cost
  * scanned.) */
 AM_API int am_get_best(am_problem *h, float coeffs[33], float *cost, float *residual, int *index);
 
+/* Re-draw the coefficients of the B trajectories the handle holds as the
+ * batch initialisation of Sec. IV: samples around the straight line between
+ * the handle's current start and goal positions (control points 0..2 at the
+ * start, 8..10 at the goal, 3..7 evenly spaced), with the interior points of
+ * c_x and c_y perturbed by sigma L z, L the Cholesky factor of the inverse
+ * of D2^T D2 restricted to points 3..7 (D2 the second-difference operator on
+ * the 11 control points; scaled to a largest standard deviation of 1 m), z
+ * standard normal.  c_psi is the straight line between the heading
+ * boundary values and the slacks c, s start at cos, sin of its control
+ * points.  The multipliers lambda, lambda_psi are kept (the MPC warm start of
+ * Sec. IV).  Trajectory 0 takes no perturbation (z = 0), so a batch of one is
+ * the straight line.  z comes from a counter-based generator: SplitMix64
+ * (Steele, Lea and Flood, 2014) of (seed, trajectory, draw) gives two 53-bit
+ * uniforms for one Box-Muller pair, so a seed fixes the draw on any device.
+ * Queued on the handle's stream; requires a state (am_init_state or a solve)
+ * and sigma finite and >= 0. */
+AM_API int am_resample(am_problem *h, unsigned long long seed, float sigma, void *stream);
+
+/* Evaluate a plan (c_x, c_y, c_psi: 33 floats, host) of horizon T at `count`
+ * times t[i] (clamped to [0, T]): out[9 i ..] = x, x', x'', y, y', y'', psi,
+ * psi', psi'' (derivatives in 1/s, 1/s^2; Eq. param).  Host arithmetic in
+ * FP64, no device work. */
+AM_API int am_plan_eval(const float coeffs[33], double T, int count, const double *t, double *out);
+
 /* Copy the B x AM_STATE_FLOATS state out of / into the handle. */
 AM_API int am_get_state(am_problem *h, float *out, int mem);
 AM_API int am_set_state(am_problem *h, int B, const float *in, int mem);
@@ -146,6 +170,13 @@ AM_API int am_get_history(am_problem *h, float *out, int mem);
 
 /* Options.  AM_OPT_KERNEL: AM_KERNEL_FUSED or AM_KERNEL_PLAIN.
  * AM_OPT_TILE: trajectories per CTA of the fused kernel (0 = automatic).
+ * AM_OPT_SELECT: the best-trajectory rule of am_get_best and of grouped
+ * and served solves when no trajectory is collision-free.  AM_SELECT_COST
+ * (default): the lowest cost (Fig. 1's rule applied to every trajectory);
+ * AM_SELECT_CLEARANCE: the largest smallest ellipse distance, for a
+ * receding-horizon loop, where the cheapest colliding plan is the worst one
+ * to execute.  Collision-free trajectories always rank first, by cost.
+ * Groups and servers read it when they are created or started.
  * AM_OPT_DIAG_STALL: diagnostic for failure-detection tests (no counterpart
  * in the paper).  While set, the fused kernel stages its constants without
  * issuing the copy, so its bounded device-side wait (about one second) runs
@@ -155,6 +186,9 @@ AM_API int am_get_history(am_problem *h, float *out, int mem);
 #define AM_OPT_KERNEL 1
 #define AM_OPT_TILE 2
 #define AM_OPT_DIAG_STALL 3
+#define AM_OPT_SELECT 4
+#define AM_SELECT_COST 0
+#define AM_SELECT_CLEARANCE 1
 AM_API int am_set_option(am_problem *h, int option, int value);
 
 /* Stream used by calls that take none (am_set_obstacles, am_set_boundary,
@@ -269,13 +303,22 @@ typedef struct {
     int max_pending;        /* queue bound (0 = 65536)                         */
 } am_server_desc;
 
+#define AM_REQ_GOAL 1       /* am_request.flags: replace the goal state        */
+#define AM_REQ_RESAMPLE 2   /* am_request.flags: re-draw the batch (am_resample) */
+
 typedef struct {
     int scene;              /* as returned by am_server_add_scene              */
     double advance;         /* > 0: the start state becomes the scene's last
                                best plan at t = advance s (position, velocity,
-                               acceleration of x, y and psi); goal unchanged   */
+                               acceleration of x, y and psi)                   */
     const float *xo, *yo;   /* nullable: new obstacle centre tracks, n x q
                                each, host memory, copied by am_server_submit   */
+    int flags;              /* AM_REQ_GOAL | AM_REQ_RESAMPLE, applied after the
+                               advance and the tracks, before the solve        */
+    double goal[9];         /* AM_REQ_GOAL: x, x', x'', y, y', y'', psi, psi',
+                               psi'' at t = T                                   */
+    unsigned long long seed;  /* AM_REQ_RESAMPLE: generator seed               */
+    float sigma;            /* AM_REQ_RESAMPLE: perturbation scale (m)         */
 } am_request;
 
 typedef struct {

@@ -88,6 +88,7 @@ struct am_problem {
     int launches = 0;
     bool solved = false;
     int diag_stall = 0;
+    int select = AM_SELECT_COST;
     float *h_best = nullptr;  // pinned
 };
 
@@ -149,6 +150,7 @@ void set_scalars(am_problem *h)
 {
     ConstLayout &L = h->L;
     L.diag_stall = h->diag_stall;
+    L.select = h->select;
     L.rho = float(h->pp.rho);
     L.rho_psi = float(h->pp.rho_psi);
     L.v_max = float(h->pp.v_max);
@@ -332,6 +334,12 @@ int am_set_option(am_problem *h, int option, int value)
         h->tile = value;
         return AM_OK;
     }
+    if (option == AM_OPT_SELECT) {
+        if (value != AM_SELECT_COST && value != AM_SELECT_CLEARANCE) return fail(AM_ERR_ARG, "bad selection rule");
+        h->select = value;
+        h->L.select = value;
+        return AM_OK;
+    }
     if (option == AM_OPT_DIAG_STALL) {
         h->diag_stall = value != 0;
         h->L.diag_stall = h->diag_stall;
@@ -438,7 +446,7 @@ int am_get_best(am_problem *h, float coeffs[33], float *cost, float *residual, i
 {
     if (!h) return fail(AM_ERR_ARG, "null handle");
     if (!h->solved) return fail(AM_ERR_STATE, "no solve yet");
-    if (launch_argmin(h->d_state, h->d_out + 2 * size_t(h->B), h->d_out, h->d_out + 3 * size_t(h->B),
+    if (launch_argmin(h->select, h->d_state, h->d_out + 2 * size_t(h->B), h->d_out, h->d_out + 3 * size_t(h->B),
                       h->B, h->d_best, h->stream, nullptr))
         return fail(AM_ERR_CUDA, "argmin launch failed");
     CK(cudaMemcpyAsync(h->h_best, h->d_best, 36 * sizeof(float), cudaMemcpyDeviceToHost, h->stream),
@@ -819,6 +827,40 @@ int am_init_state(am_problem *h, int B, const float *init, const float *warm_lam
     CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream), "status reset");
     h->B = B;
     h->solved = true;
+    return AM_OK;
+}
+
+int am_resample(am_problem *h, unsigned long long seed, float sigma, void *stream)
+{
+    if (!h) return fail(AM_ERR_ARG, "null handle");
+    if (!(sigma >= 0.f) || !std::isfinite(sigma)) return fail(AM_ERR_ARG, "sigma must be finite and >= 0");
+    if (!h->solved || h->B < 1) return fail(AM_ERR_STATE, "no state yet");
+    h->stream = static_cast<cudaStream_t>(stream);
+    NvtxRange nvtx("am_resample");
+    ResampleArgs a;
+    double Lc[25];
+    init_cov_factor(Lc);
+    for (int i = 0; i < 25; ++i) a.Lc[i] = float(Lc[i]);
+    const float line[6] = {float(h->pp.x_bc[0]), float(h->pp.x_bc[3]), float(h->pp.y_bc[0]),
+                           float(h->pp.y_bc[3]), float(h->pp.psi_bc[0]), float(h->pp.psi_bc[3])};
+    std::memcpy(a.line, line, sizeof(line));
+    a.sigma = sigma;
+    a.seed = seed;
+    a.B = h->B;
+    if (launch_resample(h->d_state, a, h->stream, nullptr)) return fail(AM_ERR_CUDA, "resample launch failed");
+    return AM_OK;
+}
+
+int am_plan_eval(const float coeffs[33], double T, int count, const double *t, double *out)
+{
+    if (!coeffs || count < 0 || (count > 0 && (!t || !out))) return fail(AM_ERR_ARG, "null argument");
+    if (!(T > 0) || !std::isfinite(T)) return fail(AM_ERR_ARG, "T must be finite and > 0");
+    for (int i = 0; i < count; ++i)
+        if (!std::isfinite(t[i])) return fail(AM_ERR_ARG, "non-finite time %d", i);
+    for (int k = 0; k < 33; ++k)
+        if (!std::isfinite(coeffs[k])) return fail(AM_ERR_ARG, "non-finite coefficient %d", k);
+    for (int i = 0; i < count; ++i)
+        for (int s = 0; s < 3; ++s) bernstein_eval(coeffs + 11 * s, T, t[i], out + 9 * i + 3 * s);
     return AM_OK;
 }
 

@@ -30,6 +30,69 @@ __global__ void init_state_kernel(float *state, const float *init, const float *
     state[i] = v;
 }
 
+// SplitMix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number
+// generators", OOPSLA 2014): one output of the generator whose state is x.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x)
+{
+    unsigned long long z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Uniform in (0, 1) for draw k of trajectory l: the top 53 bits of
+// SplitMix64(seed XOR SplitMix64(256 l + k)), offset by half a unit.
+__device__ __forceinline__ double uniform_draw(unsigned long long seed, int l, int k)
+{
+    const unsigned long long z = splitmix64(seed ^ splitmix64(256ull * (unsigned long long)l + k));
+    return (double(z >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+}
+
+// Batch re-draw (am_resample): one thread per trajectory.  Ten standard
+// normals from five Box-Muller pairs (draws 2p, 2p + 1), z_x = 0..4 and
+// z_y = 5..9; trajectory 0 takes none.  Control points 3..7 of c_x, c_y are the
+// straight line plus sigma L z; the heading is the straight line between its
+// boundary values and the slacks its cos, sin (as init_state_kernel).  The
+// multipliers (state entries 55..109) are left as they are.
+__global__ void resample_kernel(float *state, ResampleArgs a)
+{
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= a.B) return;
+    double z[10];
+    for (int p = 0; p < 5; ++p) {
+        double r = 0.0, c = 0.0, s = 0.0;
+        if (l > 0) {
+            const double u1 = uniform_draw(a.seed, l, 2 * p), u2 = uniform_draw(a.seed, l, 2 * p + 1);
+            r = sqrt(-2.0 * log(u1));
+            sincospi(2.0 * u2, &s, &c);
+        }
+        z[2 * p] = r * c;
+        z[2 * p + 1] = r * s;
+    }
+    float *st = state + (size_t)l * STATE;
+    for (int k = 0; k < NV; ++k) {
+        const float w = fminf(fmaxf((k - 2) / 6.f, 0.f), 1.f);
+        float cx = fmaf(a.line[1] - a.line[0], w, a.line[0]);
+        float cy = fmaf(a.line[3] - a.line[2], w, a.line[2]);
+        const float cp = fmaf(a.line[5] - a.line[4], w, a.line[4]);
+        if (k >= 3 && k <= 7) {
+            const int i = k - 3;
+            double dx = 0.0, dy = 0.0;
+            for (int j = 0; j <= i; ++j) {
+                dx += double(a.Lc[i * 5 + j]) * z[j];
+                dy += double(a.Lc[i * 5 + j]) * z[5 + j];
+            }
+            cx += a.sigma * float(dx);
+            cy += a.sigma * float(dy);
+        }
+        st[k] = cx;
+        st[11 + k] = cosf(cp);
+        st[22 + k] = cy;
+        st[33 + k] = sinf(cp);
+        st[44 + k] = cp;
+    }
+}
+
 // Obstacle sections of the constant block: centre tracks in ellipse-scaled
 // coordinates (x_j(t)/a_j, y_j(t)/b_j) and per-obstacle (1/a_j, 1/b_j, a_j, b_j),
 // with the semi-axes inflated by the robot circle radius.
@@ -73,16 +136,19 @@ __device__ __forceinline__ bool better(const Key &a, const Key &b)
 
 // Lexicographic minimum over the batch of (collides, cost, index), where a
 // trajectory collides when its smallest ellipse distance is below 0.99; a
-// non-finite cost ranks last.  Writes {index, cost, residual, c_x, c_y, c_psi}.
-// Lexicographic best over B trajectories (collision-free first, then cost,
-// then index); the whole block takes part, out gets 36 floats.
-__device__ void select_best(const float *state, const float *cost, const float *res,
+// non-finite cost ranks last.  With select = 1, colliding trajectories rank
+// by their smallest distance, largest first, instead of by cost.  Writes
+// {index, cost, residual, c_x, c_y, c_psi}; the whole block takes part, out
+// gets 36 floats.
+__device__ void select_best(int select, const float *state, const float *cost, const float *res,
                             const float *mind, int B, float *out, Key *sk)
 {
     Key best{2, FLT_MAX, 0x7fffffff};
     for (int l = threadIdx.x; l < B; l += blockDim.x) {
         float c = cost[l];
-        Key k{mind[l] < 0.99f ? 1 : 0, isfinite(c) ? c : FLT_MAX, l};
+        const bool coll = mind[l] < 0.99f;
+        const float v = coll && select == 1 ? -mind[l] : c;
+        Key k{coll ? 1 : 0, isfinite(v) ? v : FLT_MAX, l};
         if (!isfinite(c)) k.coll = 2;
         if (better(k, best)) best = k;
     }
@@ -107,18 +173,18 @@ __device__ void select_best(const float *state, const float *cost, const float *
     }
 }
 
-__global__ void argmin_kernel(const float *state, const float *cost, const float *res,
+__global__ void argmin_kernel(int select, const float *state, const float *cost, const float *res,
                               const float *mind, int B, float *out)
 {
     __shared__ Key sk[1024];
-    select_best(state, cost, res, mind, B, out, sk);
+    select_best(select, state, cost, res, mind, B, out, sk);
 }
 
 __global__ void group_argmin_kernel(const FusedProblem *probs, const int *list, float *out)
 {
     __shared__ Key sk[1024];
     const FusedProblem &p = probs[list[blockIdx.x]];
-    select_best(p.state, p.cost, p.res, p.mind, p.B, out + 36 * blockIdx.x, sk);
+    select_best(p.L.select, p.state, p.cost, p.res, p.mind, p.B, out + 36 * blockIdx.x, sk);
 }
 
 }  // namespace
@@ -129,6 +195,14 @@ int launch_init_state(float *state, const float *init, const float *warm, int B,
     const int n = B * STATE;
     init_state_kernel<<<(n + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(state, init,
                                                                                       warm, B);
+    if (launches) ++*launches;
+    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
+int launch_resample(float *state, const ResampleArgs &a, void *stream, int *launches)
+{
+    if (a.B < 1) return 0;
+    resample_kernel<<<(a.B + 127) / 128, 128, 0, static_cast<cudaStream_t>(stream)>>>(state, a);
     if (launches) ++*launches;
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
@@ -153,10 +227,10 @@ int launch_group_argmin(const FusedProblem *d_probs, const int *d_list, int coun
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
-int launch_argmin(const float *state, const float *cost, const float *res, const float *mind,
+int launch_argmin(int select, const float *state, const float *cost, const float *res, const float *mind,
                   int B, float *best_out, void *stream, int *launches)
 {
-    argmin_kernel<<<1, 1024, 0, static_cast<cudaStream_t>(stream)>>>(state, cost, res, mind, B,
+    argmin_kernel<<<1, 1024, 0, static_cast<cudaStream_t>(stream)>>>(select, state, cost, res, mind, B,
                                                                      best_out);
     if (launches) ++*launches;
     return cudaGetLastError() == cudaSuccess ? 0 : -2;

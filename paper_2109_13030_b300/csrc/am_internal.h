@@ -56,6 +56,8 @@ struct HostSetup {
     double kbpsi[NV];                         // K_psi^{-1}[:11, 11:] b_psi
     std::vector<double> W;                    // q x NV: W = P Mpsi^T
     double cond_pos = 0, cond_psi = 0;        // inf-norm condition estimates
+    std::vector<double> Kp, Kq;               // both KKT inverses (b-independent), kept so a
+    int kdim = 0;                             // boundary change only re-folds kb, kbpsi
 };
 
 // Bernstein basis and derivatives on t_k = k T / (q - 1).
@@ -68,6 +70,16 @@ int build_setup(const ProblemParams &pp, int n, HostSetup &S);
 
 // Recomputes only the boundary-dependent vectors kb, kbpsi.
 int rebuild_boundary(const ProblemParams &pp, HostSetup &S);
+
+// Value, first and second time derivative at t (clamped to [0, T]) of a
+// degree-10 Bernstein polynomial with control points c on [0, T] (Eq. param).
+void bernstein_eval(const float *c, double T, double t, double out[3]);
+
+// Lower Cholesky factor (row-major 5 x 5) of the batch initialisation's
+// covariance of control points 3..7: the inverse of D2^T D2 restricted to
+// them (D2 the second-difference operator on 11 points), scaled to a largest
+// variance of 1.
+void init_cov_factor(double Lc[25]);
 
 // ------------------------------------------------------------ device layout
 
@@ -105,6 +117,8 @@ struct ConstLayout {
                               // products), 1 one TF32 product, 2 one BF16 product
     int diag_stall;           // diagnostic: stage without the copy, so the bounded
                               // wait on it runs out (failure-detection tests)
+    int select;               // best selection among colliding trajectories:
+                              // 0 lowest cost, 1 largest smallest distance
 };
 
 ConstLayout make_layout(int q, int m, int n);
@@ -174,13 +188,24 @@ int launch_plain(const SolveArgs &a, float *scratch, size_t scratch_floats, void
                  int *launches);
 size_t plain_scratch_floats(const ConstLayout &L, int B);
 // Best-trajectory selection; writes {index, cost, res, 33 coefficients}.
-int launch_argmin(const float *state, const float *cost, const float *res, const float *mind,
+int launch_argmin(int select, const float *state, const float *cost, const float *res, const float *mind,
                   int B, float *best_out, void *stream, int *launches);
 // Converts raw obstacle arrays (device) into the kernel's obstacle sections.
 int launch_prep_obstacles(float *cblob, const ConstLayout &L, const float *xo, const float *yo,
                           const float *a, const float *b, float r_c, void *stream, int *launches);
 // Builds the initial state from B x 3 x 11 coefficients (+ optional lambdas);
 // the slack control points start at cos / sin of the heading control points.
+// Batch re-draw around the straight line between the boundary positions
+// (am_resample); line = (x0, x1, y0, y1, psi0, psi1).
+struct ResampleArgs {
+    float Lc[25];
+    float line[6];
+    float sigma;
+    unsigned long long seed;
+    int B;
+};
+int launch_resample(float *state, const ResampleArgs &a, void *stream, int *launches);
+
 int launch_init_state(float *state, const float *init, const float *warm, int B, void *stream,
                       int *launches);
 // Handle accessors for entry points outside the C-ABI file.

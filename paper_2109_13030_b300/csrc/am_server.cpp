@@ -44,31 +44,6 @@ struct Scene {
     float best[33];
 };
 
-double binom(int n, int k)
-{
-    double c = 1;
-    for (int i = 1; i <= k; ++i) c = c * (n - k + i) / i;
-    return c;
-}
-
-// Value, first and second time derivative at t of a degree-10 Bernstein
-// polynomial with control points c on [0, T] (derivatives through the
-// differences of the control points).
-void bernstein_eval(const float *c, double T, double t, double out[3])
-{
-    const int n = 10;
-    double tau = t / T;
-    tau = tau < 0 ? 0 : tau > 1 ? 1 : tau;
-    auto basis = [&](int k, int deg) { return binom(deg, k) * std::pow(tau, k) * std::pow(1 - tau, deg - k); };
-    double v = 0, d = 0, dd = 0;
-    for (int k = 0; k <= n; ++k) v += double(c[k]) * basis(k, n);
-    for (int k = 0; k < n; ++k) d += (double(c[k + 1]) - c[k]) * basis(k, n - 1);
-    for (int k = 0; k < n - 1; ++k) dd += (double(c[k + 2]) - 2.0 * c[k + 1] + c[k]) * basis(k, n - 2);
-    out[0] = v;
-    out[1] = d * n / T;
-    out[2] = dd * n * (n - 1) / (T * T);
-}
-
 }  // namespace
 
 struct am_server {
@@ -91,17 +66,24 @@ struct am_server {
 
 namespace {
 
-// Start state from the scene's last best plan at t = advance.
-int advance_start(Scene &sc, double advance)
+// New boundary conditions of a request: the start state from the scene's
+// last best plan at t = advance, and/or the goal state given with it.
+int update_boundary(Scene &sc, const am_request &r)
 {
-    double x[6], y[6], psi[6], v[3];
+    const bool adv = r.advance > 0 && sc.has_best, goal = (r.flags & AM_REQ_GOAL) != 0;
+    if (!adv && !goal) return AM_OK;
+    double x[6], y[6], psi[6];
     problem_boundary(sc.h, x, y, psi);
-    bernstein_eval(sc.best, sc.T, advance, v);
-    std::memcpy(x, v, sizeof(v));
-    bernstein_eval(sc.best + 11, sc.T, advance, v);
-    std::memcpy(y, v, sizeof(v));
-    bernstein_eval(sc.best + 22, sc.T, advance, v);
-    std::memcpy(psi, v, sizeof(v));
+    if (adv) {
+        bernstein_eval(sc.best, sc.T, r.advance, x);
+        bernstein_eval(sc.best + 11, sc.T, r.advance, y);
+        bernstein_eval(sc.best + 22, sc.T, r.advance, psi);
+    }
+    if (goal) {
+        std::memcpy(x + 3, r.goal, 3 * sizeof(double));
+        std::memcpy(y + 3, r.goal + 3, 3 * sizeof(double));
+        std::memcpy(psi + 3, r.goal + 6, 3 * sizeof(double));
+    }
     return am_set_boundary(sc.h, x, y, psi);
 }
 
@@ -114,7 +96,8 @@ int serve_round(am_server *s, std::vector<Request> &batch)
         Scene &sc = s->scenes[q.r.scene];
         rc = am_set_stream(sc.h, s->st);
         if (!rc && !q.xo.empty()) rc = problem_update_tracks(sc.h, q.xo.data(), q.yo.data());
-        if (!rc && q.r.advance > 0 && sc.has_best) rc = advance_start(sc, q.r.advance);
+        if (!rc) rc = update_boundary(sc, q.r);
+        if (!rc && (q.r.flags & AM_REQ_RESAMPLE)) rc = am_resample(sc.h, q.r.seed, q.r.sigma, s->st);
         if (rc) return rc;
     }
     // A round of several requests goes through one grouped launch; a round of
@@ -296,6 +279,12 @@ int am_server_submit(am_server *s, const am_request *req, long long *ticket)
     if (req->scene < 0 || req->scene >= int(s->scenes.size())) return report_error(AM_ERR_ARG, "unknown scene");
     if (!(req->advance >= 0) || !std::isfinite(req->advance)) return report_error(AM_ERR_ARG, "bad advance");
     if ((req->xo == nullptr) != (req->yo == nullptr)) return report_error(AM_ERR_ARG, "xo and yo go together");
+    if (req->flags & ~(AM_REQ_GOAL | AM_REQ_RESAMPLE)) return report_error(AM_ERR_ARG, "unknown request flags");
+    if (req->flags & AM_REQ_GOAL)
+        for (int k = 0; k < 9; ++k)
+            if (!std::isfinite(req->goal[k])) return report_error(AM_ERR_ARG, "non-finite goal");
+    if ((req->flags & AM_REQ_RESAMPLE) && !(req->sigma >= 0.f && std::isfinite(req->sigma)))
+        return report_error(AM_ERR_ARG, "sigma must be finite and >= 0");
     const Scene &sc = s->scenes[req->scene];
     Request q;
     q.r = *req;

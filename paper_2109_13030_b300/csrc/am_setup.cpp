@@ -284,17 +284,65 @@ int build_setup(const ProblemParams &pp, int n, HostSetup &S)
             S.W[t * NV + k] = v;
         }
     fold_boundary(pp, S, Kp, dim, Kq);
+    S.Kp.swap(Kp);
+    S.Kq.swap(Kq);
+    S.kdim = dim;
     return 0;
 }
 
 int rebuild_boundary(const ProblemParams &pp, HostSetup &S)
 {
-    int dim = 0;
-    std::vector<double> Kp = pos_kkt_inverse(pp, S, dim);
-    std::vector<double> Kq = psi_kkt_inverse(pp, S);
-    if (Kp.empty() || Kq.empty()) return -1;
-    fold_boundary(pp, S, Kp, dim, Kq);
+    // The KKT matrices depend on the basis, rho, n and the boundary rows A,
+    // not on b: re-fold with the inverses formed by build_setup.
+    if (S.Kp.empty() || S.Kq.empty()) return -1;
+    fold_boundary(pp, S, S.Kp, S.kdim, S.Kq);
     return 0;
+}
+
+void bernstein_eval(const float *c, double T, double t, double out[3])
+{
+    const int n = NV - 1;
+    double tau = t / T;
+    tau = tau < 0 ? 0 : tau > 1 ? 1 : tau;
+    auto basis = [&](int k, int deg) { return binomial(deg, k) * ipow(tau, k) * ipow(1 - tau, deg - k); };
+    double v = 0, d = 0, dd = 0;
+    for (int k = 0; k <= n; ++k) v += double(c[k]) * basis(k, n);
+    // derivatives through the first and second differences of the control points
+    for (int k = 0; k < n; ++k) d += (double(c[k + 1]) - c[k]) * basis(k, n - 1);
+    for (int k = 0; k < n - 1; ++k) dd += (double(c[k + 2]) - 2.0 * c[k + 1] + c[k]) * basis(k, n - 2);
+    out[0] = v;
+    out[1] = d * n / T;
+    out[2] = dd * n * (n - 1) / (T * T);
+}
+
+void init_cov_factor(double Lc[25])
+{
+    // R = D2^T D2 on the 11 control points, restricted to points 3..7
+    double R[NV][NV] = {};
+    for (int k = 0; k + 2 < NV; ++k) {
+        const double w[3] = {1.0, -2.0, 1.0};
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) R[k + a][k + b] += w[a] * w[b];
+    }
+    std::vector<double> C(25);
+    for (int i = 0; i < 5; ++i)
+        for (int j = 0; j < 5; ++j) C[i * 5 + j] = R[3 + i][3 + j];
+    invert(C, 5);  // R restricted to 3..7 is positive definite
+    double dmax = 0;
+    for (int i = 0; i < 5; ++i) dmax = std::fmax(dmax, C[i * 5 + i]);
+    for (double &v : C) v /= dmax;
+    // Cholesky C = L L^T
+    for (int i = 0; i < 25; ++i) Lc[i] = 0.0;
+    for (int j = 0; j < 5; ++j) {
+        double s = C[j * 5 + j];
+        for (int k = 0; k < j; ++k) s -= Lc[j * 5 + k] * Lc[j * 5 + k];
+        Lc[j * 5 + j] = std::sqrt(s);
+        for (int i = j + 1; i < 5; ++i) {
+            double t = C[i * 5 + j];
+            for (int k = 0; k < j; ++k) t -= Lc[i * 5 + k] * Lc[j * 5 + k];
+            Lc[i * 5 + j] = t / Lc[j * 5 + j];
+        }
+    }
 }
 
 static int align4(int x) { return (x + 3) & ~3; }

@@ -19,16 +19,18 @@ AM_OK, AM_ERR_ARG, AM_ERR_CUDA, AM_ERR_BUDGET, AM_ERR_TIMEOUT, AM_ERR_NAN, AM_ER
 AM_HOST, AM_DEVICE = 0, 1
 AM_FP32, AM_TF32, AM_BF16 = 0, 1, 2
 AM_KERNEL_FUSED, AM_KERNEL_PLAIN = 0, 1
-AM_OPT_KERNEL, AM_OPT_TILE, AM_OPT_DIAG_STALL = 1, 2, 3
+AM_OPT_KERNEL, AM_OPT_TILE, AM_OPT_DIAG_STALL, AM_OPT_SELECT = 1, 2, 3, 4
+AM_SELECT_COST, AM_SELECT_CLEARANCE = 0, 1
 AM_GOPT_THREADS, AM_GOPT_GRAPH = 1, 2
 AM_PENDING = 1
 AM_SRV_BATCHED, AM_SRV_SEQUENTIAL = 0, 1
+AM_REQ_GOAL, AM_REQ_RESAMPLE = 1, 2
 AM_NV, AM_STATE_FLOATS = 11, 110
 
 EXPORTS = ["am_init_problem", "am_set_obstacles", "am_set_boundary", "am_solve_batch",
            "am_get_results", "am_get_best", "am_get_state", "am_set_state", "am_set_history",
            "am_get_history", "am_set_option", "am_set_stream", "am_last_solve_stats",
-           "am_solve_batch_noalloc", "am_init_state", "am_group_create", "am_group_solve",
+           "am_solve_batch_noalloc", "am_init_state", "am_resample", "am_plan_eval", "am_group_create", "am_group_solve",
            "am_group_autotune", "am_group_set_option", "am_group_set_active", "am_group_get_best",
            "am_group_stats", "am_group_destroy", "am_server_create", "am_server_add_scene",
            "am_server_start", "am_server_submit", "am_server_poll", "am_server_stats",
@@ -51,7 +53,8 @@ class AmServerDesc(C.Structure):
 
 class AmRequest(C.Structure):
     _fields_ = [("scene", C.c_int), ("advance", C.c_double),
-                ("xo", C.c_void_p), ("yo", C.c_void_p)]
+                ("xo", C.c_void_p), ("yo", C.c_void_p), ("flags", C.c_int),
+                ("goal", C.c_double * 9), ("seed", C.c_ulonglong), ("sigma", C.c_float)]
 
 
 class AmResult(C.Structure):
@@ -88,6 +91,8 @@ def _load():
         "am_last_solve_stats": ([vp, C.POINTER(C.c_int)], ip),
         "am_solve_batch_noalloc": ([vp, ip, fp, fp, fp, fp, fp, ip, vp], ip),
         "am_init_state": ([vp, ip, fp, fp, vp, ip], ip),
+        "am_resample": ([vp, C.c_ulonglong, C.c_float, vp], ip),
+        "am_plan_eval": ([fp, C.c_double, ip, fp, fp], ip),
         "am_group_create": ([C.POINTER(vp), ip, C.POINTER(vp)], ip),
         "am_group_solve": ([vp, ip, vp], ip),
         "am_group_autotune": ([vp, ip, vp, C.POINTER(C.c_int), C.POINTER(C.c_float)], ip),
@@ -259,6 +264,19 @@ def am_init_state(h, B, init, warm_lambda=None, stream=None):
     _check(_lib.am_init_state(h, int(B), pi, pw, _stream_ptr(stream), mem))
 
 
+def am_resample(h, seed, sigma=1.0, stream=None):
+    _check(_lib.am_resample(h, int(seed) & (2**64 - 1), float(sigma), _stream_ptr(stream)))
+
+
+def am_plan_eval(coeffs, T, t):
+    """x, x', x'', y, y', y'', psi, psi', psi'' of a plan at the times t: (len(t), 9)."""
+    c = np.ascontiguousarray(coeffs, dtype=np.float32).reshape(33)
+    tt = np.ascontiguousarray(np.atleast_1d(t), dtype=np.float64)
+    out = np.zeros((tt.size, 9))
+    _check(_lib.am_plan_eval(c.ctypes.data, float(T), tt.size, tt.ctypes.data, out.ctypes.data))
+    return out
+
+
 def am_group_create(handles) -> int:
     arr = (C.c_void_p * len(handles))(*handles)
     g = C.c_void_p()
@@ -319,9 +337,18 @@ def am_server_start(s):
     _check(_lib.am_server_start(s))
 
 
-def am_server_submit(s, scene, advance=0.0, xo=None, yo=None) -> int:
+def am_server_submit(s, scene, advance=0.0, xo=None, yo=None, goal=None, resample_seed=None,
+                     sigma=1.0) -> int:
     keep = []
     r = AmRequest(int(scene), float(advance), None, None)
+    if goal is not None:
+        r.flags |= AM_REQ_GOAL
+        for k, v in enumerate(np.asarray(goal, dtype=np.float64).reshape(9)):
+            r.goal[k] = float(v)
+    if resample_seed is not None:
+        r.flags |= AM_REQ_RESAMPLE
+        r.seed = int(resample_seed) & (2**64 - 1)
+        r.sigma = float(sigma)
     if xo is not None:
         ax = np.ascontiguousarray(xo, dtype=np.float32)
         ay = np.ascontiguousarray(yo, dtype=np.float32)
@@ -372,7 +399,7 @@ class Problem:
     """Owns one handle; methods forward to the C calls above."""
 
     def __init__(self, pb: dict, precision=AM_FP32, alpha_mode=0, psi_dual_sign=0, cs_boundary=1,
-                 kernel=AM_KERNEL_FUSED, tile=0):
+                 kernel=AM_KERNEL_FUSED, tile=0, select=AM_SELECT_COST):
         self.desc = make_desc(pb, precision, alpha_mode, psi_dual_sign, cs_boundary)
         self.h = am_init_problem(self.desc)
         self.q, self.m, self.n = int(pb["q"]), int(pb["m"]), int(pb["n"])
@@ -381,6 +408,7 @@ class Problem:
         self.iters = 0
         am_set_option(self.h, AM_OPT_KERNEL, kernel)
         am_set_option(self.h, AM_OPT_TILE, tile)
+        am_set_option(self.h, AM_OPT_SELECT, select)
         if int(pb["n"]) > 0:
             self.set_obstacles(pb["xo"], pb["yo"], pb["ao"], pb["bo"])
 
@@ -390,6 +418,14 @@ class Problem:
     def init_state(self, init, warm_lambda=None, stream=None):
         am_init_state(self.h, int(init.shape[0]), init, warm_lambda, stream)
         self.B = int(init.shape[0])
+        return self
+
+    def resample(self, seed, sigma=1.0, stream=None):
+        am_resample(self.h, seed, sigma, stream)
+        return self
+
+    def set_boundary(self, x_bc, y_bc, psi_bc):
+        am_set_boundary(self.h, x_bc, y_bc, psi_bc)
         return self
 
     def solve(self, init, iters, warm_lambda=None, stream=None, history=False):
@@ -493,8 +529,11 @@ class Server:
         am_server_start(self.s)
         return self
 
-    def submit(self, scene, advance=0.0, xo=None, yo=None):
-        return am_server_submit(self.s, scene, advance, xo, yo)
+    def submit(self, scene, advance=0.0, xo=None, yo=None, goal=None, resample_seed=None, sigma=1.0):
+        """goal: 9 values (x, x', x'', y, y', y'', psi, psi', psi'' at t = T);
+        resample_seed: re-draw the scene's batch around the new straight line
+        with that seed (multipliers kept)."""
+        return am_server_submit(self.s, scene, advance, xo, yo, goal, resample_seed, sigma)
 
     def poll(self, ticket, timeout_ms=0):
         return am_server_poll(self.s, ticket, timeout_ms)

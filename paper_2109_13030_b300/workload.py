@@ -19,6 +19,10 @@ these synthetic scenes stand in for them):
 * ``precision`` the ``paper`` scene at 4096 trajectories.
 * ``uneven``    64 independent problems of mixed batch, horizon, obstacle and
                 circle counts.
+* crowds        (``make_crowd``) the closed-loop benchmarks of Sec. IV: 30
+                people walking on straight lines in a 10 m wide band ahead of a
+                robot that should follow the x axis at 1 m/s (static crowd,
+                same-direction flow up to 0.3 m/s, opposite flow up to 1.0 m/s).
 """
 from __future__ import annotations
 
@@ -214,3 +218,47 @@ def with_obstacles_removed(pb: dict, v_max: float = 1e6, a_max: float = 1e6) -> 
     out.update(n=0, xo=np.zeros((0, q)), yo=np.zeros((0, q)), ao=np.zeros(0),
                bo=np.zeros(0), v_max=v_max, a_max=a_max)
     return out
+
+
+CROWD_KINDS = ("static", "same", "opposite")
+
+
+def make_crowd(kind: str, seed: int, n: int = 30, radius: float = 0.3, v_des: float = 1.0,
+               width: float = 5.0) -> dict:
+    """One closed-loop benchmark scene (Sec. IV, Benchmarks 1-3), synthetic.
+
+    n people of radius ``radius`` with centres uniform in x in [3, 25] m
+    (static, same) or [6, 36] m (opposite, walking towards the robot) and y in
+    [-width, width] m, at least 1.2 m apart and 2 m from the robot's start (0, 0);
+    velocities 0 (static), vx uniform in [0, 0.3] m/s (same direction as the
+    robot), or vx uniform in [-1.0, -0.3] m/s (opposite), with vy uniform in
+    [-0.05, 0.05] m/s for the moving crowds.  The desired motion is
+    (v_des t, 0).  Rejection draws are part of the seeded stream.
+    """
+    if kind not in CROWD_KINDS:
+        raise ValueError(f"unknown crowd {kind!r}")
+    rng = np.random.default_rng(seed)
+    xlo, xhi = (6.0, 36.0) if kind == "opposite" else (3.0, 25.0)
+    pos = []
+    while len(pos) < n:
+        p = np.array([rng.uniform(xlo, xhi), rng.uniform(-width, width)])
+        if np.hypot(*p) < 2.0 or any(np.hypot(*(p - o)) < 1.2 for o in pos):
+            continue
+        pos.append(p)
+    pos = np.array(pos)
+    if kind == "static":
+        vel = np.zeros((n, 2))
+    elif kind == "same":
+        vel = np.stack([rng.uniform(0.0, 0.3, n), rng.uniform(-0.05, 0.05, n)], 1)
+    else:
+        vel = np.stack([rng.uniform(-1.0, -0.3, n), rng.uniform(-0.05, 0.05, n)], 1)
+    return dict(kind=kind, seed=seed, n=n, p0=_f32(pos), v=_f32(vel), radius=float(np.float32(radius)),
+                v_des=v_des)
+
+
+def crowd_positions(crowd: dict, t) -> tuple[np.ndarray, np.ndarray]:
+    """Centres of the crowd at the times t (any shape): xo, yo of shape (n,) + t.shape."""
+    t = np.asarray(t, dtype=np.float64)
+    xo = crowd["p0"][:, 0].reshape((-1,) + (1,) * t.ndim) + crowd["v"][:, 0].reshape((-1,) + (1,) * t.ndim) * t
+    yo = crowd["p0"][:, 1].reshape((-1,) + (1,) * t.ndim) + crowd["v"][:, 1].reshape((-1,) + (1,) * t.ndim) * t
+    return xo, yo
