@@ -153,6 +153,17 @@ AM_API int am_get_best(am_problem *h, float coeffs[33], float *cost, float *resi
  * and sigma finite and >= 0. */
 AM_API int am_resample(am_problem *h, unsigned long long seed, float sigma, void *stream);
 
+/* Re-time the B trajectories the handle holds by dt seconds (0 <= dt <= T):
+ * each of a trajectory's five polynomials (c_x, c, c_y, s, c_psi) is
+ * re-expressed on [dt, dt + T] (past T by extending the same polynomial), so
+ * a warm-started re-plan (Sec. IV) continues every plan from where it is dt
+ * later.  The new control points are c'_k = f(dt/T repeated 10 - k times,
+ * 1 + dt/T repeated k times), f the blossom of the polynomial, evaluated on
+ * the host in FP64 by de Casteljau steps; the device applies the resulting
+ * 11 x 11 matrix.  The multipliers are kept.  Queued on the handle's stream;
+ * requires a state. */
+AM_API int am_shift(am_problem *h, double dt, void *stream);
+
 /* Evaluate a plan (c_x, c_y, c_psi: 33 floats, host) of horizon T at `count`
  * times t[i] (clamped to [0, T]): out[9 i ..] = x, x', x'', y, y', y'', psi,
  * psi', psi'' (derivatives in 1/s, 1/s^2; Eq. param).  Host arithmetic in
@@ -305,6 +316,7 @@ typedef struct {
 
 #define AM_REQ_GOAL 1       /* am_request.flags: replace the goal state        */
 #define AM_REQ_RESAMPLE 2   /* am_request.flags: re-draw the batch (am_resample) */
+#define AM_REQ_SHIFT 4      /* am_request.flags: re-time the batch by the advance (am_shift) */
 
 typedef struct {
     int scene;              /* as returned by am_server_add_scene              */
@@ -313,8 +325,9 @@ typedef struct {
                                acceleration of x, y and psi)                   */
     const float *xo, *yo;   /* nullable: new obstacle centre tracks, n x q
                                each, host memory, copied by am_server_submit   */
-    int flags;              /* AM_REQ_GOAL | AM_REQ_RESAMPLE, applied after the
-                               advance and the tracks, before the solve        */
+    int flags;              /* AM_REQ_GOAL | AM_REQ_RESAMPLE | AM_REQ_SHIFT,
+                               applied after the advance and the tracks,
+                               before the solve (a re-draw supersedes a shift) */
     double goal[9];         /* AM_REQ_GOAL: x, x', x'', y, y', y'', psi, psi',
                                psi'' at t = T                                   */
     unsigned long long seed;  /* AM_REQ_RESAMPLE: generator seed               */

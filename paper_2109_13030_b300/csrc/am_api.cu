@@ -851,6 +851,22 @@ int am_resample(am_problem *h, unsigned long long seed, float sigma, void *strea
     return AM_OK;
 }
 
+int am_shift(am_problem *h, double dt, void *stream)
+{
+    if (!h) return fail(AM_ERR_ARG, "null handle");
+    if (!(dt >= 0.0) || !(dt <= h->pp.T)) return fail(AM_ERR_ARG, "dt must be in [0, T]");
+    if (!h->solved || h->B < 1) return fail(AM_ERR_STATE, "no state yet");
+    h->stream = static_cast<cudaStream_t>(stream);
+    NvtxRange nvtx("am_shift");
+    double S[121];
+    shift_matrix(dt / h->pp.T, S);
+    ShiftArgs a;
+    for (int i = 0; i < 121; ++i) a.S[i] = float(S[i]);
+    a.B = h->B;
+    if (launch_shift(h->d_state, a, h->stream, nullptr)) return fail(AM_ERR_CUDA, "shift launch failed");
+    return AM_OK;
+}
+
 int am_plan_eval(const float coeffs[33], double T, int count, const double *t, double *out)
 {
     if (!coeffs || count < 0 || (count > 0 && (!t || !out))) return fail(AM_ERR_ARG, "null argument");

@@ -93,6 +93,22 @@ __global__ void resample_kernel(float *state, ResampleArgs a)
     }
 }
 
+// Re-timing (am_shift): one thread per (trajectory, polynomial); the five
+// polynomials of a trajectory are state entries 0, 11, 22, 33, 44 on.
+__global__ void shift_kernel(float *state, ShiftArgs a)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.B * 5) return;
+    float *c = state + (size_t)(i / 5) * STATE + 11 * (i % 5);
+    float in[NV];
+    for (int k = 0; k < NV; ++k) in[k] = c[k];
+    for (int k = 0; k < NV; ++k) {
+        float v = 0.f;
+        for (int j = 0; j < NV; ++j) v = fmaf(a.S[k * NV + j], in[j], v);
+        c[k] = v;
+    }
+}
+
 // Obstacle sections of the constant block: centre tracks in ellipse-scaled
 // coordinates (x_j(t)/a_j, y_j(t)/b_j) and per-obstacle (1/a_j, 1/b_j, a_j, b_j),
 // with the semi-axes inflated by the robot circle radius.
@@ -203,6 +219,15 @@ int launch_resample(float *state, const ResampleArgs &a, void *stream, int *laun
 {
     if (a.B < 1) return 0;
     resample_kernel<<<(a.B + 127) / 128, 128, 0, static_cast<cudaStream_t>(stream)>>>(state, a);
+    if (launches) ++*launches;
+    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
+int launch_shift(float *state, const ShiftArgs &a, void *stream, int *launches)
+{
+    if (a.B < 1) return 0;
+    const int n = 5 * a.B;
+    shift_kernel<<<(n + 127) / 128, 128, 0, static_cast<cudaStream_t>(stream)>>>(state, a);
     if (launches) ++*launches;
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }

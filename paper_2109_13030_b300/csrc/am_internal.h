@@ -206,6 +206,17 @@ struct ResampleArgs {
 };
 int launch_resample(float *state, const ResampleArgs &a, void *stream, int *launches);
 
+// Re-timing of a batch (am_shift): S maps old control points to new, row-major.
+struct ShiftArgs {
+    float S[121];
+    int B;
+};
+int launch_shift(float *state, const ShiftArgs &a, void *stream, int *launches);
+
+// Control points of a degree-10 Bernstein polynomial on [s, s + 1] from those on
+// [0, 1] (blossoming): row-major 11 x 11, c' = S c.
+void shift_matrix(double s, double S[121]);
+
 int launch_init_state(float *state, const float *init, const float *warm, int B, void *stream,
                       int *launches);
 // Handle accessors for entry points outside the C-ABI file.

@@ -98,6 +98,7 @@ int serve_round(am_server *s, std::vector<Request> &batch)
         if (!rc && !q.xo.empty()) rc = problem_update_tracks(sc.h, q.xo.data(), q.yo.data());
         if (!rc) rc = update_boundary(sc, q.r);
         if (!rc && (q.r.flags & AM_REQ_RESAMPLE)) rc = am_resample(sc.h, q.r.seed, q.r.sigma, s->st);
+        else if (!rc && (q.r.flags & AM_REQ_SHIFT) && q.r.advance > 0) rc = am_shift(sc.h, q.r.advance, s->st);
         if (rc) return rc;
     }
     // A round of several requests goes through one grouped launch; a round of
@@ -279,7 +280,10 @@ int am_server_submit(am_server *s, const am_request *req, long long *ticket)
     if (req->scene < 0 || req->scene >= int(s->scenes.size())) return report_error(AM_ERR_ARG, "unknown scene");
     if (!(req->advance >= 0) || !std::isfinite(req->advance)) return report_error(AM_ERR_ARG, "bad advance");
     if ((req->xo == nullptr) != (req->yo == nullptr)) return report_error(AM_ERR_ARG, "xo and yo go together");
-    if (req->flags & ~(AM_REQ_GOAL | AM_REQ_RESAMPLE)) return report_error(AM_ERR_ARG, "unknown request flags");
+    if (req->flags & ~(AM_REQ_GOAL | AM_REQ_RESAMPLE | AM_REQ_SHIFT))
+        return report_error(AM_ERR_ARG, "unknown request flags");
+    if ((req->flags & AM_REQ_SHIFT) && !(req->advance <= s->scenes[req->scene].T))
+        return report_error(AM_ERR_ARG, "a shifted advance must be <= T");
     if (req->flags & AM_REQ_GOAL)
         for (int k = 0; k < 9; ++k)
             if (!std::isfinite(req->goal[k])) return report_error(AM_ERR_ARG, "non-finite goal");

@@ -345,6 +345,23 @@ void init_cov_factor(double Lc[25])
     }
 }
 
+void shift_matrix(double s, double S[121])
+{
+    // column j: the new control points of the polynomial whose old control
+    // points are the unit vector e_j; new point k is the blossom at
+    // (s x (10 - k), (1 + s) x k), one de Casteljau level per argument
+    for (int j = 0; j < NV; ++j)
+        for (int k = 0; k < NV; ++k) {
+            double c[NV];
+            for (int i = 0; i < NV; ++i) c[i] = i == j ? 1.0 : 0.0;
+            for (int lev = 0; lev < NV - 1; ++lev) {
+                const double u = lev < NV - 1 - k ? s : 1.0 + s;
+                for (int i = 0; i < NV - 1 - lev; ++i) c[i] = (1.0 - u) * c[i] + u * c[i + 1];
+            }
+            S[k * NV + j] = c[0];
+        }
+}
+
 static int align4(int x) { return (x + 3) & ~3; }
 
 ConstLayout make_layout(int q, int m, int n)

@@ -64,6 +64,7 @@ class MPCConfig:
     seed: int = 0            # seed of the batch draws
     free_goal: bool = True   # move the goal sideways off people (see goal_state)
     resample: bool = False   # re-draw the batch every step (else keep xi as well as lambda)
+    shift: bool = True       # kept xi: re-time it by the control period (am_shift)
     select: int = TJ.AM_SELECT_CLEARANCE  # when no plan is collision-free, take the one with the most clearance
     margin: float = 0.2      # added to the people's radius in the planner only (m)
 
@@ -125,7 +126,8 @@ def episode_metrics(states: np.ndarray, t: np.ndarray, crowd: dict) -> dict:
 
     states: (len(t), 9) rows x, x', x'', y, y', y'', psi, psi', psi''.
     Tracking error: mean over time of the distance to the desired point
-    (v_des t, 0); acceleration: mean over time of |(x'', y'')|.
+    (v_des t, 0) (and that distance at the last sample); acceleration: mean
+    over time of |(x'', y'')|.
     """
     clear = circle_clearance(states, crowd, t)
     hit = np.nonzero(clear < 0.99)[0]
@@ -133,7 +135,7 @@ def episode_metrics(states: np.ndarray, t: np.ndarray, crowd: dict) -> dict:
     acc = np.hypot(states[:, 2], states[:, 5])
     return dict(success=bool(hit.size == 0), collision_time=float(t[hit[0]]) if hit.size else None,
                 min_clearance=float(clear.min()), tracking_error=float(err.mean()),
-                acceleration=float(acc.mean()))
+                final_tracking_error=float(err[-1]), acceleration=float(acc.mean()))
 
 
 def run(crowds: list[dict], cfg: MPCConfig, budget_bytes: int = 16 << 30) -> dict:
@@ -164,7 +166,7 @@ def run(crowds: list[dict], cfg: MPCConfig, budget_bytes: int = 16 << 30) -> dic
                 tickets.append(server.submit(e, advance=cfg.dt if k else 0.0, xo=xo, yo=yo,
                                              goal=goal_state(crowd, t, cfg),
                                              resample_seed=seed if (cfg.resample or k == 0) else None,
-                                             sigma=cfg.sigma))
+                                             sigma=cfg.sigma, shift=cfg.shift))
             for e, tk in enumerate(tickets):
                 r = server.wait(tk)
                 if r["status"] != TJ.AM_OK:

@@ -24,13 +24,13 @@ AM_SELECT_COST, AM_SELECT_CLEARANCE = 0, 1
 AM_GOPT_THREADS, AM_GOPT_GRAPH = 1, 2
 AM_PENDING = 1
 AM_SRV_BATCHED, AM_SRV_SEQUENTIAL = 0, 1
-AM_REQ_GOAL, AM_REQ_RESAMPLE = 1, 2
+AM_REQ_GOAL, AM_REQ_RESAMPLE, AM_REQ_SHIFT = 1, 2, 4
 AM_NV, AM_STATE_FLOATS = 11, 110
 
 EXPORTS = ["am_init_problem", "am_set_obstacles", "am_set_boundary", "am_solve_batch",
            "am_get_results", "am_get_best", "am_get_state", "am_set_state", "am_set_history",
            "am_get_history", "am_set_option", "am_set_stream", "am_last_solve_stats",
-           "am_solve_batch_noalloc", "am_init_state", "am_resample", "am_plan_eval", "am_group_create", "am_group_solve",
+           "am_solve_batch_noalloc", "am_init_state", "am_resample", "am_shift", "am_plan_eval", "am_group_create", "am_group_solve",
            "am_group_autotune", "am_group_set_option", "am_group_set_active", "am_group_get_best",
            "am_group_stats", "am_group_destroy", "am_server_create", "am_server_add_scene",
            "am_server_start", "am_server_submit", "am_server_poll", "am_server_stats",
@@ -92,6 +92,7 @@ def _load():
         "am_solve_batch_noalloc": ([vp, ip, fp, fp, fp, fp, fp, ip, vp], ip),
         "am_init_state": ([vp, ip, fp, fp, vp, ip], ip),
         "am_resample": ([vp, C.c_ulonglong, C.c_float, vp], ip),
+        "am_shift": ([vp, C.c_double, vp], ip),
         "am_plan_eval": ([fp, C.c_double, ip, fp, fp], ip),
         "am_group_create": ([C.POINTER(vp), ip, C.POINTER(vp)], ip),
         "am_group_solve": ([vp, ip, vp], ip),
@@ -268,6 +269,10 @@ def am_resample(h, seed, sigma=1.0, stream=None):
     _check(_lib.am_resample(h, int(seed) & (2**64 - 1), float(sigma), _stream_ptr(stream)))
 
 
+def am_shift(h, dt, stream=None):
+    _check(_lib.am_shift(h, float(dt), _stream_ptr(stream)))
+
+
 def am_plan_eval(coeffs, T, t):
     """x, x', x'', y, y', y'', psi, psi', psi'' of a plan at the times t: (len(t), 9)."""
     c = np.ascontiguousarray(coeffs, dtype=np.float32).reshape(33)
@@ -338,9 +343,11 @@ def am_server_start(s):
 
 
 def am_server_submit(s, scene, advance=0.0, xo=None, yo=None, goal=None, resample_seed=None,
-                     sigma=1.0) -> int:
+                     sigma=1.0, shift=False) -> int:
     keep = []
     r = AmRequest(int(scene), float(advance), None, None)
+    if shift:
+        r.flags |= AM_REQ_SHIFT
     if goal is not None:
         r.flags |= AM_REQ_GOAL
         for k, v in enumerate(np.asarray(goal, dtype=np.float64).reshape(9)):
@@ -418,6 +425,10 @@ class Problem:
     def init_state(self, init, warm_lambda=None, stream=None):
         am_init_state(self.h, int(init.shape[0]), init, warm_lambda, stream)
         self.B = int(init.shape[0])
+        return self
+
+    def shift(self, dt, stream=None):
+        am_shift(self.h, dt, stream)
         return self
 
     def resample(self, seed, sigma=1.0, stream=None):
@@ -529,11 +540,13 @@ class Server:
         am_server_start(self.s)
         return self
 
-    def submit(self, scene, advance=0.0, xo=None, yo=None, goal=None, resample_seed=None, sigma=1.0):
+    def submit(self, scene, advance=0.0, xo=None, yo=None, goal=None, resample_seed=None, sigma=1.0,
+               shift=False):
         """goal: 9 values (x, x', x'', y, y', y'', psi, psi', psi'' at t = T);
         resample_seed: re-draw the scene's batch around the new straight line
-        with that seed (multipliers kept)."""
-        return am_server_submit(self.s, scene, advance, xo, yo, goal, resample_seed, sigma)
+        with that seed (multipliers kept); shift: re-time the batch by the
+        advance (am_shift)."""
+        return am_server_submit(self.s, scene, advance, xo, yo, goal, resample_seed, sigma, shift)
 
     def poll(self, ticket, timeout_ms=0):
         return am_server_poll(self.s, ticket, timeout_ms)

@@ -135,17 +135,19 @@ def test_server_goal_and_advance():
 
 
 def test_closed_loop_free_space():
-    """One person far off the line: every episode succeeds and the robot
-    follows the line (it starts at rest, so it lags the desired point)."""
+    """One person far off the line: every episode succeeds, and the robot,
+    which starts at rest behind the desired point, catches up (its final
+    distance to the desired point is below its mean distance)."""
     far = dict(kind="static", seed=0, n=1, p0=np.array([[10.0, 30.0]]), v=np.zeros((1, 2)),
                radius=0.3, v_des=1.0)
-    cfg = M.MPCConfig(batch=64, duration=8.0)
+    cfg = M.MPCConfig(batch=64, duration=12.0)
     out = M.run([far, dict(far, seed=1)], cfg)
     s = M.summarize(out["episodes"])
     assert s["success_rate"] == 1.0
-    assert s["tracking_error_m"]["max"] < 2.0
+    for e in out["episodes"]:
+        assert e["final_tracking_error"] < e["tracking_error"] < 4.0
     assert s["acceleration_mps2"]["max"] < cfg.a_max
-    assert out["steps"] == 80 and out["replan_ms"]["p50"] > 0
+    assert out["steps"] == 120 and out["replan_ms"]["p50"] > 0
 
 
 @pytest.mark.parametrize("batch", [1, 256])
@@ -195,3 +197,37 @@ def test_selection_rules(blocked):
         P.close()
     if not blocked:
         assert picks[0] == picks[1]
+
+
+def test_shift_retimes_every_polynomial():
+    """After am_shift(dt) each polynomial of the batch evaluated at t equals the
+    old one at t + dt (values and both derivatives), for the five polynomials;
+    the multipliers are untouched; dt = 0 is the identity."""
+    T = tj()
+    pb = W.make_problem("paper", 0, B=256)
+    P = T.Problem(pb)
+    P.solve(pb["init"].astype(np.float32), 5)
+    old = P.state()
+    dt = 0.37
+    P.shift(dt)
+    new = P.state()
+    np.testing.assert_array_equal(new[:, 55:], old[:, 55:])
+    t = np.linspace(0.0, pb["T"] - dt, 23)
+    for l in (0, 17, 255):
+        for base in (0, 11, 22, 33, 44):
+            a = np.zeros(33, np.float32)
+            b = np.zeros(33, np.float32)
+            a[:11] = new[l, base:base + 11]
+            b[:11] = old[l, base:base + 11]
+            ea = T.am_plan_eval(a, pb["T"], t)[:, :3]
+            eb = T.am_plan_eval(b, pb["T"], t + dt)[:, :3]
+            scale = np.abs(b[:11]).max() + 1.0
+            for d, unit in enumerate((1.0, 10.0 / pb["T"], 100.0 / pb["T"] ** 2)):
+                np.testing.assert_allclose(ea[:, d], eb[:, d], atol=2e-5 * scale * unit)
+    P.shift(0.0)
+    np.testing.assert_allclose(P.state(), new, atol=1e-6)
+    for bad in (-0.1, pb["T"] + 0.1, float("nan")):
+        with pytest.raises(T.TrajamError) as e:
+            P.shift(bad)
+        assert e.value.code == T.AM_ERR_ARG
+    P.close()
