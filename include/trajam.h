@@ -164,6 +164,44 @@ AM_API int am_resample(am_problem *h, unsigned long long seed, float sigma, void
  * requires a state. */
 AM_API int am_shift(am_problem *h, double dt, void *stream);
 
+/* Cross-entropy method planner on the handle's problem: the sampling-based
+ * comparator of Sec. IV (Table IV; the paper runs it with 8k samples).  The
+ * search space is z = control points 3..7 of c_x, c_y and c_psi (the others
+ * come from the boundary conditions).  Each iteration draws `samples` z from
+ * N(mu, Sigma) (counter-based normals as in am_resample, stream = iteration
+ * x 2^24 + sample), scores them with
+ *   J = sum_t (x''^2 + y''^2 + psi''^2) + w_coll sum_{t,i,j} max(0, 1 - d_ij)^2
+ *       + w_bound sum_t (max(0, |v| - v_max)^2 + max(0, |a| - a_max)^2)
+ * (d_ij the ellipse distance of circle i to the inflated obstacle j at step
+ * t), and refits mu, Sigma to the `elites` lowest (ties to the lower index):
+ * mu <- alpha mean + (1 - alpha) mu, Sigma <- alpha cov + (1 - alpha) Sigma
+ * + reg I, cov normalised by the elite count.  Start: mu = the straight line
+ * between the boundary positions and headings (or, with warm, control
+ * points 3..7 of the plan warm re-timed by warm_dt as in am_shift), Sigma =
+ * blockdiag(sigma_xy^2 C, sigma_xy^2 C, sigma_psi^2 C), C the covariance of
+ * am_resample.  The result is the lowest J over all iterations.  Bounds:
+ * 16 <= samples <= 8192, 2 <= elites <= min(samples, 1024), iters >= 1. */
+typedef struct {
+    int samples, elites, iters;
+    float sigma_xy, sigma_psi;  /* initial spread (m, rad)                     */
+    float alpha, reg;           /* smoothing in (0, 1]; covariance floor > 0   */
+    float w_coll, w_bound;      /* penalty weights >= 0                        */
+    unsigned long long seed;
+    const float *warm;          /* nullable: 33 floats (c_x, c_y, c_psi), host */
+    double warm_dt;             /* re-timing of warm, 0 <= warm_dt <= T        */
+} am_cem_desc;
+AM_API int am_cem_solve(am_problem *h, const am_cem_desc *d, void *stream);
+/* Best plan of the last am_cem_solve (waits for it): coefficients (33), J and
+ * its smallest ellipse distance. */
+AM_API int am_cem_get_best(am_problem *h, float coeffs[33], float *cost, float *min_dist);
+/* Samples (N x 15) and scores (N) of the last iteration, and mu (15) and
+ * Sigma (15 x 15) after its refit (any output may be NULL; host memory). */
+AM_API int am_cem_get_samples(am_problem *h, float *z, float *cost, float *mu, float *sigma);
+/* Score `count` (1..8192) given plans (count x 33 floats, host) with J above:
+ * cost and min_dist get count floats each (host). */
+AM_API int am_cem_score(am_problem *h, int count, const float *coeffs, float w_coll, float w_bound,
+                        float *cost, float *min_dist);
+
 /* Evaluate a plan (c_x, c_y, c_psi: 33 floats, host) of horizon T at `count`
  * times t[i] (clamped to [0, T]): out[9 i ..] = x, x', x'', y, y', y'', psi,
  * psi', psi'' (derivatives in 1/s, 1/s^2; Eq. param).  Host arithmetic in

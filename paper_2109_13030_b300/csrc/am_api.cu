@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cfloat>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -90,6 +91,10 @@ struct am_problem {
     int diag_stall = 0;
     int select = AM_SELECT_COST;
     float *h_best = nullptr;  // pinned
+    // CEM comparator: samples, scores, distribution and best of the last run
+    float *d_cem = nullptr, *d_score = nullptr;
+    size_t cem_cap = 0, score_cap = 0;
+    int cem_N = 0;
 };
 
 namespace {
@@ -262,6 +267,8 @@ void am_destroy(am_problem *h)
     cudaFree(h->d_hist);
     cudaFree(h->d_scratch);
     cudaFree(h->d_err);
+    cudaFree(h->d_cem);
+    cudaFree(h->d_score);
     if (h->h_best) cudaFreeHost(h->h_best);
     if (h->ev) cudaEventDestroy(h->ev);
     delete h;
@@ -865,6 +872,173 @@ int am_shift(am_problem *h, double dt, void *stream)
     a.B = h->B;
     if (launch_shift(h->d_state, a, h->stream, nullptr)) return fail(AM_ERR_CUDA, "shift launch failed");
     return AM_OK;
+}
+
+namespace {
+
+// Float offsets of the CEM buffer for N samples.
+struct CemLayout {
+    size_t z, cost, dmin, mu, sig, chol, best, total;
+};
+
+CemLayout cem_layout(int N)
+{
+    CemLayout c;
+    c.z = 0;
+    c.cost = size_t(N) * 15;
+    c.dmin = c.cost + N;
+    c.mu = (c.dmin + N + 3) & ~size_t(3);
+    c.sig = c.mu + 16;
+    c.chol = c.sig + 228;
+    c.best = c.chol + 228;
+    c.total = c.best + 64;
+    return c;
+}
+
+bool finite_nonneg(double v) { return std::isfinite(v) && v >= 0.0; }
+
+}  // namespace
+
+int am_cem_solve(am_problem *h, const am_cem_desc *d, void *stream)
+{
+    if (!h || !d) return fail(AM_ERR_ARG, "null argument");
+    if (d->samples < 16 || d->samples > 8192) return fail(AM_ERR_ARG, "samples must be in [16, 8192]");
+    if (d->elites < 2 || d->elites > d->samples || d->elites > 1024)
+        return fail(AM_ERR_ARG, "elites must be in [2, min(samples, 1024)]");
+    if (d->iters < 1) return fail(AM_ERR_ARG, "iters must be >= 1");
+    if (!finite_nonneg(d->sigma_xy) || !finite_nonneg(d->sigma_psi) || !finite_nonneg(d->w_coll) ||
+        !finite_nonneg(d->w_bound))
+        return fail(AM_ERR_ARG, "spreads and weights must be finite and >= 0");
+    if (!(d->alpha > 0.f && d->alpha <= 1.f)) return fail(AM_ERR_ARG, "alpha must be in (0, 1]");
+    if (!(d->reg > 0.f) || !std::isfinite(d->reg)) return fail(AM_ERR_ARG, "reg must be finite and > 0");
+    if (d->warm) {
+        if (!(d->warm_dt >= 0.0 && d->warm_dt <= h->pp.T)) return fail(AM_ERR_ARG, "warm_dt must be in [0, T]");
+        for (int k = 0; k < 33; ++k)
+            if (!std::isfinite(d->warm[k])) return fail(AM_ERR_ARG, "non-finite warm plan");
+    }
+    h->stream = static_cast<cudaStream_t>(stream);
+    NvtxRange nvtx("am_cem_solve");
+    const int N = d->samples;
+    const CemLayout c = cem_layout(N);
+    int rc = ensure(h->d_cem, h->cem_cap, c.total, "CEM buffers");
+    if (rc) return rc;
+    // starting distribution (FP64 on the host)
+    double mu0[15];
+    if (d->warm) {
+        double S[121];
+        shift_matrix(d->warm_dt / h->pp.T, S);
+        for (int b = 0; b < 3; ++b)
+            for (int i = 0; i < 5; ++i) {
+                double v = 0.0;
+                for (int j = 0; j < NV; ++j) v += S[(3 + i) * NV + j] * d->warm[11 * b + j];
+                mu0[5 * b + i] = v;
+            }
+    } else {
+        const double *bc[3] = {h->pp.x_bc, h->pp.y_bc, h->pp.psi_bc};
+        for (int b = 0; b < 3; ++b)
+            for (int i = 0; i < 5; ++i) mu0[5 * b + i] = bc[b][0] + (bc[b][3] - bc[b][0]) * (i + 1) / 6.0;
+    }
+    double Lc[25];
+    init_cov_factor(Lc);
+    std::vector<float> up(c.total - c.mu, 0.f);
+    float *mu = up.data(), *sig = mu + (c.sig - c.mu), *chol = mu + (c.chol - c.mu), *best = mu + (c.best - c.mu);
+    for (int k = 0; k < 15; ++k) mu[k] = float(mu0[k]);
+    for (int b = 0; b < 3; ++b) {
+        const double s = b < 2 ? d->sigma_xy : d->sigma_psi;
+        for (int i = 0; i < 5; ++i)
+            for (int j = 0; j < 5; ++j) {
+                double cov = 0.0;
+                for (int k = 0; k < 5; ++k) cov += Lc[i * 5 + k] * Lc[j * 5 + k];
+                sig[(5 * b + i) * 15 + 5 * b + j] = float(s * s * cov);
+                chol[(5 * b + i) * 15 + 5 * b + j] = float(s * Lc[i * 5 + j]);
+            }
+    }
+    best[15] = FLT_MAX;
+    CK(cudaMemcpyAsync(h->d_cem + c.mu, up.data(), sizeof(float) * up.size(), cudaMemcpyHostToDevice, h->stream),
+       "CEM start copy");
+    CemArgs a;
+    a.cblob = h->d_blob;
+    a.L = h->L;
+    a.z = h->d_cem + c.z;
+    a.cost = h->d_cem + c.cost;
+    a.dmin = h->d_cem + c.dmin;
+    a.mu = h->d_cem + c.mu;
+    a.sig = h->d_cem + c.sig;
+    a.chol = h->d_cem + c.chol;
+    a.best = h->d_cem + c.best;
+    a.given = nullptr;
+    a.N = N;
+    a.K = d->elites;
+    a.NP = 1;
+    while (a.NP < N) a.NP <<= 1;
+    a.seed = d->seed;
+    a.w_coll = d->w_coll;
+    a.w_bound = d->w_bound;
+    a.alpha = d->alpha;
+    a.reg = d->reg;
+    h->cem_N = 0;
+    for (int it = 0; it < d->iters; ++it) {
+        a.iter = it;
+        if (launch_cem_score(a, h->stream) || launch_cem_refit(a, h->stream))
+            return fail(AM_ERR_CUDA, "CEM launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    }
+    h->cem_N = N;
+    return AM_OK;
+}
+
+int am_cem_get_best(am_problem *h, float coeffs[33], float *cost, float *min_dist)
+{
+    if (!h || !coeffs) return fail(AM_ERR_ARG, "null argument");
+    if (h->cem_N < 1) return fail(AM_ERR_STATE, "no CEM run yet");
+    const CemLayout c = cem_layout(h->cem_N);
+    float b[64];
+    CK(cudaMemcpyAsync(b, h->d_cem + c.best, sizeof(b), cudaMemcpyDeviceToHost, h->stream), "CEM best copy");
+    int rc = wait_stream(h);
+    if (rc) return rc;
+    std::memcpy(coeffs, b + 17, 33 * sizeof(float));
+    if (cost) *cost = b[15];
+    if (min_dist) *min_dist = b[16];
+    return b[15] < FLT_MAX ? AM_OK : fail(AM_ERR_NAN, "every CEM sample scored non-finite");
+}
+
+int am_cem_get_samples(am_problem *h, float *z, float *cost, float *mu, float *sigma)
+{
+    if (!h) return fail(AM_ERR_ARG, "null handle");
+    if (h->cem_N < 1) return fail(AM_ERR_STATE, "no CEM run yet");
+    const int N = h->cem_N;
+    const CemLayout c = cem_layout(N);
+    if (z) CK(cudaMemcpyAsync(z, h->d_cem + c.z, sizeof(float) * 15 * N, cudaMemcpyDeviceToHost, h->stream), "copy");
+    if (cost) CK(cudaMemcpyAsync(cost, h->d_cem + c.cost, sizeof(float) * N, cudaMemcpyDeviceToHost, h->stream), "copy");
+    if (mu) CK(cudaMemcpyAsync(mu, h->d_cem + c.mu, sizeof(float) * 15, cudaMemcpyDeviceToHost, h->stream), "copy");
+    if (sigma) CK(cudaMemcpyAsync(sigma, h->d_cem + c.sig, sizeof(float) * 225, cudaMemcpyDeviceToHost, h->stream), "copy");
+    return wait_stream(h);
+}
+
+int am_cem_score(am_problem *h, int count, const float *coeffs, float w_coll, float w_bound, float *cost,
+                 float *min_dist)
+{
+    if (!h || !coeffs || !cost || !min_dist) return fail(AM_ERR_ARG, "null argument");
+    if (count < 1 || count > 8192) return fail(AM_ERR_ARG, "count must be in [1, 8192]");
+    if (!finite_nonneg(w_coll) || !finite_nonneg(w_bound)) return fail(AM_ERR_ARG, "weights must be finite and >= 0");
+    for (size_t k = 0; k < size_t(count) * 33; ++k)
+        if (!std::isfinite(coeffs[k])) return fail(AM_ERR_ARG, "non-finite coefficient");
+    int rc = ensure(h->d_score, h->score_cap, size_t(count) * 35, "CEM score buffers");
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(h->d_score, coeffs, sizeof(float) * 33 * count, cudaMemcpyHostToDevice, h->stream),
+       "plan copy");
+    CemArgs a{};
+    a.cblob = h->d_blob;
+    a.L = h->L;
+    a.given = h->d_score;
+    a.cost = h->d_score + size_t(33) * count;
+    a.dmin = a.cost + count;
+    a.N = count;
+    a.w_coll = w_coll;
+    a.w_bound = w_bound;
+    if (launch_cem_score(a, h->stream)) return fail(AM_ERR_CUDA, "score launch failed");
+    CK(cudaMemcpyAsync(cost, a.cost, sizeof(float) * count, cudaMemcpyDeviceToHost, h->stream), "copy");
+    CK(cudaMemcpyAsync(min_dist, a.dmin, sizeof(float) * count, cudaMemcpyDeviceToHost, h->stream), "copy");
+    return wait_stream(h);
 }
 
 int am_plan_eval(const float coeffs[33], double T, int count, const double *t, double *out)

@@ -5,6 +5,7 @@
 #include <cfloat>
 
 #include "am_internal.h"
+#include "am_rng.cuh"
 
 namespace trajam {
 namespace {
@@ -30,24 +31,6 @@ __global__ void init_state_kernel(float *state, const float *init, const float *
     state[i] = v;
 }
 
-// SplitMix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number
-// generators", OOPSLA 2014): one output of the generator whose state is x.
-__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x)
-{
-    unsigned long long z = x + 0x9E3779B97F4A7C15ull;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-
-// Uniform in (0, 1) for draw k of trajectory l: the top 53 bits of
-// SplitMix64(seed XOR SplitMix64(256 l + k)), offset by half a unit.
-__device__ __forceinline__ double uniform_draw(unsigned long long seed, int l, int k)
-{
-    const unsigned long long z = splitmix64(seed ^ splitmix64(256ull * (unsigned long long)l + k));
-    return (double(z >> 11) + 0.5) * (1.0 / 9007199254740992.0);
-}
-
 // Batch re-draw (am_resample): one thread per trajectory.  Ten standard
 // normals from five Box-Muller pairs (draws 2p, 2p + 1), z_x = 0..4 and
 // z_y = 5..9; trajectory 0 takes none.  Control points 3..7 of c_x, c_y are the
@@ -60,14 +43,8 @@ __global__ void resample_kernel(float *state, ResampleArgs a)
     if (l >= a.B) return;
     double z[10];
     for (int p = 0; p < 5; ++p) {
-        double r = 0.0, c = 0.0, s = 0.0;
-        if (l > 0) {
-            const double u1 = uniform_draw(a.seed, l, 2 * p), u2 = uniform_draw(a.seed, l, 2 * p + 1);
-            r = sqrt(-2.0 * log(u1));
-            sincospi(2.0 * u2, &s, &c);
-        }
-        z[2 * p] = r * c;
-        z[2 * p + 1] = r * s;
+        z[2 * p] = z[2 * p + 1] = 0.0;
+        if (l > 0) normal_pair(a.seed, (unsigned long long)l, p, z[2 * p], z[2 * p + 1]);
     }
     float *st = state + (size_t)l * STATE;
     for (int k = 0; k < NV; ++k) {

@@ -213,6 +213,24 @@ struct ShiftArgs {
 };
 int launch_shift(float *state, const ShiftArgs &a, void *stream, int *launches);
 
+// CEM comparator (am_cem_*): device buffers and settings of one run.
+struct CemArgs {
+    const float *cblob;
+    ConstLayout L;
+    float *z, *cost, *dmin;    // N x 15 samples, N scores, N smallest ellipse distances
+    float *mu, *sig, *chol;    // 15, 15 x 15, 15 x 15 (lower)
+    float *best;               // z (15), J, d_min, coefficients (33)
+    const float *given;        // nullable: score these N x 33 coefficient vectors instead
+    int N, K, NP;              // samples, elites, N rounded up to a power of two
+    int iter;
+    unsigned long long seed;
+    float w_coll, w_bound, alpha, reg;
+};
+size_t cem_score_smem(const ConstLayout &L);
+size_t cem_refit_smem(int NP, int K);
+int launch_cem_score(const CemArgs &a, void *stream);
+int launch_cem_refit(const CemArgs &a, void *stream);
+
 // Control points of a degree-10 Bernstein polynomial on [s, s + 1] from those on
 // [0, 1] (blossoming): row-major 11 x 11, c' = S c.
 void shift_matrix(double s, double S[121]);

@@ -192,6 +192,56 @@ def run(crowds: list[dict], cfg: MPCConfig, budget_bytes: int = 16 << 30) -> dic
                 mean_round_batch=statistics.mean(batches))
 
 
+def run_cem(crowds: list[dict], cfg: MPCConfig, **cem) -> dict:
+    """The same closed loop with the CEM comparator as the planner (Sec. IV,
+    Table IV): per step and episode one ``am_cem_solve`` on the episode's own
+    problem, warm-started from the previous best plan re-timed by dt.  The
+    boundary, goal, obstacle tracks, planning margin and metrics are those of
+    ``run``; the episodes are planned one after another.  Keyword arguments
+    override ``trajam.CEM_DEFAULTS``."""
+    steps = int(round(cfg.duration / cfg.dt))
+    tg = np.linspace(0.0, cfg.horizon, cfg.q)
+    sub = np.arange(cfg.substeps) * (cfg.dt / cfg.substeps)
+    problems = [TJ.Problem(_problem(c, cfg)) for c in crowds]
+    traj = [[] for _ in crowds]
+    feasible = [0 for _ in crowds]
+    plans = [None for _ in crowds]
+    lat = []
+    t_wall = time.perf_counter()
+    try:
+        for k in range(steps):
+            t = k * cfg.dt
+            for e, crowd in enumerate(crowds):
+                P = problems[e]
+                xo, yo = W.crowd_positions(crowd, t + tg)
+                rad = np.full(crowd["n"], crowd["radius"] + cfg.margin)
+                P.set_obstacles(xo, yo, rad, rad)
+                start = np.zeros(9) if plans[e] is None else TJ.am_plan_eval(plans[e], cfg.horizon, [cfg.dt])[0]
+                g = goal_state(crowd, t, cfg)
+                P.set_boundary(np.r_[start[0:3], g[0:3]], np.r_[start[3:6], g[3:6]], np.r_[start[6:9], g[6:9]])
+                t0 = time.perf_counter()
+                seed = ((cfg.seed * 1_000_003 + e) * 1_000_033 + k) & (2**64 - 1)
+                TJ.am_cem_solve(P.h, warm=plans[e], warm_dt=cfg.dt if plans[e] is not None else 0.0,
+                                **dict(dict(seed=seed), **cem))
+                best = TJ.am_cem_get_best(P.h)
+                lat.append(time.perf_counter() - t0)
+                plans[e] = best["coeffs"]
+                traj[e].append(TJ.am_plan_eval(plans[e], cfg.horizon, sub))
+                plan = TJ.am_plan_eval(plans[e], cfg.horizon, tg)
+                feasible[e] += int(circle_clearance(plan, crowd, t + tg).min() >= 0.99)
+        wall = time.perf_counter() - t_wall
+    finally:
+        for P in problems:
+            P.close()
+    times = np.arange(steps * cfg.substeps) * (cfg.dt / cfg.substeps)
+    episodes = [dict(kind=c["kind"], seed=c["seed"], feasible_plans=f / steps,
+                     **episode_metrics(np.concatenate(s), times, c))
+                for c, s, f in zip(crowds, traj, feasible)]
+    lat_ms = sorted(1e3 * x for x in lat)
+    return dict(episodes=episodes, steps=steps, wall_s=wall,
+                replan_ms={"p50": lat_ms[len(lat_ms) // 2], "p99": lat_ms[min(len(lat_ms) - 1, int(0.99 * len(lat_ms)))]})
+
+
 def summarize(episodes: list[dict]) -> dict:
     """Table III-style statistics: success rate, tracking error and
     acceleration as mean / max / min over episodes (and the share of control

@@ -30,7 +30,8 @@ AM_NV, AM_STATE_FLOATS = 11, 110
 EXPORTS = ["am_init_problem", "am_set_obstacles", "am_set_boundary", "am_solve_batch",
            "am_get_results", "am_get_best", "am_get_state", "am_set_state", "am_set_history",
            "am_get_history", "am_set_option", "am_set_stream", "am_last_solve_stats",
-           "am_solve_batch_noalloc", "am_init_state", "am_resample", "am_shift", "am_plan_eval", "am_group_create", "am_group_solve",
+           "am_solve_batch_noalloc", "am_init_state", "am_resample", "am_shift", "am_plan_eval", "am_cem_solve",
+           "am_cem_get_best", "am_cem_get_samples", "am_cem_score", "am_group_create", "am_group_solve",
            "am_group_autotune", "am_group_set_option", "am_group_set_active", "am_group_get_best",
            "am_group_stats", "am_group_destroy", "am_server_create", "am_server_add_scene",
            "am_server_start", "am_server_submit", "am_server_poll", "am_server_stats",
@@ -64,6 +65,13 @@ class AmResult(C.Structure):
                 ("batch", C.c_int)]
 
 
+class AmCemDesc(C.Structure):
+    _fields_ = [("samples", C.c_int), ("elites", C.c_int), ("iters", C.c_int),
+                ("sigma_xy", C.c_float), ("sigma_psi", C.c_float), ("alpha", C.c_float), ("reg", C.c_float),
+                ("w_coll", C.c_float), ("w_bound", C.c_float), ("seed", C.c_ulonglong),
+                ("warm", C.c_void_p), ("warm_dt", C.c_double)]
+
+
 class TrajamError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"trajam error {code}: {msg}")
@@ -93,6 +101,10 @@ def _load():
         "am_init_state": ([vp, ip, fp, fp, vp, ip], ip),
         "am_resample": ([vp, C.c_ulonglong, C.c_float, vp], ip),
         "am_shift": ([vp, C.c_double, vp], ip),
+        "am_cem_solve": ([vp, C.POINTER(AmCemDesc), vp], ip),
+        "am_cem_get_best": ([vp, fp, C.POINTER(C.c_float), C.POINTER(C.c_float)], ip),
+        "am_cem_get_samples": ([vp, fp, fp, fp, fp], ip),
+        "am_cem_score": ([vp, ip, fp, C.c_float, C.c_float, fp, fp], ip),
         "am_plan_eval": ([fp, C.c_double, ip, fp, fp], ip),
         "am_group_create": ([C.POINTER(vp), ip, C.POINTER(vp)], ip),
         "am_group_solve": ([vp, ip, vp], ip),
@@ -271,6 +283,49 @@ def am_resample(h, seed, sigma=1.0, stream=None):
 
 def am_shift(h, dt, stream=None):
     _check(_lib.am_shift(h, float(dt), _stream_ptr(stream)))
+
+
+CEM_DEFAULTS = dict(samples=8000, elites=800, iters=15, sigma_xy=1.0, sigma_psi=0.3, alpha=0.8, reg=1e-3,
+                    w_coll=1e4, w_bound=1e2, seed=0)
+
+
+def am_cem_solve(h, stream=None, warm=None, warm_dt=0.0, **kw):
+    """Cross-entropy method on the handle's problem (see am_cem_solve in the
+    header); keyword arguments override CEM_DEFAULTS."""
+    o = dict(CEM_DEFAULTS, **kw)
+    keep = None
+    d = AmCemDesc(int(o["samples"]), int(o["elites"]), int(o["iters"]), float(o["sigma_xy"]),
+                  float(o["sigma_psi"]), float(o["alpha"]), float(o["reg"]), float(o["w_coll"]),
+                  float(o["w_bound"]), int(o["seed"]) & (2**64 - 1), None, float(warm_dt))
+    if warm is not None:
+        keep = np.ascontiguousarray(warm, dtype=np.float32).reshape(33)
+        d.warm = keep.ctypes.data
+    _check(_lib.am_cem_solve(h, C.byref(d), _stream_ptr(stream)))
+
+
+def am_cem_get_best(h):
+    c = np.zeros(33, dtype=np.float32)
+    cost, md = C.c_float(), C.c_float()
+    _check(_lib.am_cem_get_best(h, c.ctypes.data, C.byref(cost), C.byref(md)))
+    return dict(coeffs=c.reshape(3, 11), cost=cost.value, min_dist=md.value)
+
+
+def am_cem_get_samples(h, n):
+    z = np.zeros((n, 15), dtype=np.float32)
+    cost = np.zeros(n, dtype=np.float32)
+    mu = np.zeros(15, dtype=np.float32)
+    sig = np.zeros((15, 15), dtype=np.float32)
+    _check(_lib.am_cem_get_samples(h, z.ctypes.data, cost.ctypes.data, mu.ctypes.data, sig.ctypes.data))
+    return dict(z=z, cost=cost, mu=mu, sigma=sig)
+
+
+def am_cem_score(h, coeffs, w_coll=1e4, w_bound=1e2):
+    c = np.ascontiguousarray(coeffs, dtype=np.float32).reshape(-1, 33)
+    cost = np.zeros(c.shape[0], dtype=np.float32)
+    md = np.zeros(c.shape[0], dtype=np.float32)
+    _check(_lib.am_cem_score(h, c.shape[0], c.ctypes.data, float(w_coll), float(w_bound), cost.ctypes.data,
+                             md.ctypes.data))
+    return cost, md
 
 
 def am_plan_eval(coeffs, T, t):

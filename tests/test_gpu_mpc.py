@@ -231,3 +231,12 @@ def test_shift_retimes_every_polynomial():
             P.shift(bad)
         assert e.value.code == T.AM_ERR_ARG
     P.close()
+
+
+def test_closed_loop_with_cem_runs():
+    from paper_2109_13030_b300 import mpc as M2
+    crowds = [W.make_crowd(k, 12) for k in W.CROWD_KINDS]
+    out = M2.run_cem(crowds, M2.MPCConfig(duration=2.0), samples=1024, elites=100, iters=5)
+    assert len(out["episodes"]) == 3 and out["steps"] == 20
+    for e in out["episodes"]:
+        assert np.isfinite(e["tracking_error"]) and e["min_clearance"] > 0
