@@ -326,7 +326,7 @@ def bench_serving(TJ, W, seconds: float, plain_seconds: float) -> dict:
     return out
 
 
-def bench_closed_loop(episodes: int, batches=(1, 200, 1000)) -> dict:
+def bench_closed_loop(episodes: int, cem_episodes: int, batches=(1, 200, 1000)) -> dict:
     """Closed-loop MPC on the crowd benchmarks of Sec. IV (Table III's
     metrics against batch size): `episodes` scenes per benchmark (static,
     same-direction, opposite flow), 20 s at 10 Hz, 10 iterations per re-plan,
@@ -351,6 +351,21 @@ def bench_closed_loop(episodes: int, batches=(1, 200, 1000)) -> dict:
         row["control_steps"] = r["steps"]
         row["loop_wall_s"] = r["wall_s"]
         out["by_batch"][str(batch)] = row
+    if cem_episodes > 0:
+        # the CEM comparator (Table IV) on the first cem_episodes scenes of each benchmark,
+        # at the AM loop's budget (1000 samples x 10 iterations) and at the paper's 8000 samples
+        sub = [c for c in crowds if c["seed"] < cem_episodes]
+        out["cem"] = {"episodes": len(sub), "planned": "one episode at a time, warm mean from the previous plan"}
+        for name, kw in (("samples_1000_iters_10", dict(samples=1000, elites=100, iters=10)),
+                         ("samples_8000_iters_15", dict(samples=8000, elites=800, iters=15))):
+            r = M.run_cem(sub, cfg, **kw)
+            row = M.summarize(r["episodes"])
+            row["replan_ms"] = r["replan_ms"]
+            out["cem"][name] = row
+        r = M.run(sub, M.MPCConfig(batch=1000))
+        row = M.summarize(r["episodes"])
+        row["replan_ms"] = r["replan_ms"]
+        out["cem"]["am_batch_1000_same_episodes"] = row
     return out
 
 
@@ -403,6 +418,7 @@ def main():
     ap.add_argument("--precision-steps", type=int, default=3)
     ap.add_argument("--jsonl", default=None, help="also append the JSON line to this file")
     ap.add_argument("--mpc-episodes", type=int, default=20, help="closed-loop episodes per crowd benchmark (0: skip)")
+    ap.add_argument("--cem-episodes", type=int, default=5, help="of those, episodes per benchmark for the CEM rows")
     ap.add_argument("--profile-plain", type=int, default=0, metavar="B",
                     help="profiling aid: solve 2 iterations of the paper-shaped scene at batch B with the "
                          "plain loop and exit (no JSON line)")
@@ -577,7 +593,7 @@ def main():
         if args.serve_seconds > 0:
             line["serving"] = bench_serving(TJ, W, args.serve_seconds, args.serve_plain_seconds)
         if args.mpc_episodes > 0:
-            line["closed_loop"] = bench_closed_loop(args.mpc_episodes)
+            line["closed_loop"] = bench_closed_loop(args.mpc_episodes, min(args.cem_episodes, args.mpc_episodes))
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(pb, B, ITERS)
         print(json.dumps(line), flush=True)
