@@ -25,7 +25,9 @@ namespace trajam {
 namespace {
 
 constexpr int kCemWarps = 8;   // samples in flight per block of the scoring kernel
+constexpr int kCemObsSmem = 48 * 1024;  // obstacle tracks staged in shared memory up to this size
 constexpr int kZ = 15;         // interior control points searched
+constexpr int kParts = 4;      // partial sums per statistic in the refit (225 x 4 <= 1024 threads)
 
 __device__ __forceinline__ float dot11(const float *a, const float *b)
 {
@@ -35,10 +37,14 @@ __device__ __forceinline__ float dot11(const float *a, const float *b)
     return s;
 }
 
+// Bytes of the obstacle sections (tracks and per-obstacle constants) of the constant block.
+__host__ __device__ inline int cem_obs_floats(const ConstLayout &L) { return L.off_obt - L.off_obs; }
+
 // Score samples: one warp per sample, the lanes over the time steps.  With
 // `given`, the samples are full coefficient vectors (count x 33: c_x, c_y,
-// c_psi) instead of draws.
-__global__ void __launch_bounds__(32 * kCemWarps) cem_score_kernel(CemArgs a)
+// c_psi) instead of draws.  The basis rows, and the obstacle sections when
+// they fit, are staged in shared memory once per block.
+__global__ void __launch_bounds__(32 * kCemWarps, 3) cem_score_kernel(CemArgs a)
 {
     extern __shared__ __align__(16) float cem_sm[];
     const ConstLayout &L = a.L;
@@ -46,12 +52,18 @@ __global__ void __launch_bounds__(32 * kCemWarps) cem_score_kernel(CemArgs a)
     const int nrow = 3 * L.q * 12;
     for (int i = threadIdx.x; i < nrow; i += blockDim.x) rows[i] = a.cblob[L.off_prow + i];
     float *coef = cem_sm + nrow + 36 * (threadIdx.x >> 5);   // this warp's 33 coefficients
+    const int nobs = cem_obs_floats(L);
+    const bool staged = nobs * 4 <= kCemObsSmem;
+    float *os = cem_sm + nrow + 36 * kCemWarps;      // 16-byte aligned: nrow and 36 k are multiples of 4
+    if (staged)
+        for (int i = threadIdx.x; i < nobs; i += blockDim.x) os[i] = a.cblob[L.off_obs + i];
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const unsigned full = 0xffffffffu;
     const float *ends = a.cblob + L.off_ends;
-    const float2 *obs = reinterpret_cast<const float2 *>(a.cblob + L.off_obs);
-    const float4 *obc = reinterpret_cast<const float4 *>(a.cblob + L.off_obc);
+    const float *ob = staged ? os : a.cblob + L.off_obs;
+    const float2 *obs = reinterpret_cast<const float2 *>(ob);
+    const float4 *obc = reinterpret_cast<const float4 *>(ob + (L.off_obc - L.off_obs));
     for (int s = blockIdx.x * kCemWarps + (threadIdx.x >> 5); s < a.N; s += gridDim.x * kCemWarps) {
         if (a.given) {
             // 33 coefficients over 32 lanes: lane 0 also takes the last one
@@ -88,13 +100,14 @@ __global__ void __launch_bounds__(32 * kCemWarps) cem_score_kernel(CemArgs a)
             pb += ev * ev + ea * ea;
             float sp, cp;
             sincosf(psi, &sp, &cp);
-            for (int i = 0; i < L.m; ++i) {
-                const float X = fmaf(L.r[i], cp, x), Y = fmaf(L.r[i], sp, y);
-                for (int j = 0; j < L.n; ++j) {
-                    const float2 o = obs[j * L.qs + t];
-                    const float4 c = obc[j];
+            for (int j = 0; j < L.n; ++j) {
+                const float2 o = obs[j * L.qs + t];   // one load per obstacle and step
+                const float4 c = obc[j];
+                for (int i = 0; i < L.m; ++i) {
+                    const float X = fmaf(L.r[i], cp, x), Y = fmaf(L.r[i], sp, y);
                     const float xh = fmaf(X, c.x, -o.x), yh = fmaf(Y, c.y, -o.y);
-                    const float d = sqrtf(xh * xh + yh * yh);
+                    const float D = fmaf(xh, xh, yh * yh);
+                    const float d = D * rsqrtf(D + 1e-30f);   // sqrt(D), within a few ulp
                     const float e = fmaxf(0.f, 1.f - d);
                     pc += e * e;
                     dmin = fminf(dmin, d);
@@ -129,6 +142,8 @@ __global__ void __launch_bounds__(1024) cem_refit_kernel(CemArgs a)
     float *E = cem_sm + 2 * np;          // [K][15] elite samples
     float *mn = E + a.K * kZ;            // [16] elite mean
     float *S = mn + 16;                  // [225] smoothed covariance
+    float *Lf = S + 228;                 // [225] its Cholesky factor
+    float *part = Lf + 228;              // [kParts][225] partial sums
     const int tid = threadIdx.x;
     for (int i = tid; i < np; i += blockDim.x) {
         key[i] = i < a.N ? a.cost[i] : FLT_MAX;
@@ -156,17 +171,33 @@ __global__ void __launch_bounds__(1024) cem_refit_kernel(CemArgs a)
         }
     for (int e = tid; e < a.K * kZ; e += blockDim.x) E[e] = a.z[(size_t)idx[e / kZ] * kZ + e % kZ];
     __syncthreads();
+    // elite mean and covariance: kParts threads per entry over strided elites,
+    // then one thread per entry adds the partials in a fixed order
+    const int slot = tid / kParts, pp = tid - kParts * slot;   // entry (of 225), part
+    if (slot < kZ) {
+        float s = 0.f;
+        for (int e = pp; e < a.K; e += kParts) s += E[e * kZ + slot];
+        part[pp * 225 + slot] = s;
+    }
+    __syncthreads();
     if (tid < kZ) {
         float s = 0.f;
-        for (int e = 0; e < a.K; ++e) s += E[e * kZ + tid];
+        for (int k = 0; k < kParts; ++k) s += part[k * 225 + tid];
         mn[tid] = s / float(a.K);
+    }
+    __syncthreads();
+    if (slot < kZ * kZ) {
+        const int r = slot / kZ, c = slot - kZ * r;
+        const int lo = r < c ? r : c, hi = r < c ? c : r;   // both triangles from the same sums
+        float s = 0.f;
+        for (int e = pp; e < a.K; e += kParts) s = fmaf(E[e * kZ + hi] - mn[hi], E[e * kZ + lo] - mn[lo], s);
+        part[pp * 225 + slot] = s;
     }
     __syncthreads();
     if (tid < kZ * kZ) {
         const int r = tid / kZ, c = tid - kZ * r;
-        const int lo = r < c ? r : c, hi = r < c ? c : r;   // both triangles from the same sum
         float s = 0.f;
-        for (int e = 0; e < a.K; ++e) s = fmaf(E[e * kZ + hi] - mn[hi], E[e * kZ + lo] - mn[lo], s);
+        for (int k = 0; k < kParts; ++k) s += part[k * 225 + tid];
         const float v = a.alpha * (s / float(a.K)) + (1.f - a.alpha) * a.sig[tid] + (r == c ? a.reg : 0.f);
         S[tid] = v;
         a.sig[tid] = v;
@@ -185,39 +216,69 @@ __global__ void __launch_bounds__(1024) cem_refit_kernel(CemArgs a)
                                                        : a.z[(size_t)w * kZ + 5 * b + k - 3];
     }
     __syncthreads();
-    if (tid == 0) {
-        // Cholesky of the smoothed covariance (positive definite: reg > 0)
+    if (tid < 32) {
+        // Cholesky of the smoothed covariance (positive definite: reg > 0) by
+        // the first warp, column by column: lane i < 15 owns row i
+        const int i = tid;
         for (int j = 0; j < kZ; ++j) {
-            float d = S[j * kZ + j];
-            for (int k = 0; k < j; ++k) d -= a.chol[j * kZ + k] * a.chol[j * kZ + k];
-            d = sqrtf(fmaxf(d, 1e-12f));
-            a.chol[j * kZ + j] = d;
-            for (int i = j + 1; i < kZ; ++i) {
+            float s2 = i < j ? Lf[j * kZ + i] * Lf[j * kZ + i] : 0.f;
+            for (int off = 16; off > 0; off >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+            const float d = sqrtf(fmaxf(S[j * kZ + j] - s2, 1e-12f));
+            if (i == j) Lf[j * kZ + j] = d;
+            if (i > j && i < kZ) {
                 float v = S[i * kZ + j];
-                for (int k = 0; k < j; ++k) v -= a.chol[i * kZ + k] * a.chol[j * kZ + k];
-                a.chol[i * kZ + j] = v / d;
+                for (int k = 0; k < j; ++k) v -= Lf[i * kZ + k] * Lf[j * kZ + k];
+                Lf[i * kZ + j] = v / d;
             }
-            for (int i = 0; i < j; ++i) a.chol[i * kZ + j] = 0.f;
+            if (i < j) Lf[i * kZ + j] = 0.f;
+            __syncwarp();
         }
     }
+    __syncthreads();
+    if (tid < kZ * kZ) a.chol[tid] = Lf[tid];
 }
 
 }  // namespace
 
-size_t cem_score_smem(const ConstLayout &L) { return sizeof(float) * (3 * L.q * 12 + 36 * kCemWarps); }
+size_t cem_score_smem(const ConstLayout &L)
+{
+    const int nobs = cem_obs_floats(L);
+    return sizeof(float) * (3 * L.q * 12 + 36 * kCemWarps + (nobs * 4 <= kCemObsSmem ? nobs : 0));
+}
 
-size_t cem_refit_smem(int NP, int K) { return sizeof(float) * (2 * size_t(NP) + size_t(K) * kZ + 16 + 225); }
+size_t cem_refit_smem(int NP, int K)
+{
+    return sizeof(float) * (2 * size_t(NP) + size_t(K) * kZ + 16 + 228 + 228 + kParts * 225);
+}
+
+// Largest dynamic shared memory either kernel takes (q <= 256, staged
+// obstacles <= kCemObsSmem; N <= 8192, K <= 1024), set once per device.
+constexpr int kScoreSmemMax = (3 * 256 * 12 + 36 * kCemWarps) * 4 + kCemObsSmem;
+constexpr int kRefitSmemMax = (2 * 8192 + 1024 * kZ + 16 + 228 + 228 + kParts * 225) * 4;
+
+int cem_prepare(int dev, int *sms)
+{
+    static int ready_dev = -1, n_sms = 0;
+    if (ready_dev != dev) {
+        if (cudaFuncSetAttribute(cem_score_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kScoreSmemMax) !=
+                cudaSuccess ||
+            cudaFuncSetAttribute(cem_refit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kRefitSmemMax) !=
+                cudaSuccess ||
+            cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return -2;
+        ready_dev = dev;
+    }
+    *sms = n_sms;
+    return 0;
+}
 
 int launch_cem_score(const CemArgs &a, void *stream)
 {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const size_t smem = cem_score_smem(a.L);
-    if (cudaFuncSetAttribute(cem_score_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
-        cudaSuccess)
-        return -2;
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (smem > size_t(kScoreSmemMax) || cem_prepare(dev, &sms)) return -2;
     int blocks = (a.N + kCemWarps - 1) / kCemWarps;
     if (blocks > 8 * sms) blocks = 8 * sms;
     cem_score_kernel<<<blocks, 32 * kCemWarps, smem, st>>>(a);
@@ -227,9 +288,9 @@ int launch_cem_score(const CemArgs &a, void *stream)
 int launch_cem_refit(const CemArgs &a, void *stream)
 {
     const size_t smem = cem_refit_smem(a.NP, a.K);
-    if (cudaFuncSetAttribute(cem_refit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
-        cudaSuccess)
-        return -2;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (smem > size_t(kRefitSmemMax) || cem_prepare(dev, &sms)) return -2;
     cem_refit_kernel<<<1, 1024, smem, static_cast<cudaStream_t>(stream)>>>(a);
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
