@@ -326,7 +326,7 @@ def bench_serving(TJ, W, seconds: float, plain_seconds: float) -> dict:
     return out
 
 
-def bench_closed_loop(episodes: int, cem_episodes: int, batches=(1, 200, 1000)) -> dict:
+def bench_closed_loop(episodes: int, cem_episodes: int, seconds: float = 20.0, batches=(1, 200, 1000)) -> dict:
     """Closed-loop MPC on the crowd benchmarks of Sec. IV (Table III's
     metrics against batch size): `episodes` scenes per benchmark (static,
     same-direction, opposite flow), 20 s at 10 Hz, 10 iterations per re-plan,
@@ -334,16 +334,16 @@ def bench_closed_loop(episodes: int, cem_episodes: int, batches=(1, 200, 1000)) 
     from paper_2109_13030_b300 import mpc as M
     from paper_2109_13030_b300 import workload as W
     crowds = [W.make_crowd(k, s) for k in W.CROWD_KINDS for s in range(episodes)]
-    cfg = M.MPCConfig()
+    cfg = M.MPCConfig(duration=seconds)
     out = {"workload": f"{len(crowds)} synthetic crowd episodes ({episodes} per benchmark: static, same-direction "
                        "flow <= 0.3 m/s, opposite flow <= 1.0 m/s; 30 people of radius 0.3 m in a 10 m band), "
-                       "robot of 3 circles tracking (t m/s, 0), 20 s at 10 Hz",
+                       f"robot of 3 circles tracking (t m/s, 0), {seconds:g} s at 10 Hz",
            "config": {"iters_per_replan": cfg.iters, "horizon_s": cfg.horizon, "q": cfg.q,
                       "planning_margin_m": cfg.margin, "warm_start": "xi and lambda kept between steps",
                       "fallback": "most clearance"},
            "by_batch": {}}
     for batch in batches:
-        r = M.run(crowds, M.MPCConfig(batch=batch))
+        r = M.run(crowds, M.MPCConfig(batch=batch, duration=seconds))
         row = M.summarize(r["episodes"])
         row["by_benchmark_success"] = {k: M.summarize([e for e in r["episodes"] if e["kind"] == k])["success_rate"]
                                        for k in W.CROWD_KINDS}
@@ -362,7 +362,7 @@ def bench_closed_loop(episodes: int, cem_episodes: int, batches=(1, 200, 1000)) 
             row = M.summarize(r["episodes"])
             row["replan_ms"] = r["replan_ms"]
             out["cem"][name] = row
-        r = M.run(sub, M.MPCConfig(batch=1000))
+        r = M.run(sub, M.MPCConfig(batch=1000, duration=seconds))
         row = M.summarize(r["episodes"])
         row["replan_ms"] = r["replan_ms"]
         out["cem"]["am_batch_1000_same_episodes"] = row
@@ -419,6 +419,7 @@ def main():
     ap.add_argument("--jsonl", default=None, help="also append the JSON line to this file")
     ap.add_argument("--mpc-episodes", type=int, default=20, help="closed-loop episodes per crowd benchmark (0: skip)")
     ap.add_argument("--cem-episodes", type=int, default=5, help="of those, episodes per benchmark for the CEM rows")
+    ap.add_argument("--mpc-seconds", type=float, default=20.0, help="closed-loop episode length (s)")
     ap.add_argument("--profile-plain", type=int, default=0, metavar="B",
                     help="profiling aid: solve 2 iterations of the paper-shaped scene at batch B with the "
                          "plain loop and exit (no JSON line)")
@@ -593,7 +594,8 @@ def main():
         if args.serve_seconds > 0:
             line["serving"] = bench_serving(TJ, W, args.serve_seconds, args.serve_plain_seconds)
         if args.mpc_episodes > 0:
-            line["closed_loop"] = bench_closed_loop(args.mpc_episodes, min(args.cem_episodes, args.mpc_episodes))
+            line["closed_loop"] = bench_closed_loop(args.mpc_episodes, min(args.cem_episodes, args.mpc_episodes),
+                                                    args.mpc_seconds)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(pb, B, ITERS)
         print(json.dumps(line), flush=True)
