@@ -557,8 +557,10 @@ __device__ void phase_dot(const KParams &p, float *sm, const Smem &S, const Tile
         const uint2 *bc0 = B + g * L.qp, *bc1 = B + (g < 3 ? 8 + g : g) * L.qp;
         const float *a_lo = sm + S.G2 + row * S.RS + seg * L.qp;
         const float *a_hi = sm + S.G2 + (S.T + row) * S.RS + seg * L.qp;
-        float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f}, d2[4] = {0.f, 0.f, 0.f, 0.f};
-        float e0[4] = {0.f, 0.f, 0.f, 0.f}, e1[4] = {0.f, 0.f, 0.f, 0.f}, e2[4] = {0.f, 0.f, 0.f, 0.f};
+        // the two cross products (lo*hi, hi*lo) share an accumulator: two
+        // chains per n-tile (measured faster than three, fewer registers)
+        float d0[4] = {0.f, 0.f, 0.f, 0.f}, d2[4] = {0.f, 0.f, 0.f, 0.f};
+        float e0[4] = {0.f, 0.f, 0.f, 0.f}, e2[4] = {0.f, 0.f, 0.f, 0.f};
         const int k0 = part * quarter, k1 = min(nks, k0 + quarter);
 #pragma unroll 1
         for (int ks = k0; ks < k1; ++ks) {
@@ -570,16 +572,16 @@ __device__ void phase_dot(const KParams &p, float *sm, const Smem &S, const Tile
             split4(a, ap);
             ld_pair2(bc0 + c0, b0, b1);
             ld_pair2(bc1 + c0, b2, b3);
-            mma_pairs<PR>(d0, d1, d2, ap, b0, b1);
-            mma_pairs<PR>(e0, e1, e2, ap, b2, b3);
+            mma_pairs<PR>(d0, d0, d2, ap, b0, b1);
+            mma_pairs<PR>(e0, e0, e2, ap, b2, b3);
         }
         if (g < tl.count) {
             float *R = sm + S.rb + (seg < 3 ? 4 * seg + part : part) * S.T * 48 + g * 48;
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int side = e >> 1, c = 2 * tq + (e & 1);
-                R[24 * side + (seg < 3 ? c : 12 + c)] = d0[e] + d1[e] + d2[e];
-                if (c < 3) R[24 * side + (seg < 3 ? 8 + c : 20 + c)] = e0[e] + e1[e] + e2[e];
+                R[24 * side + (seg < 3 ? c : 12 + c)] = d0[e] + d2[e];
+                if (c < 3) R[24 * side + (seg < 3 ? 8 + c : 20 + c)] = e0[e] + e2[e];
             }
         }
     }
@@ -627,7 +629,7 @@ __device__ void phase_psi(const KParams &p, float *sm, const Smem &S, const Tile
                                            (col < NS ? col - NV : col - NV - 8) * L.qp;
         float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f}, d2[4] = {0.f, 0.f, 0.f, 0.f};
         const int k0 = part * per, k1 = min(nks, k0 + per);
-#pragma unroll 1
+#pragma unroll 2
         for (int ks = k0; ks < k1; ++ks) {
             const int c0 = ks * 8 + 2 * tq;
             const float2 av = *reinterpret_cast<const float2 *>(arow + c0);
