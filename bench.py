@@ -112,6 +112,11 @@ class ClockSampler:
                 self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
+                self.proc.wait()
+            # the reader thread ends at the pipe's end of file; join it and close
+            # the pipe so that nothing of the sampler outlives the timed region
+            self.thread.join(timeout=5)
+            self.proc.stdout.close()
 
     def summary(self):
         sm, mx, reasons = [], [], set()
@@ -471,6 +476,8 @@ def main():
         collides = bool(mind_d[best["index"]].item() < 0.99)
         return D.merge_best(collides, best["cost"], lo + best["index"], best["coeffs"], dev)
 
+    best_d = torch.empty(36, dtype=torch.float32, device=dev)
+
     def step(i=None):
         TJ.am_init_state(P.h, B, init_d, None, stream)          # cold start from resident samples
         if i is not None:
@@ -478,45 +485,15 @@ def main():
         TJ.am_solve_batch(P.h, B, None, None, ITERS, stream)     # the fused kernel
         if i is not None:
             kends[i].record(stream)
+        if dist is None:
+            TJ.am_get_best_async(P.h, best_d, stream)            # selection on the device, no host wait
+            return None
         return merged_best()
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    launches_per_step = 1 + TJ.am_last_solve_stats(P.h) + 1  # init state, solve, argmin
-
-    # Timed region: CUDA events around each step on the solve's stream, and
-    # around the fused kernel inside it (its average launch duration).
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    kstarts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    kends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        for i in range(args.steps):
-            flush.fill_(float(i))
-            starts[i].record(stream)
-            step(i)
-            ends[i].record(stream)
-        torch.cuda.synchronize()
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    kern_ms = [s.elapsed_time(e) for s, e in zip(kstarts, kends)]
-    tot_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([tot_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
-        dist.barrier()
-    value = world * B * ITERS * args.steps / (tot_ms / 1e3)
-    kern_avg = statistics.mean(kern_ms)
-    q, m, n = pb["q"], pb["m"], pb["n"]
-    flops = algorithmic_flops(q, m, n) * B * ITERS
-    clocks = clk.summary()
-    peak = peak_fp32_tflops(torch.cuda.get_device_properties(dev).multi_processor_count)
-    achieved = flops / (kern_avg / 1e3) / 1e12
-
+    # Host-facing measurements first, before any clock sampling: reading the
+    # GPU's clocks through NVML (nvidia-smi, or the library in-process) slows
+    # this process's later host-side CUDA calls severalfold on these hosts,
+    # which would add to every end-to-end and latency figure below.
     # end to end through the C ABI with host buffers: pinned H2D of the
     # initial samples, the solve, D2H of per-trajectory results and the best
     init_h = torch.tensor(pb["init"], dtype=torch.float32).pin_memory()
@@ -558,6 +535,55 @@ def main():
     Pp.close()
     fused_res = float(np.median(outs[0].numpy()))
 
+    extra = {}
+    if rank == 0:
+        if args.uneven_steps > 0:
+            extra["uneven"] = bench_uneven(TJ, W, torch, dev, flush, args.uneven_steps)
+        if args.precision_steps > 0:
+            extra["precision"] = bench_precision(TJ, W, torch, dev, flush, args.precision_steps)
+        if args.serve_seconds > 0:
+            extra["serving"] = bench_serving(TJ, W, args.serve_seconds, args.serve_plain_seconds)
+        if args.mpc_episodes > 0:
+            extra["closed_loop"] = bench_closed_loop(args.mpc_episodes, min(args.cem_episodes, args.mpc_episodes),
+                                                    args.mpc_seconds)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    launches_per_step = 1 + TJ.am_last_solve_stats(P.h) + 1  # init state, solve, argmin
+
+    # Timed region: CUDA events around each step on the solve's stream, and
+    # around the fused kernel inside it (its average launch duration).
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    kstarts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    kends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            starts[i].record(stream)
+            step(i)
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    kern_ms = [s.elapsed_time(e) for s, e in zip(kstarts, kends)]
+    tot_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([tot_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+        dist.barrier()
+    value = world * B * ITERS * args.steps / (tot_ms / 1e3)
+    kern_avg = statistics.mean(kern_ms)
+    q, m, n = pb["q"], pb["m"], pb["n"]
+    flops = algorithmic_flops(q, m, n) * B * ITERS
+    clocks = clk.summary()
+    peak = peak_fp32_tflops(torch.cuda.get_device_properties(dev).multi_processor_count)
+    achieved = flops / (kern_avg / 1e3) / 1e12
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -587,15 +613,7 @@ def main():
                                                 "final_residual_median": plain_res}},
             "final_residual_median": fused_res,
         }
-        if args.uneven_steps > 0:
-            line["uneven"] = bench_uneven(TJ, W, torch, dev, flush, args.uneven_steps)
-        if args.precision_steps > 0:
-            line["precision"] = bench_precision(TJ, W, torch, dev, flush, args.precision_steps)
-        if args.serve_seconds > 0:
-            line["serving"] = bench_serving(TJ, W, args.serve_seconds, args.serve_plain_seconds)
-        if args.mpc_episodes > 0:
-            line["closed_loop"] = bench_closed_loop(args.mpc_episodes, min(args.cem_episodes, args.mpc_episodes),
-                                                    args.mpc_seconds)
+        line.update(extra)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(pb, B, ITERS)
         print(json.dumps(line), flush=True)

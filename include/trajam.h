@@ -208,6 +208,12 @@ AM_API int am_cem_score(am_problem *h, int count, const float *coeffs, float w_c
  * FP64, no device work. */
 AM_API int am_plan_eval(const float coeffs[33], double T, int count, const double *t, double *out);
 
+/* The same selection queued on `stream` without a wait: out gets 36 floats
+ * {index, cost, residual, c_x, c_y, c_psi} in host (pinned) or device
+ * memory when the stream reaches it.  A non-finite out[1] means every
+ * trajectory was non-finite (am_get_best reports that as AM_ERR_NAN). */
+AM_API int am_get_best_async(am_problem *h, float *out, int mem, void *stream);
+
 /* Copy the B x AM_STATE_FLOATS state out of / into the handle. */
 AM_API int am_get_state(am_problem *h, float *out, int mem);
 AM_API int am_set_state(am_problem *h, int B, const float *in, int mem);

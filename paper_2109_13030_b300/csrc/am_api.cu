@@ -90,7 +90,7 @@ struct am_problem {
     bool solved = false;
     int diag_stall = 0;
     int select = AM_SELECT_COST;
-    float *h_best = nullptr;  // pinned
+    float *h_best = nullptr;  // pinned: best record (36 floats), status word at 40
     // CEM comparator: samples, scores, distribution and best of the last run
     float *d_cem = nullptr, *d_score = nullptr;
     size_t cem_cap = 0, score_cap = 0;
@@ -116,10 +116,13 @@ int wait_event(cudaEvent_t ev, cudaStream_t st)
 
 int wait_stream(am_problem *h)
 {
+    // the status word rides on the same stream into pinned memory, so one
+    // bounded wait covers the work and its status
+    int *h_err = reinterpret_cast<int *>(h->h_best + 40);
+    CK(cudaMemcpyAsync(h_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "status read");
     int rc = wait_event(h->ev, h->stream);
     if (rc) return rc;
-    int err = 0;
-    CK(cudaMemcpy(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost), "status read");
+    const int err = *h_err;
     if (err) return fail(AM_ERR_TIMEOUT, "a kernel gave up a bounded wait (status %d)", err);
     return AM_OK;
 }
@@ -466,6 +469,21 @@ int am_get_best(am_problem *h, float coeffs[33], float *cost, float *residual, i
     if (coeffs) std::memcpy(coeffs, h->h_best + 3, 33 * sizeof(float));
     // non-finite trajectories rank last, so a non-finite best means all are
     if (!std::isfinite(h->h_best[1])) return fail(AM_ERR_NAN, "every trajectory of the batch is non-finite");
+    return AM_OK;
+}
+
+int am_get_best_async(am_problem *h, float *out, int mem, void *stream)
+{
+    if (!h || !out) return fail(AM_ERR_ARG, "null argument");
+    if (mem != AM_HOST && mem != AM_DEVICE) return fail(AM_ERR_ARG, "bad mem flag");
+    if (!h->solved) return fail(AM_ERR_STATE, "no solve yet");
+    h->stream = static_cast<cudaStream_t>(stream);
+    float *dst = mem == AM_DEVICE ? out : h->d_best;
+    if (launch_argmin(h->select, h->d_state, h->d_out + 2 * size_t(h->B), h->d_out, h->d_out + 3 * size_t(h->B),
+                      h->B, dst, h->stream, nullptr))
+        return fail(AM_ERR_CUDA, "argmin launch failed");
+    if (mem == AM_HOST)
+        CK(cudaMemcpyAsync(out, h->d_best, 36 * sizeof(float), cudaMemcpyDeviceToHost, h->stream), "best copy");
     return AM_OK;
 }
 

@@ -42,6 +42,9 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "am_internal.h"
 
@@ -1176,11 +1179,67 @@ int fused_auto_tile(const ConstLayout &L, int B, int num_sms)
     return want < tmax ? want : tmax;
 }
 
+namespace {
+
+// Launch configuration of the single-problem kernels, formed once and kept:
+// the SM count per device, and per kernel variant the shared-memory limit
+// (set to the 227 KB maximum) and the resident CTAs per SM for each (block,
+// shared memory) size.  A solve then costs one launch and no driver queries.
+std::mutex g_launch_mu;
+
+int device_sms(int dev)
+{
+    static int cached_dev = -1, count = 0;
+    std::lock_guard<std::mutex> lk(g_launch_mu);
+    if (cached_dev != dev) {
+        if (cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+        cached_dev = dev;
+    }
+    return count;
+}
+
+template <int M, bool LIT, int PR>
+int launch_variant(const KParams &p, int threads, size_t smem, int dev, int sms, cudaStream_t st)
+{
+    static int attr_dev = -1;
+    static std::map<std::pair<int, size_t>, int> resident;
+    int per_sm = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_launch_mu);
+        if (attr_dev != dev) {
+            if (cudaFuncSetAttribute(am_fused_kernel<M, LIT, PR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     227 * 1024) != cudaSuccess)
+                return -2;
+            resident.clear();
+            attr_dev = dev;
+        }
+        const auto key = std::make_pair(threads, smem);
+        const auto it = resident.find(key);
+        if (it != resident.end()) {
+            per_sm = it->second;
+        } else {
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, am_fused_kernel<M, LIT, PR>, threads, smem) !=
+                    cudaSuccess ||
+                per_sm < 1)
+                return -2;
+            resident[key] = per_sm;
+        }
+    }
+    // persistent CTAs: as many as can be resident at once (one per SM for the
+    // large tiles; more when a smaller tile lets several share an SM)
+    const int grid = p.ntiles < sms * per_sm ? p.ntiles : sms * per_sm;
+    am_fused_kernel<M, LIT, PR><<<grid, threads, smem, st>>>(p);
+    return 0;
+}
+
+}  // namespace
+
 int launch_fused(const SolveArgs &a, void *stream, int *launches)
 {
-    int dev = 0, sms = 148;
+    int dev = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int sms = device_sms(dev);
+    if (sms < 1) return -2;
     const ConstLayout &L = a.L;
     int T = a.tile > 0 ? a.tile : fused_auto_tile(L, a.B, sms);
     const int tq = T * (L.q > 88 ? L.q : 88);
@@ -1204,22 +1263,12 @@ int launch_fused(const SolveArgs &a, void *stream, int *launches)
     p.hist = a.hist;
     p.err = a.err;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    cudaError_t e;
-    // Persistent CTAs: as many as can be resident at once (one per SM for the
-    // large tiles; more when a smaller tile lets several share an SM).
-    int per_sm = 1, grid = 1;
+    int rc = -1;
     const int sel = (L.precision * 8 + (L.m - 1) * 2) + (L.alpha_mode ? 1 : 0);
     switch (sel) {
 #define AM_CASE(MM, LL, PP)                                                                   \
     case PP * 8 + (MM - 1) * 2 + LL:                                                          \
-        e = cudaFuncSetAttribute(am_fused_kernel<MM, LL, PP>,                                 \
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));     \
-        if (e != cudaSuccess) return -2;                                                      \
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, am_fused_kernel<MM, LL, PP>, \
-                                                          threads, smem);                     \
-        if (e != cudaSuccess || per_sm < 1) return -2;                                        \
-        grid = ntiles < sms * per_sm ? ntiles : sms * per_sm;                                 \
-        am_fused_kernel<MM, LL, PP><<<grid, threads, smem, st>>>(p);                          \
+        rc = launch_variant<MM, LL, PP>(p, threads, smem, dev, sms, st);                      \
         break;
 #define AM_CASES(PP)                                                                          \
         AM_CASE(1, 0, PP)                                                                     \
@@ -1238,6 +1287,7 @@ int launch_fused(const SolveArgs &a, void *stream, int *launches)
     default:
         return -1;
     }
+    if (rc) return rc;
     if (launches) ++*launches;
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }

@@ -28,7 +28,7 @@ AM_REQ_GOAL, AM_REQ_RESAMPLE, AM_REQ_SHIFT = 1, 2, 4
 AM_NV, AM_STATE_FLOATS = 11, 110
 
 EXPORTS = ["am_init_problem", "am_set_obstacles", "am_set_boundary", "am_solve_batch",
-           "am_get_results", "am_get_best", "am_get_state", "am_set_state", "am_set_history",
+           "am_get_results", "am_get_best", "am_get_best_async", "am_get_state", "am_set_state", "am_set_history",
            "am_get_history", "am_set_option", "am_set_stream", "am_last_solve_stats",
            "am_solve_batch_noalloc", "am_init_state", "am_resample", "am_shift", "am_plan_eval", "am_cem_solve",
            "am_cem_get_best", "am_cem_get_samples", "am_cem_score", "am_group_create", "am_group_solve",
@@ -91,6 +91,7 @@ def _load():
         "am_get_results": ([vp, fp, fp, fp, fp, ip], ip),
         "am_get_best": ([vp, fp, C.POINTER(C.c_float), C.POINTER(C.c_float), C.POINTER(C.c_int)], ip),
         "am_get_state": ([vp, fp, ip], ip),
+        "am_get_best_async": ([vp, fp, ip, vp], ip),
         "am_set_state": ([vp, ip, fp, ip], ip),
         "am_set_history": ([vp, ip], ip),
         "am_get_history": ([vp, fp, ip], ip),
@@ -225,6 +226,13 @@ def am_get_best(h):
     cost, res, idx = C.c_float(), C.c_float(), C.c_int()
     _check(_lib.am_get_best(h, coeffs.ctypes.data, C.byref(cost), C.byref(res), C.byref(idx)))
     return dict(coeffs=coeffs.reshape(3, 11), cost=cost.value, res=res.value, index=idx.value)
+
+
+def am_get_best_async(h, out, stream=None):
+    """Queue the best selection into out (36 floats: index, cost, residual,
+    coefficients), host (pinned) or device memory, without waiting."""
+    p, mem, k = _buf(out)
+    _check(_lib.am_get_best_async(h, p, mem, _stream_ptr(stream)))
 
 
 def am_get_state(h, out):
