@@ -313,6 +313,26 @@ def test_best_selection_matches_oracle_key():
     np.testing.assert_allclose(best["coeffs"][2], g["xi2"][i_g], rtol=0, atol=0)
 
 
+def test_best_async_equals_best():
+    """am_get_best_async (device and pinned host output) gives am_get_best's record."""
+    import torch
+    T = tj()
+    pb = W.make_problem("paper", 0, B=300)
+    P = T.Problem(pb)
+    P.solve(pb["init"].astype(np.float32), 20)
+    ref = P.best()
+    want = np.concatenate([[ref["index"], ref["cost"], ref["res"]], ref["coeffs"].ravel()]).astype(np.float32)
+    out_d = torch.zeros(36, dtype=torch.float32, device="cuda")
+    out_h = torch.zeros(36, dtype=torch.float32).pin_memory()
+    stream = torch.cuda.current_stream()
+    T.am_get_best_async(P.h, out_d, stream)
+    T.am_get_best_async(P.h, out_h, stream)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out_d.cpu().numpy(), want)
+    np.testing.assert_array_equal(out_h.numpy(), want)
+    P.close()
+
+
 def test_fused_and_plain_agree():
     pb = W.make_problem("paper", 2, B=64)
     a = gpu_solve(pb, 20, kernel=0)
