@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <cfloat>
+#include <mutex>
 
 #include "am_internal.h"
 #include "am_rng.cuh"
@@ -258,7 +259,9 @@ constexpr int kRefitSmemMax = (2 * 8192 + 1024 * kZ + 16 + 228 + 228 + kParts * 
 
 int cem_prepare(int dev, int *sms)
 {
+    static std::mutex mu;
     static int ready_dev = -1, n_sms = 0;
+    std::lock_guard<std::mutex> lk(mu);
     if (ready_dev != dev) {
         if (cudaFuncSetAttribute(cem_score_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kScoreSmemMax) !=
                 cudaSuccess ||

@@ -98,7 +98,8 @@ int serve_round(am_server *s, std::vector<Request> &batch)
         if (!rc && !q.xo.empty()) rc = problem_update_tracks(sc.h, q.xo.data(), q.yo.data());
         if (!rc) rc = update_boundary(sc, q.r);
         if (!rc && (q.r.flags & AM_REQ_RESAMPLE)) rc = am_resample(sc.h, q.r.seed, q.r.sigma, s->st);
-        else if (!rc && (q.r.flags & AM_REQ_SHIFT) && q.r.advance > 0) rc = am_shift(sc.h, q.r.advance, s->st);
+        else if (!rc && (q.r.flags & AM_REQ_SHIFT) && q.r.advance > 0 && sc.has_best)
+            rc = am_shift(sc.h, q.r.advance, s->st);  // re-timed together with the start state
         if (rc) return rc;
     }
     // A round of several requests goes through one grouped launch; a round of
