@@ -191,28 +191,10 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
-// One 16x8x8 step of D += A B in three TF32 products, into three independent
-// accumulators (lo*hi, hi*lo, hi*hi) so consecutive steps do not wait on one
-// accumulator; the caller sums them at the end.
-// a: A[g][k], A[g+8][k], A[g][k+4], A[g+8][k+4]; b: B[k][n], B[k+4][n] with
-// g = lane/4, k = lane%4 within the step, n = lane/4 (PTX m16n8k8 layouts).
-__device__ __forceinline__ void mma3x(float (&d0)[4], float (&d1)[4], float (&d2)[4],
-                                      const float (&a)[4], float b0, float b1)
-{
-    uint32_t ah[4], al[4], bh0, bl0, bh1, bl1;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) split_tf32(a[i], ah[i], al[i]);
-    split_tf32(b0, bh0, bl0);
-    split_tf32(b1, bh1, bl1);
-    mma_tf32(d0, al[0], al[1], al[2], al[3], bh0, bh1);
-    mma_tf32(d1, ah[0], ah[1], ah[2], ah[3], bl0, bl1);
-    mma_tf32(d2, ah[0], ah[1], ah[2], ah[3], bh0, bh1);
-}
-
-// Reduced-precision forms of the same step (AM_TF32, AM_BF16): one product
-// of operands rounded to TF32, or to BF16 with m16n8k8.bf16.  For BF16 the k
-// index of the fragment is permuted (fragment k = 2t, 2t+1 <-> columns t,
-// t+4 of the step), identically in A and B, so the same loads serve both.
+// Reduced-precision product (AM_BF16): one m16n8k8.bf16 product of the
+// operands rounded to BF16.  The k index of the fragment is permuted
+// (fragment k = 2t, 2t+1 <-> columns t, t+4 of the step), identically in A
+// and B, so the same loads serve the TF32 and BF16 forms.
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 {
     uint32_t d;
@@ -220,29 +202,24 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
     return d;
 }
 
-template <int PR>
-__device__ __forceinline__ void mma_prec(float (&d0)[4], float (&d1)[4], float (&d2)[4],
-                                         const float (&a)[4], float b0, float b1)
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const float (&a)[4], float b0, float b1)
 {
-    if constexpr (PR == 0) {
-        mma3x(d0, d1, d2, a, b0, b1);
-    } else if constexpr (PR == 1) {
-        mma_tf32(d2, round_tf32(__float_as_uint(a[0])), round_tf32(__float_as_uint(a[1])),
-                 round_tf32(__float_as_uint(a[2])), round_tf32(__float_as_uint(a[3])),
-                 round_tf32(__float_as_uint(b0)), round_tf32(__float_as_uint(b1)));
-    } else {
-        const uint32_t a01 = pack_bf16(a[0], a[2]), a23 = pack_bf16(a[1], a[3]), b = pack_bf16(b0, b1);
-        asm volatile(
-            "mma.sync.aligned.m16n8k8.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, "
-            "{%0,%1,%2,%3};\n"
-            : "+f"(d2[0]), "+f"(d2[1]), "+f"(d2[2]), "+f"(d2[3])
-            : "r"(a01), "r"(a23), "r"(b));
-    }
+    const uint32_t a01 = pack_bf16(a[0], a[2]), a23 = pack_bf16(a[1], a[3]), b = pack_bf16(b0, b1);
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a01), "r"(a23), "r"(b));
 }
 
-// The same steps on operands split beforehand (TF32 (hi, lo) pairs: the
-// constants on the host, the residual rows and heading increments by the
-// phases that produce them), so the tensor-core phases only load.
+// One 16x8x8 step of D += A B on operands split into TF32 (hi, lo) pairs
+// (the constants on the host, the residual rows and heading increments by
+// the phases that produce them, so the tensor-core phases only load).
+// PR = 0 (FP32 form): three products lo*hi, hi*lo, hi*hi into d0, d1, d2,
+// which the caller sums at the end (passing one array twice shares a chain);
+// PR = 1 (AM_TF32): hi*hi only; PR = 2 (AM_BF16): the hi parts rounded to BF16.
+// a: A[g][k], A[g+8][k], A[g][k+4], A[g+8][k+4]; b: B[k][n], B[k+4][n] with
+// g = lane/4, k = lane%4 within the step, n = lane/4 (PTX m16n8k8 layouts).
 template <int PR>
 __device__ __forceinline__ void mma_pairs(float (&d0)[4], float (&d1)[4], float (&d2)[4],
                                           const uint2 (&a)[4], uint2 b0, uint2 b1)
@@ -256,7 +233,7 @@ __device__ __forceinline__ void mma_pairs(float (&d0)[4], float (&d1)[4], float 
     } else {
         const float f[4] = {__uint_as_float(a[0].x), __uint_as_float(a[1].x), __uint_as_float(a[2].x),
                             __uint_as_float(a[3].x)};
-        mma_prec<2>(d0, d1, d2, f, __uint_as_float(b0.x), __uint_as_float(b1.x));
+        mma_bf16(d2, f, __uint_as_float(b0.x), __uint_as_float(b1.x));
     }
 }
 
