@@ -344,7 +344,8 @@ def bench_closed_loop(episodes: int, cem_episodes: int, seconds: float = 20.0, b
                        "flow <= 0.3 m/s, opposite flow <= 1.0 m/s; 30 people of radius 0.3 m in a 10 m band), "
                        f"robot of 3 circles tracking (t m/s, 0), {seconds:g} s at 10 Hz",
            "config": {"iters_per_replan": cfg.iters, "horizon_s": cfg.horizon, "q": cfg.q,
-                      "planning_margin_m": cfg.margin, "warm_start": "xi and lambda kept between steps",
+                      "planning_margin_m": cfg.margin,
+                      "warm_start": "coefficients kept and re-timed, multipliers kept",
                       "fallback": "most clearance"},
            "by_batch": {}}
     for batch in batches:
@@ -371,6 +372,11 @@ def bench_closed_loop(episodes: int, cem_episodes: int, seconds: float = 20.0, b
         row = M.summarize(r["episodes"])
         row["replan_ms"] = r["replan_ms"]
         out["cem"]["am_batch_1000_same_episodes"] = row
+    # the multiplier decay between steps (0.9 per step instead of the warm start's 1)
+    r = M.run(crowds, M.MPCConfig(batch=1000, duration=seconds, lambda_decay=0.9))
+    row = M.summarize(r["episodes"])
+    row["replan_ms"] = r["replan_ms"]
+    out["am_batch_1000_lambda_decay_0.9"] = row
     return out
 
 

@@ -202,6 +202,13 @@ AM_API int am_cem_get_samples(am_problem *h, float *z, float *cost, float *mu, f
 AM_API int am_cem_score(am_problem *h, int count, const float *coeffs, float w_coll, float w_bound,
                         float *cost, float *min_dist);
 
+/* Scale the multipliers lambda, lambda_psi of the B trajectories the handle
+ * holds by `factor` (finite, >= 0; 0 resets them), keeping their
+ * coefficients: a re-plan that continues the kept plans with the previous
+ * window's multipliers decayed.  Queued on the handle's stream; requires a
+ * state. */
+AM_API int am_scale_multipliers(am_problem *h, float factor, void *stream);
+
 /* Evaluate a plan (c_x, c_y, c_psi: 33 floats, host) of horizon T at `count`
  * times t[i] (clamped to [0, T]): out[9 i ..] = x, x', x'', y, y', y'', psi,
  * psi', psi'' (derivatives in 1/s, 1/s^2; Eq. param).  Host arithmetic in
@@ -361,6 +368,7 @@ typedef struct {
 #define AM_REQ_GOAL 1       /* am_request.flags: replace the goal state        */
 #define AM_REQ_RESAMPLE 2   /* am_request.flags: re-draw the batch (am_resample) */
 #define AM_REQ_SHIFT 4      /* am_request.flags: re-time the batch by the advance (am_shift) */
+#define AM_REQ_SCALE_LAMBDA 8  /* am_request.flags: scale the multipliers (am_scale_multipliers) */
 
 typedef struct {
     int scene;              /* as returned by am_server_add_scene              */
@@ -369,13 +377,15 @@ typedef struct {
                                acceleration of x, y and psi)                   */
     const float *xo, *yo;   /* nullable: new obstacle centre tracks, n x q
                                each, host memory, copied by am_server_submit   */
-    int flags;              /* AM_REQ_GOAL | AM_REQ_RESAMPLE | AM_REQ_SHIFT,
-                               applied after the advance and the tracks,
-                               before the solve (a re-draw supersedes a shift) */
+    int flags;              /* AM_REQ_GOAL | AM_REQ_RESAMPLE | AM_REQ_SHIFT |
+                               AM_REQ_SCALE_LAMBDA, applied after the advance
+                               and the tracks, before the solve (a re-draw
+                               supersedes a shift; the scaling comes last)    */
     double goal[9];         /* AM_REQ_GOAL: x, x', x'', y, y', y'', psi, psi',
                                psi'' at t = T                                   */
     unsigned long long seed;  /* AM_REQ_RESAMPLE: generator seed               */
     float sigma;            /* AM_REQ_RESAMPLE: perturbation scale (m)         */
+    float lambda_scale;     /* AM_REQ_SCALE_LAMBDA: factor (finite, >= 0)      */
 } am_request;
 
 typedef struct {

@@ -1059,6 +1059,24 @@ int am_cem_score(am_problem *h, int count, const float *coeffs, float w_coll, fl
     return wait_stream(h);
 }
 
+int am_scale_multipliers(am_problem *h, float factor, void *stream)
+{
+    if (!h) return fail(AM_ERR_ARG, "null handle");
+    if (!(factor >= 0.f) || !std::isfinite(factor)) return fail(AM_ERR_ARG, "factor must be finite and >= 0");
+    if (!h->solved || h->B < 1) return fail(AM_ERR_STATE, "no state yet");
+    h->stream = static_cast<cudaStream_t>(stream);
+    if (factor == 1.f) return AM_OK;
+    if (factor == 0.f) {
+        // entries 55..109 of every trajectory's state: one strided memset
+        CK(cudaMemset2DAsync(h->d_state + 55, STATE * sizeof(float), 0, 55 * sizeof(float), h->B, h->stream),
+           "multiplier reset");
+        return AM_OK;
+    }
+    if (launch_scale_multipliers(h->d_state, h->B, factor, h->stream, nullptr))
+        return fail(AM_ERR_CUDA, "multiplier scaling launch failed");
+    return AM_OK;
+}
+
 int am_plan_eval(const float coeffs[33], double T, int count, const double *t, double *out)
 {
     if (!coeffs || count < 0 || (count > 0 && (!t || !out))) return fail(AM_ERR_ARG, "null argument");

@@ -86,6 +86,15 @@ __global__ void shift_kernel(float *state, ShiftArgs a)
     }
 }
 
+// Multiplier decay between re-plans: state entries 55..109 of every trajectory.
+__global__ void scale_multipliers_kernel(float *state, int B, float factor)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B * 55) return;
+    float &v = state[(size_t)(i / 55) * STATE + 55 + i % 55];
+    v *= factor;
+}
+
 // Obstacle sections of the constant block: centre tracks in ellipse-scaled
 // coordinates (x_j(t)/a_j, y_j(t)/b_j) and per-obstacle (1/a_j, 1/b_j, a_j, b_j),
 // with the semi-axes inflated by the robot circle radius.
@@ -205,6 +214,15 @@ int launch_shift(float *state, const ShiftArgs &a, void *stream, int *launches)
     if (a.B < 1) return 0;
     const int n = 5 * a.B;
     shift_kernel<<<(n + 127) / 128, 128, 0, static_cast<cudaStream_t>(stream)>>>(state, a);
+    if (launches) ++*launches;
+    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
+int launch_scale_multipliers(float *state, int B, float factor, void *stream, int *launches)
+{
+    if (B < 1) return 0;
+    const int n = 55 * B;
+    scale_multipliers_kernel<<<(n + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(state, B, factor);
     if (launches) ++*launches;
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }

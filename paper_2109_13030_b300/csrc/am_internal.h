@@ -206,6 +206,9 @@ struct ResampleArgs {
 };
 int launch_resample(float *state, const ResampleArgs &a, void *stream, int *launches);
 
+// Multipliers (state entries 55..109) of B trajectories times factor.
+int launch_scale_multipliers(float *state, int B, float factor, void *stream, int *launches);
+
 // Re-timing of a batch (am_shift): S maps old control points to new, row-major.
 struct ShiftArgs {
     float S[121];

@@ -100,6 +100,7 @@ int serve_round(am_server *s, std::vector<Request> &batch)
         if (!rc && (q.r.flags & AM_REQ_RESAMPLE)) rc = am_resample(sc.h, q.r.seed, q.r.sigma, s->st);
         else if (!rc && (q.r.flags & AM_REQ_SHIFT) && q.r.advance > 0 && sc.has_best)
             rc = am_shift(sc.h, q.r.advance, s->st);  // re-timed together with the start state
+        if (!rc && (q.r.flags & AM_REQ_SCALE_LAMBDA)) rc = am_scale_multipliers(sc.h, q.r.lambda_scale, s->st);
         if (rc) return rc;
     }
     // A round of several requests goes through one grouped launch; a round of
@@ -281,7 +282,7 @@ int am_server_submit(am_server *s, const am_request *req, long long *ticket)
     if (req->scene < 0 || req->scene >= int(s->scenes.size())) return report_error(AM_ERR_ARG, "unknown scene");
     if (!(req->advance >= 0) || !std::isfinite(req->advance)) return report_error(AM_ERR_ARG, "bad advance");
     if ((req->xo == nullptr) != (req->yo == nullptr)) return report_error(AM_ERR_ARG, "xo and yo go together");
-    if (req->flags & ~(AM_REQ_GOAL | AM_REQ_RESAMPLE | AM_REQ_SHIFT))
+    if (req->flags & ~(AM_REQ_GOAL | AM_REQ_RESAMPLE | AM_REQ_SHIFT | AM_REQ_SCALE_LAMBDA))
         return report_error(AM_ERR_ARG, "unknown request flags");
     if ((req->flags & AM_REQ_SHIFT) && !(req->advance <= s->scenes[req->scene].T))
         return report_error(AM_ERR_ARG, "a shifted advance must be <= T");
@@ -290,6 +291,8 @@ int am_server_submit(am_server *s, const am_request *req, long long *ticket)
             if (!std::isfinite(req->goal[k])) return report_error(AM_ERR_ARG, "non-finite goal");
     if ((req->flags & AM_REQ_RESAMPLE) && !(req->sigma >= 0.f && std::isfinite(req->sigma)))
         return report_error(AM_ERR_ARG, "sigma must be finite and >= 0");
+    if ((req->flags & AM_REQ_SCALE_LAMBDA) && !(req->lambda_scale >= 0.f && std::isfinite(req->lambda_scale)))
+        return report_error(AM_ERR_ARG, "lambda_scale must be finite and >= 0");
     const Scene &sc = s->scenes[req->scene];
     Request q;
     q.r = *req;

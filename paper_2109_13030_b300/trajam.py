@@ -24,13 +24,13 @@ AM_SELECT_COST, AM_SELECT_CLEARANCE = 0, 1
 AM_GOPT_THREADS, AM_GOPT_GRAPH = 1, 2
 AM_PENDING = 1
 AM_SRV_BATCHED, AM_SRV_SEQUENTIAL = 0, 1
-AM_REQ_GOAL, AM_REQ_RESAMPLE, AM_REQ_SHIFT = 1, 2, 4
+AM_REQ_GOAL, AM_REQ_RESAMPLE, AM_REQ_SHIFT, AM_REQ_SCALE_LAMBDA = 1, 2, 4, 8
 AM_NV, AM_STATE_FLOATS = 11, 110
 
 EXPORTS = ["am_init_problem", "am_set_obstacles", "am_set_boundary", "am_solve_batch",
            "am_get_results", "am_get_best", "am_get_best_async", "am_get_state", "am_set_state", "am_set_history",
            "am_get_history", "am_set_option", "am_set_stream", "am_last_solve_stats",
-           "am_solve_batch_noalloc", "am_init_state", "am_resample", "am_shift", "am_plan_eval", "am_cem_solve",
+           "am_solve_batch_noalloc", "am_init_state", "am_resample", "am_shift", "am_scale_multipliers", "am_plan_eval", "am_cem_solve",
            "am_cem_get_best", "am_cem_get_samples", "am_cem_score", "am_group_create", "am_group_solve",
            "am_group_autotune", "am_group_set_option", "am_group_set_active", "am_group_get_best",
            "am_group_stats", "am_group_destroy", "am_server_create", "am_server_add_scene",
@@ -55,7 +55,8 @@ class AmServerDesc(C.Structure):
 class AmRequest(C.Structure):
     _fields_ = [("scene", C.c_int), ("advance", C.c_double),
                 ("xo", C.c_void_p), ("yo", C.c_void_p), ("flags", C.c_int),
-                ("goal", C.c_double * 9), ("seed", C.c_ulonglong), ("sigma", C.c_float)]
+                ("goal", C.c_double * 9), ("seed", C.c_ulonglong), ("sigma", C.c_float),
+                ("lambda_scale", C.c_float)]
 
 
 class AmResult(C.Structure):
@@ -102,6 +103,7 @@ def _load():
         "am_init_state": ([vp, ip, fp, fp, vp, ip], ip),
         "am_resample": ([vp, C.c_ulonglong, C.c_float, vp], ip),
         "am_shift": ([vp, C.c_double, vp], ip),
+        "am_scale_multipliers": ([vp, C.c_float, vp], ip),
         "am_cem_solve": ([vp, C.POINTER(AmCemDesc), vp], ip),
         "am_cem_get_best": ([vp, fp, C.POINTER(C.c_float), C.POINTER(C.c_float)], ip),
         "am_cem_get_samples": ([vp, fp, fp, fp, fp], ip),
@@ -336,6 +338,10 @@ def am_cem_score(h, coeffs, w_coll=1e4, w_bound=1e2):
     return cost, md
 
 
+def am_scale_multipliers(h, factor, stream=None):
+    _check(_lib.am_scale_multipliers(h, float(factor), _stream_ptr(stream)))
+
+
 def am_plan_eval(coeffs, T, t):
     """x, x', x'', y, y', y'', psi, psi', psi'' of a plan at the times t: (len(t), 9)."""
     c = np.ascontiguousarray(coeffs, dtype=np.float32).reshape(33)
@@ -406,11 +412,14 @@ def am_server_start(s):
 
 
 def am_server_submit(s, scene, advance=0.0, xo=None, yo=None, goal=None, resample_seed=None,
-                     sigma=1.0, shift=False) -> int:
+                     sigma=1.0, shift=False, lambda_scale=None) -> int:
     keep = []
     r = AmRequest(int(scene), float(advance), None, None)
     if shift:
         r.flags |= AM_REQ_SHIFT
+    if lambda_scale is not None:
+        r.flags |= AM_REQ_SCALE_LAMBDA
+        r.lambda_scale = float(lambda_scale)
     if goal is not None:
         r.flags |= AM_REQ_GOAL
         for k, v in enumerate(np.asarray(goal, dtype=np.float64).reshape(9)):
@@ -488,6 +497,10 @@ class Problem:
     def init_state(self, init, warm_lambda=None, stream=None):
         am_init_state(self.h, int(init.shape[0]), init, warm_lambda, stream)
         self.B = int(init.shape[0])
+        return self
+
+    def scale_multipliers(self, factor, stream=None):
+        am_scale_multipliers(self.h, factor, stream)
         return self
 
     def shift(self, dt, stream=None):
@@ -604,12 +617,12 @@ class Server:
         return self
 
     def submit(self, scene, advance=0.0, xo=None, yo=None, goal=None, resample_seed=None, sigma=1.0,
-               shift=False):
+               shift=False, lambda_scale=None):
         """goal: 9 values (x, x', x'', y, y', y'', psi, psi', psi'' at t = T);
         resample_seed: re-draw the scene's batch around the new straight line
         with that seed (multipliers kept); shift: re-time the batch by the
-        advance (am_shift)."""
-        return am_server_submit(self.s, scene, advance, xo, yo, goal, resample_seed, sigma, shift)
+        advance (am_shift); lambda_scale: scale the multipliers (am_scale_multipliers)."""
+        return am_server_submit(self.s, scene, advance, xo, yo, goal, resample_seed, sigma, shift, lambda_scale)
 
     def poll(self, ticket, timeout_ms=0):
         return am_server_poll(self.s, ticket, timeout_ms)

@@ -189,3 +189,29 @@ def test_cem_argument_checks(paper):
     with pytest.raises(T.TrajamError):
         T.am_cem_solve(P.h, warm=np.zeros(33), warm_dt=-1.0)
     P.close()
+
+
+def test_cem_reaches_the_free_space_optimum():
+    """No obstacles, inactive bounds: J is the smoothness cost alone, whose
+    minimum over control points 3..7 (the rest fixed by the boundary
+    conditions) is a least-squares problem, solved here in numpy.  CEM's best
+    plan must come within 1 % of it and never below it."""
+    T = tj()
+    pb = W.with_obstacles_removed(W.make_problem("paper", 0, B=8))
+    P = T.Problem(pb)
+    T.am_cem_solve(P.h, seed=11, iters=30)
+    best = T.am_cem_get_best(P.h)
+    _, _, Pdd = basis(pb["q"], pb["T"])
+    H = Pdd.T @ Pdd
+    J_star = 0.0
+    for bc in (pb["x_bc"], pb["y_bc"], pb["psi_bc"]):
+        lo, hi = end_points(bc, pb["T"])
+        c_fixed = np.zeros(11)
+        c_fixed[:3], c_fixed[8:] = lo, hi
+        E = np.zeros((11, 5))
+        E[3:8, :] = np.eye(5)
+        z = -np.linalg.solve(E.T @ H @ E, E.T @ H @ c_fixed)
+        c = c_fixed + E @ z
+        J_star += c @ H @ c
+    assert J_star * (1 - 1e-4) <= best["cost"] <= J_star * 1.01, (best["cost"], J_star)
+    P.close()

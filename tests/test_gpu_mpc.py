@@ -240,3 +240,32 @@ def test_closed_loop_with_cem_runs():
     assert len(out["episodes"]) == 3 and out["steps"] == 20
     for e in out["episodes"]:
         assert np.isfinite(e["tracking_error"]) and e["min_clearance"] > 0
+
+
+def test_scale_multipliers_touches_lambda_only():
+    T = tj()
+    pb = W.make_problem("paper", 0, B=200)
+    P = T.Problem(pb)
+    P.solve(pb["init"].astype(np.float32), 5)
+    before = P.state()
+    assert np.abs(before[:, 55:]).max() > 0
+    P.scale_multipliers(0.5)
+    half = P.state()
+    np.testing.assert_array_equal(half[:, :55], before[:, :55])
+    np.testing.assert_array_equal(half[:, 55:], before[:, 55:] * np.float32(0.5))
+    P.scale_multipliers(1.0)
+    np.testing.assert_array_equal(P.state(), half)
+    P.scale_multipliers(0.0)
+    zero = P.state()
+    np.testing.assert_array_equal(zero[:, :55], before[:, :55])
+    assert not zero[:, 55:].any()
+    for bad in (-0.5, float("nan")):
+        with pytest.raises(T.TrajamError) as e:
+            P.scale_multipliers(bad)
+        assert e.value.code == T.AM_ERR_ARG
+    P.close()
+    Q = T.Problem(pb)
+    with pytest.raises(T.TrajamError) as e:
+        Q.scale_multipliers(0.0)
+    assert e.value.code == T.AM_ERR_STATE
+    Q.close()
