@@ -542,7 +542,9 @@ def main():
     fused_res = float(np.median(outs[0].numpy()))
 
     extra = {}
-    if rank == 0:
+    # single-GPU sections; under torchrun they would hold every rank's GPU
+    # while rank 0 alone works, so they run at N = 1 only
+    if rank == 0 and world == 1:
         if args.uneven_steps > 0:
             extra["uneven"] = bench_uneven(TJ, W, torch, dev, flush, args.uneven_steps)
         if args.precision_steps > 0:
@@ -620,7 +622,7 @@ def main():
             "final_residual_median": fused_res,
         }
         line.update(extra)
-        if not args.no_cpu_baseline:
+        if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(pb, B, ITERS)
         print(json.dumps(line), flush=True)
         if args.jsonl:
