@@ -572,11 +572,9 @@ __device__ void phase_dot(const KParams &p, float *sm, const Smem &S, const Tile
 // heading step is then applied once per coefficient:
 //   xi2' = xi2 + (Mpsi lam_psi - Mpsi H xi2) + rho W^T delta
 // (the first bracket formed in the EVAL phase), writing xi2' and the increment.
-// With twelve or more warps: twelve tasks (three n-tiles x four quarters of
-// the steps) write partials, meet at a named barrier of those twelve warps,
-// and the first of them sum the partials and apply the step.  Smaller blocks:
-// three tasks (one per n-tile) over all steps, each applying the step to its
-// own outputs.
+// Partials over four quarters of the steps (three n-tiles each) are written,
+// the task warps meet at a named barrier, and the first of them sum the
+// partials and apply the step.
 __device__ __forceinline__ void psi_apply(const KParams &p, float *sm, const Smem &S, int g, int c,
                                           float v, int cur2)
 {
@@ -595,54 +593,60 @@ __device__ void phase_psi(const KParams &p, float *sm, const Smem &S, const Tile
     const ConstLayout &L = p.L;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane >> 2, tq = lane & 3;
-    const int nks = (L.q + 7) >> 3;
+    const int nks = (L.q + 7) >> 3, per = (nks + kPsiParts - 1) / kPsiParts;
+    // Twelve task warps take one (n-tile, quarter) each; a smaller block has
+    // three, each running its n-tile's four quarters in turn.  Either way every
+    // quarter's partial is formed alone and the four are added in the same
+    // order, so the result does not depend on the block size.
     const bool split = (blockDim.x >> 5) >= 3 * kPsiParts;
-    const int ntask = split ? 3 * kPsiParts : 3, per = split ? (nks + kPsiParts - 1) / kPsiParts : nks;
+    const int ntask = split ? 3 * kPsiParts : 3;
     const float *arow = sm + S.PS + frag_row4(g, tl.count) * L.qp;
     const uint2 z = make_uint2(0u, 0u);
     if (warp < ntask) {
-        const int nt = warp % 3, part = warp / 3;
+        const int nt = warp % 3;
         const int col = nt * 8 + g;
         // columns 22, 23 give discarded outputs: read columns of the same parity
         const uint2 *bcol = col < NV ? reinterpret_cast<const uint2 *>(sm + S.cst + L.off_wcol2) + col * L.qp
                                      : reinterpret_cast<const uint2 *>(sm + S.cst + L.off_pcol2) +
                                            (col < NS ? col - NV : col - NV - 8) * L.qp;
-        float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f}, d2[4] = {0.f, 0.f, 0.f, 0.f};
-        const int k0 = part * per, k1 = min(nks, k0 + per);
+        // one quarter's partial of this warp's n-tile
+        auto quarter = [&](int part) {
+            float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f}, d2[4] = {0.f, 0.f, 0.f, 0.f};
+            const int k0 = part * per, k1 = min(nks, k0 + per);
 #pragma unroll 2
-        for (int ks = k0; ks < k1; ++ks) {
-            const int c0 = ks * 8 + 2 * tq;
-            const float2 av = *reinterpret_cast<const float2 *>(arow + c0);
-            uint2 a[4], b0, b1;
-            split_tf32(av.x, a[0].x, a[0].y);
-            split_tf32(av.y, a[2].x, a[2].y);
-            a[1] = z;
-            a[3] = z;
-            ld_pair2(bcol + c0, b0, b1);
-            mma_pairs<PR>(d0, d1, d2, a, b0, b1);
-        }
-        if (g < tl.count) {
+            for (int ks = k0; ks < k1; ++ks) {
+                const int c0 = ks * 8 + 2 * tq;
+                const float2 av = *reinterpret_cast<const float2 *>(arow + c0);
+                uint2 a[4], b0, b1;
+                split_tf32(av.x, a[0].x, a[0].y);
+                split_tf32(av.y, a[2].x, a[2].y);
+                a[1] = z;
+                a[3] = z;
+                ld_pair2(bcol + c0, b0, b1);
+                mma_pairs<PR>(d0, d1, d2, a, b0, b1);
+            }
+            if (g < tl.count) {
 #pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                const int c = nt * 8 + 2 * tq + e;
-                const float v = d0[e] + d1[e] + d2[e];
-                if (split) {
-                    if (c < NS) sm[S.psp + (part * kMaxTile + g) * 24 + (c < NV ? c : c + 1)] = v;
-                } else {
-                    psi_apply(p, sm, S, g, c, v, cur2);
+                for (int e = 0; e < 2; ++e) {
+                    const int c = nt * 8 + 2 * tq + e;
+                    if (c < NS) sm[S.psp + (part * kMaxTile + g) * 24 + (c < NV ? c : c + 1)] = d0[e] + d1[e] + d2[e];
                 }
             }
-        }
+        };
         if (split) {
-            // the twelve task warps only (barrier 0 is the block's)
-            asm volatile("bar.sync 1, %0;\n" :: "r"(32 * 3 * kPsiParts) : "memory");
-            for (int i = threadIdx.x; i < tl.count * NS; i += 32 * 3 * kPsiParts) {
-                const int tt = i / NS, c = i - NS * tt, o = c < NV ? c : c + 1;
-                float v = 0.f;
+            quarter(warp / 3);
+        } else {
+#pragma unroll 1
+            for (int part = 0; part < kPsiParts; ++part) quarter(part);
+        }
+        // the task warps only (barrier 0 is the block's)
+        asm volatile("bar.sync 1, %0;\n" :: "r"(32 * ntask) : "memory");
+        for (int i = threadIdx.x; i < tl.count * NS; i += 32 * ntask) {
+            const int tt = i / NS, c = i - NS * tt, o = c < NV ? c : c + 1;
+            float v = 0.f;
 #pragma unroll
-                for (int k = 0; k < kPsiParts; ++k) v += sm[S.psp + (k * kMaxTile + tt) * 24 + o];
-                psi_apply(p, sm, S, tt, c, v, cur2);
-            }
+            for (int k = 0; k < kPsiParts; ++k) v += sm[S.psp + (k * kMaxTile + tt) * 24 + o];
+            psi_apply(p, sm, S, tt, c, v, cur2);
         }
     }
 }

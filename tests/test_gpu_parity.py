@@ -313,6 +313,24 @@ def test_best_selection_matches_oracle_key():
     np.testing.assert_allclose(best["coeffs"][2], g["xi2"][i_g], rtol=0, atol=0)
 
 
+@pytest.mark.parametrize("tile", [1, 2, 3, 5])
+def test_result_independent_of_tile_size(tile):
+    """Every per-trajectory sum has a fixed order whatever the tile and block
+    size (the heading contraction's four quarter-partials included), so a
+    solve with small tiles equals the default one bit for bit."""
+    T = tj()
+    pb = W.make_problem("paper", 0, B=40)
+    out = []
+    for t in (0, tile):
+        P = T.Problem(pb, tile=t)
+        P.solve(pb["init"].astype(np.float32), 20)
+        out.append((P.state(), P.results()))
+        P.close()
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    for k in ("res", "res_psi", "cost", "mind"):
+        np.testing.assert_array_equal(out[0][1][k], out[1][1][k])
+
+
 def test_best_async_equals_best():
     """am_get_best_async (device and pinned host output) gives am_get_best's record."""
     import torch
