@@ -31,8 +31,9 @@
 //   XI1   lam += rho R; xi1 += Minv (lam - Q xi1 + rho R); lambda_psi update
 //         (Eq. update_lambda_psi); per-trajectory sums of the last sweep
 //   EVAL  x, xdot, xddot, y, ..., c, s at step t (Eq. param); heading target
-//         psi_t and delta = psi_t - P xi2; Mpsi lam_psi - Mpsi H xi2
-//   PSI   W^T delta and P^T delta on the tensor cores
+//         psi_t and delta = psi_t - P xi2
+//   PSI   W^T delta and P^T delta on the tensor cores; Mpsi lam_psi -
+//         Mpsi H xi2 on warps without an MMA task (in EVAL on a small block)
 //   SWEEP xi2 += Mpsi (lam_psi - H xi2) + rho W^T delta; psi = P xi2; the
 //         closed-form alpha/d steps for every circle and obstacle (Eq. zeta_2 -
 //         compute_da) in the trig-free form (xt, yt) max(1, 1/sqrt(xt^2/a^2 +
@@ -53,7 +54,8 @@ namespace {
 
 constexpr int kMaxThreads = 768;
 constexpr int kMaxTile = 8;     // rows (side, trajectory) of one 16-row MMA tile
-constexpr int kRParts = 12;     // partials of R: (rv | ra | r0 segment) x quarter of the steps
+constexpr int kDotParts = 2;    // parts of the steps per segment of R in the DOT phase
+constexpr int kRParts = 3 * kDotParts;  // partials of R: (rv | ra | r0 segment) x part of the steps
 constexpr int kPsiParts = 4;    // partials of W^T delta, P^T delta: quarters of the steps
 
 constexpr float kTwoPi = 6.28318530717958647692f;
@@ -65,9 +67,9 @@ struct Smem {
 
 // Shared-memory layout (float offsets).
 //   xi1, lam  [2][T][48]   double-buffered, padded blocks of 12 per polynomial
-//   rb        [12][T][48]  partials of R per side (c_pos rows 0..10, c_slack rows
-//                          12..22): (rv, ra, r0 segment) x quarter of the steps;
-//                          the c_slack rows in the first four (R is the sum of all)
+//   rb        [3D][T][48]  partials of R per side (c_pos rows 0..10, c_slack rows
+//                          12..22), D = kDotParts: (rv, ra, r0 segment) x part of
+//                          the steps; the c_slack rows in the first D (R is the sum of all)
 //   xi2       [2][T][12]   double-buffered c_psi;  dx2 [T][12] last increment
 //   lps       [T][12]      lambda_psi
 //   ptp       [8][12]      P^T delta
@@ -358,12 +360,17 @@ __device__ void xi1_operand(const KParams &p, float *sm, const Smem &S, const Ti
 {
     const float rho = p.L.rho, coef = first ? rho : 2.f * rho;
     uint2 *XA = reinterpret_cast<uint2 *>(sm + S.XA);
-    for (int i = threadIdx.x; i < tl.count * 96; i += blockDim.x) {
-        const int tt = i / 96, e = i - 96 * tt, side = e / 48, k = e - 48 * side;
-        const int o = side * 24 + (k < 24 ? k : k - 24);
+    // the tile's lam + coef R entries first, then its xi1 entries, so that
+    // the threads summing the partials of R fill whole warps
+    const int nr = tl.count * 48;
+    for (int i = threadIdx.x; i < 2 * nr; i += blockDim.x) {
+        const bool lam_part = i < nr;
+        const int j = lam_part ? i : i - nr;
+        const int tt = j / 48, o = j - 48 * tt, side = o / 24;
+        const int k = lam_part ? o - 24 * side : o - 24 * side + 24;
         const int src = (cur * p.T + tt) * 48 + o;
         float v;
-        if (k < 24) {
+        if (lam_part) {
             const float lam = sm[S.lam + src], R = rsum(sm, S, tt * 48 + o);
             v = fmaf(coef, R, lam);
             sm[S.lam + ((cur ^ 1) * p.T + tt) * 48 + o] = first ? lam : fmaf(rho, R, lam);
@@ -491,45 +498,54 @@ __device__ void phase_xi1(const KParams &p, float *sm, const Smem &S, const Tile
     }
 }
 
-// Zero the accumulators the tensor-core phases add into, and form
-// Mpsi lam_psi - Mpsi H xi2 for the heading step.  Runs in the EVAL phase
-// (after XI1 has read R and P^T delta, before PSI and DOT write them).
-__device__ void prepare_accumulators(const KParams &p, float *sm, const Smem &S, const Tile &tl,
-                                     int cur2)
+// Mpsi lam_psi - Mpsi H xi2 for the heading step, row j of trajectory tt
+// (i = tt * NV + j).  Formed after XI1 has updated lam_psi and before the
+// PSI epilogue applies the step: in the PSI phase by warps that have no MMA
+// task when the block has them, else by the whole block in the EVAL phase.
+__device__ __forceinline__ void heading_base(const KParams &p, float *sm, const Smem &S, int i, int cur2)
 {
     const ConstLayout &L = p.L;
     const float *cst = sm + S.cst;
-    const int Tn = tl.count;
-    for (int i = threadIdx.x; i < Tn * NV; i += blockDim.x) {
-        const int tt = i / NV, j = i - NV * tt;
-        const float *lp = sm + S.lps + tt * 12;
-        const float *x2 = sm + S.xi2 + (cur2 * p.T + tt) * 12;
-        float b0 = 0.f, b1 = 0.f;
+    const int tt = i / NV, j = i - NV * tt;
+    const float *lp = sm + S.lps + tt * 12;
+    const float *x2 = sm + S.xi2 + (cur2 * p.T + tt) * 12;
+    float b0 = 0.f, b1 = 0.f;
 #pragma unroll
-        for (int c = 0; c < NV; ++c) {
-            b0 = fmaf(cst[L.off_mpsi + c * 12 + j], lp[c], b0);
-            b1 = fmaf(cst[L.off_mpsih + c * 12 + j], x2[c], b1);
-        }
-        sm[S.bas + tt * 12 + j] = b0 - b1;
+    for (int c = 0; c < NV; ++c) {
+        b0 = fmaf(cst[L.off_mpsi + c * 12 + j], lp[c], b0);
+        b1 = fmaf(cst[L.off_mpsih + c * 12 + j], x2[c], b1);
     }
+    sm[S.bas + tt * 12 + j] = b0 - b1;
+}
+
+// Warps of the PSI phase: twelve (n-tile, quarter) MMA tasks when the block
+// has twelve warps, and three more forming the heading base when it has
+// fifteen (tile * NV <= 88 rows).
+constexpr int kBaseWarps = 3;
+
+__device__ __forceinline__ bool base_in_psi()
+{
+    return int(blockDim.x >> 5) >= 3 * kPsiParts + kBaseWarps;
 }
 
 // DOT phase on the tensor cores.  One 16-row tile: row = side*8 + trajectory.
-// Sixteen warp tasks: (segment rv | ra | r0 | r1, quarter of the steps), each
-// for both n-tiles of 8 output columns, so a task loads its A fragment once
-// (FP32, split here) for two products.  Each task writes its own partial of R
-// (rv, ra, r0 -> c_pos rows of partial 4 seg + quarter; r1 -> c_slack rows of
-// partial quarter), so no two tasks write one word.
+// 4 kDotParts warp tasks: (segment rv | ra | r0 | r1, part of the steps),
+// each for both n-tiles of 8 output columns, so a task loads its A fragment
+// once (FP32, split here) for two products.  Each task writes its own partial
+// of R (rv, ra, r0 -> c_pos rows of partial kDotParts seg + part; r1 -> c_slack
+// rows of partial part), so no two tasks write one word.  A block with fewer
+// warps runs the tasks in turn.  Few long tasks measured faster than many
+// short ones: every partial costs shared-memory stores here and loads in XI1.
 template <int PR>
 __device__ void phase_dot(const KParams &p, float *sm, const Smem &S, const Tile &tl)
 {
     const ConstLayout &L = p.L;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane >> 2, tq = lane & 3;
-    const int nks = (L.q + 7) >> 3, quarter = (nks + 3) >> 2;
+    const int nks = (L.q + 7) >> 3, per = (nks + kDotParts - 1) / kDotParts;
     const int row = frag_row4(g, tl.count);
-    for (int task = warp; task < 16; task += blockDim.x >> 5) {
-        const int seg = task >> 2, part = task & 3;
+    for (int task = warp; task < 4 * kDotParts; task += blockDim.x >> 5) {
+        const int seg = task / kDotParts, part = task - kDotParts * seg;
         const int bsel = seg == 0 ? 1 : seg == 1 ? 2 : 0;  // Pd, Pdd, P, P
         const uint2 *B = reinterpret_cast<const uint2 *>(sm + S.cst + L.off_pcol2) + bsel * NV * L.qp;
         // n-tile 1 holds columns 8..10; its other lanes give discarded
@@ -541,7 +557,7 @@ __device__ void phase_dot(const KParams &p, float *sm, const Smem &S, const Tile
         // chains per n-tile (measured faster than three, fewer registers)
         float d0[4] = {0.f, 0.f, 0.f, 0.f}, d2[4] = {0.f, 0.f, 0.f, 0.f};
         float e0[4] = {0.f, 0.f, 0.f, 0.f}, e2[4] = {0.f, 0.f, 0.f, 0.f};
-        const int k0 = part * quarter, k1 = min(nks, k0 + quarter);
+        const int k0 = part * per, k1 = min(nks, k0 + per);
 #pragma unroll 1
         for (int ks = k0; ks < k1; ++ks) {
             const int c0 = ks * 8 + 2 * tq;
@@ -556,7 +572,7 @@ __device__ void phase_dot(const KParams &p, float *sm, const Smem &S, const Tile
             mma_pairs<PR>(e0, e0, e2, ap, b2, b3);
         }
         if (g < tl.count) {
-            float *R = sm + S.rb + (seg < 3 ? 4 * seg + part : part) * S.T * 48 + g * 48;
+            float *R = sm + S.rb + (seg < 3 ? kDotParts * seg + part : part) * S.T * 48 + g * 48;
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int side = e >> 1, c = 2 * tq + (e & 1);
@@ -571,7 +587,8 @@ __device__ void phase_dot(const KParams &p, float *sm, const Smem &S, const Tile
 // 11..21) per trajectory; rows 0..7 = trajectories, rows 8..15 are zero.  The
 // heading step is then applied once per coefficient:
 //   xi2' = xi2 + (Mpsi lam_psi - Mpsi H xi2) + rho W^T delta
-// (the first bracket formed in the EVAL phase), writing xi2' and the increment.
+// (the first bracket formed by the base warps of this phase, or in the EVAL
+// phase on a small block), writing xi2' and the increment.
 // Partials over four quarters of the steps (three n-tiles each) are written,
 // the task warps meet at a named barrier, and the first of them sum the
 // partials and apply the step.
@@ -600,6 +617,10 @@ __device__ void phase_psi(const KParams &p, float *sm, const Smem &S, const Tile
     // order, so the result does not depend on the block size.
     const bool split = (blockDim.x >> 5) >= 3 * kPsiParts;
     const int ntask = split ? 3 * kPsiParts : 3;
+    // warps ntask .. ntask + nbase - 1 form the heading base and hand it to
+    // the epilogue through the named barrier (arrive, no wait)
+    const int nbase = base_in_psi() ? kBaseWarps : 0;
+    const int nbar = 32 * (ntask + nbase);
     const float *arow = sm + S.PS + frag_row4(g, tl.count) * L.qp;
     const uint2 z = make_uint2(0u, 0u);
     if (warp < ntask) {
@@ -639,8 +660,8 @@ __device__ void phase_psi(const KParams &p, float *sm, const Smem &S, const Tile
 #pragma unroll 1
             for (int part = 0; part < kPsiParts; ++part) quarter(part);
         }
-        // the task warps only (barrier 0 is the block's)
-        asm volatile("bar.sync 1, %0;\n" :: "r"(32 * ntask) : "memory");
+        // the task and base warps only (barrier 0 is the block's)
+        asm volatile("bar.sync 1, %0;\n" :: "r"(nbar) : "memory");
         for (int i = threadIdx.x; i < tl.count * NS; i += 32 * ntask) {
             const int tt = i / NS, c = i - NS * tt, o = c < NV ? c : c + 1;
             float v = 0.f;
@@ -648,6 +669,11 @@ __device__ void phase_psi(const KParams &p, float *sm, const Smem &S, const Tile
             for (int k = 0; k < kPsiParts; ++k) v += sm[S.psp + (k * kMaxTile + tt) * 24 + o];
             psi_apply(p, sm, S, tt, c, v, cur2);
         }
+    } else if (warp < ntask + nbase) {
+        const int i = int(threadIdx.x) - 32 * ntask;
+        if (i < tl.count * NV) heading_base(p, sm, S, i, cur2);
+        __threadfence_block();
+        asm volatile("bar.arrive 1, %0;\n" :: "r"(nbar) : "memory");
     }
 }
 
@@ -977,7 +1003,8 @@ __device__ void run_tile(const KParams &p, float *sm, const Smem &S, const Tile 
             r.psi_t = r.psi_prev + wrap_pi(atan2_heading(r.s, r.c) - r.psi_prev);
             sm[S.PS + tt * L.qp + t] = r.psi_t - r.psi_cur;
         }
-        prepare_accumulators(p, sm, S, tl, cur2);
+        if (!base_in_psi())
+            for (int i = threadIdx.x; i < Tn * NV; i += blockDim.x) heading_base(p, sm, S, i, cur2);
         __syncthreads();
         phase_psi<PR>(p, sm, S, tl, cur2);
         __syncthreads();

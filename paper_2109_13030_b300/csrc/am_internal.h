@@ -155,7 +155,7 @@ struct FusedProblem {
 // World-space margin (m) of the near-obstacle test: a warp's list of
 // obstacles near its steps stays valid until one of its robot centres has
 // moved farther than this since the list was formed.
-constexpr float kNearMargin = 0.25f;
+constexpr float kNearMargin = 0.6f;
 
 // Grouped launch: many problems' tiles in persistent kernels, one kernel per
 // variant (circle count, alpha form) present; the variant kernels of one
