@@ -151,25 +151,44 @@ __global__ void __launch_bounds__(1024) cem_refit_kernel(CemArgs a)
         idx[i] = i;
     }
     __syncthreads();
+    // Bitonic sort of the (score, index) pairs.  The pairs form one chunk per
+    // warp (np / 32 pairs, at least 32 or all of them); a sub-stage whose
+    // partners lie within a chunk runs on its warp with warp synchronisation,
+    // the others on the whole block.  The compare-exchange network, and so
+    // the result, is the same either way.
+    auto exchange = [&](int i, int j, int k) {
+        const int l = i ^ j;
+        if (l > i) {
+            const bool up = (i & k) == 0;
+            const bool gt = key[i] > key[l] || (key[i] == key[l] && idx[i] > idx[l]);
+            if (gt == up) {
+                const float tk = key[i];
+                key[i] = key[l];
+                key[l] = tk;
+                const int ti = idx[i];
+                idx[i] = idx[l];
+                idx[l] = ti;
+            }
+        }
+    };
+    const int warp = tid >> 5, lane = tid & 31;
+    const int chunk = np <= 32 ? np : (np / 32 > 32 ? np / 32 : 32), nchunks = np / chunk;
+    bool warp_local = false;  // the last sub-stage ended with warp synchronisation only
     for (int k = 2; k <= np; k <<= 1)
         for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = tid; i < np; i += blockDim.x) {
-                const int l = i ^ j;
-                if (l > i) {
-                    const bool up = (i & k) == 0;
-                    const bool gt = key[i] > key[l] || (key[i] == key[l] && idx[i] > idx[l]);
-                    if (gt == up) {
-                        const float tk = key[i];
-                        key[i] = key[l];
-                        key[l] = tk;
-                        const int ti = idx[i];
-                        idx[i] = idx[l];
-                        idx[l] = ti;
-                    }
-                }
+            if (j < chunk) {
+                if (warp < nchunks)
+                    for (int m = lane; m < chunk; m += 32) exchange(warp * chunk + m, j, k);
+                __syncwarp();
+                warp_local = true;
+            } else {
+                if (warp_local) __syncthreads();
+                for (int i = tid; i < np; i += blockDim.x) exchange(i, j, k);
+                __syncthreads();
+                warp_local = false;
             }
-            __syncthreads();
         }
+    __syncthreads();
     for (int e = tid; e < a.K * kZ; e += blockDim.x) E[e] = a.z[(size_t)idx[e / kZ] * kZ + e % kZ];
     __syncthreads();
     // elite mean and covariance: kParts threads per entry over strided elites,
