@@ -45,7 +45,7 @@ __host__ __device__ inline int cem_obs_floats(const ConstLayout &L) { return L.o
 // `given`, the samples are full coefficient vectors (count x 33: c_x, c_y,
 // c_psi) instead of draws.  The basis rows, and the obstacle sections when
 // they fit, are staged in shared memory once per block.
-__global__ void __launch_bounds__(32 * kCemWarps, 3) cem_score_kernel(CemArgs a)
+__global__ void __launch_bounds__(32 * kCemWarps, 4) cem_score_kernel(CemArgs a)
 {
     extern __shared__ __align__(16) float cem_sm[];
     const ConstLayout &L = a.L;
