@@ -1237,7 +1237,7 @@ int am_group_autotune(am_group *g, int iters, void *stream, int *threads_out, fl
     const int saved = g->threads;
     int best = 0;
     float best_ms = 1e30f;
-    for (int threads = 256; threads <= fused_max_threads(); threads += 64) {
+    for (int threads = 128; threads <= fused_max_threads(); threads += 64) {
         g->threads = threads;
         if (build_work(g, threads, iters, sms) != AM_OK) continue;
         if (am_group_solve(g, iters, stream) != AM_OK) continue;  // warm-up (and graph capture)

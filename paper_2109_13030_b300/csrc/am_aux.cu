@@ -97,7 +97,10 @@ __global__ void scale_multipliers_kernel(float *state, int B, float factor)
 
 // Obstacle sections of the constant block: centre tracks in ellipse-scaled
 // coordinates (x_j(t)/a_j, y_j(t)/b_j) and per-obstacle (1/a_j, 1/b_j, a_j, b_j),
-// with the semi-axes inflated by the robot circle radius.
+// with the semi-axes inflated by the robot circle radius.  The same values in
+// the fused kernel's paired form: per pair of steps (t, t + 1) the negated
+// scaled centre coordinates, and every per-obstacle constant twice, so that
+// one 128-bit load gives the operands of paired FP32 instructions.
 __global__ void prep_obstacles_kernel(float *cblob, ConstLayout L, const float *xo, const float *yo,
                                       const float *a, const float *b, float r_c)
 {
@@ -106,11 +109,19 @@ __global__ void prep_obstacles_kernel(float *cblob, ConstLayout L, const float *
         const int j = i / L.q, t = i - L.q * j;
         const float aj = a[j] + r_c, bj = b[j] + r_c;
         float2 *obs = reinterpret_cast<float2 *>(cblob + L.off_obs);
-        obs[j * L.qs + t] = make_float2(xo[i] / aj, yo[i] / bj);
+        const float u = xo[i] / aj, v = yo[i] / bj;
+        obs[j * L.qs + t] = make_float2(u, v);
+        float *o2 = cblob + L.off_obs2 + j * 2 * L.qs + 4 * (t >> 1) + (t & 1);
+        o2[0] = -u;
+        o2[2] = -v;
     }
     if (i < L.n) {
         const float aj = a[i] + r_c, bj = b[i] + r_c;
-        reinterpret_cast<float4 *>(cblob + L.off_obc)[i] = make_float4(1.f / aj, 1.f / bj, aj, bj);
+        const float ia = 1.f / aj, ib = 1.f / bj;
+        reinterpret_cast<float4 *>(cblob + L.off_obc)[i] = make_float4(ia, ib, aj, bj);
+        float4 *c2 = reinterpret_cast<float4 *>(cblob + L.off_obc2) + 2 * i;
+        c2[0] = make_float4(ia, ia, ib, ib);
+        c2[1] = make_float4(aj, aj, bj, bj);
         // Every circle centre lies within r_max max(1/a, 1/b) of the robot
         // centre in the ellipse-scaled frame; a centre at squared distance
         // above this threshold (with a relative margin for rounding) has every

@@ -3,10 +3,11 @@
 //
 // One CTA stays resident on each SM and works through tiles of T <= 8
 // trajectories.  It stages the constant block into shared memory once (bulk
-// async copy, completion on an mbarrier), keeps xi1, xi2, lambda, lambda_psi
-// and the residual contraction R = F^T (g - F xi1) of every trajectory of the
-// tile in shared memory for all iterations, and writes the state back only
-// after the last one.  Nothing per element (alpha, d, g) is ever stored.
+// async copies, completion on an mbarrier), keeps xi1, xi2, lambda,
+// lambda_psi and the residual contraction R = F^T (g - F xi1) of every
+// trajectory of the tile in shared memory for all iterations, and writes the
+// state back only after the last one.  Nothing per element (alpha, d, g) is
+// ever stored.
 //
 // The position step of Eq. over_3, xi1' = Minv (lam + rho F^T g) + kb, is
 // evaluated in the algebraically equal increment form
@@ -19,6 +20,15 @@
 // starts from a reference whose boundary control points are set from the
 // boundary conditions, so A xi = b holds from the first step on.
 //
+// Per-step work (the trajectory values of Eq. param, the heading target and
+// the closed-form alpha/d steps) runs on one thread per pair of consecutive
+// steps (t, t + 1) of a trajectory.  The thread keeps the basis rows P, Pd,
+// Pdd of its two steps in registers for the whole tile and evaluates both
+// steps with paired FP32 instructions (fma/mul/add on float2, each component
+// rounded exactly like its scalar form); the coefficients it reads are kept
+// duplicated, (c, c), beside xi1 and xi2 so that one 128-bit load gives two
+// paired operands.
+//
 // The two contractions over the time steps -- R (Pd^T rv + Pdd^T ra + P^T r0
 // and P^T r1 per side) and the heading right-hand side (W^T delta, P^T delta)
 // -- are dense products of a [rows x steps] operand written by the sweep with
@@ -30,15 +40,15 @@
 // Phases of one iteration, separated by __syncthreads():
 //   XI1   lam += rho R; xi1 += Minv (lam - Q xi1 + rho R); lambda_psi update
 //         (Eq. update_lambda_psi); per-trajectory sums of the last sweep
-//   EVAL  x, xdot, xddot, y, ..., c, s at step t (Eq. param); heading target
-//         psi_t and delta = psi_t - P xi2
-//   PSI   W^T delta and P^T delta on the tensor cores; Mpsi lam_psi -
-//         Mpsi H xi2 on warps without an MMA task (in EVAL on a small block)
-//   SWEEP xi2 += Mpsi (lam_psi - H xi2) + rho W^T delta; psi = P xi2; the
-//         closed-form alpha/d steps for every circle and obstacle (Eq. zeta_2 -
-//         compute_da) in the trig-free form (xt, yt) max(1, 1/sqrt(xt^2/a^2 +
-//         yt^2/b^2)), the velocity and acceleration projections, and the
-//         per-step residual vectors of R
+//   EVAL  x, xdot, xddot, y, ..., c, s at the thread's two steps (Eq. param);
+//         heading target psi_t and delta = psi_t - P xi2; Mpsi lam_psi -
+//         Mpsi H xi2 for the heading step
+//   PSI   W^T delta and P^T delta on the tensor cores, then
+//         xi2 += Mpsi (lam_psi - H xi2) + rho W^T delta
+//   SWEEP psi = P xi2; the closed-form alpha/d steps for every circle and
+//         obstacle (Eq. zeta_2 - compute_da) in the trig-free form (xt, yt)
+//         max(1, 1/sqrt(xt^2/a^2 + yt^2/b^2)), the velocity and acceleration
+//         projections, and the per-step residual vectors of R
 //   DOT   R on the tensor cores
 #include <cuda_runtime.h>
 
@@ -52,46 +62,54 @@
 namespace trajam {
 namespace {
 
-constexpr int kMaxThreads = 768;
-constexpr int kMaxTile = 8;     // rows (side, trajectory) of one 16-row MMA tile
-constexpr int kDotParts = 2;    // parts of the steps per segment of R in the DOT phase
+constexpr int kMaxThreads = 384;  // twelve warps: every tensor-core task of a phase at once
+constexpr int kMaxTile = 8;       // rows (side, trajectory) of one 16-row MMA tile
+constexpr int kDotParts = 2;      // parts of the steps per segment of R in the DOT phase
 constexpr int kRParts = 3 * kDotParts;  // partials of R: (rv | ra | r0 segment) x part of the steps
-constexpr int kPsiParts = 4;    // partials of W^T delta, P^T delta: quarters of the steps
+constexpr int kMinPairThreads = 44;  // threads per trajectory at least (short horizons)
 
 constexpr float kTwoPi = 6.28318530717958647692f;
 constexpr float kPi = 3.14159265358979323846f;
 
+// Threads per trajectory: one per pair of consecutive steps.
+__host__ __device__ inline int pair_threads(int q)
+{
+    const int np = (q + 1) / 2;
+    return np > kMinPairThreads ? np : kMinPairThreads;
+}
+
 struct Smem {
-    int cst, xi1, lam, rb, xi2, dx2, lps, ptp, psp, bas, G2, RS, GX, PS, XA, NR, NM, bar, total, T;
+    int cst, cob, xi1, lam, rb, xi2, dx2, lps, ptp, G2, RS, GX, U, PTD, XD, X2D, bar, total, T;
 };
 
 // Shared-memory layout (float offsets).
+//   cst region [off_fused, off_obs) of the constant block (shape sections);
+//   cob region [off_obt, total) (near thresholds, paired obstacle sections)
 //   xi1, lam  [2][T][48]   double-buffered, padded blocks of 12 per polynomial
 //   rb        [3D][T][48]  partials of R per side (c_pos rows 0..10, c_slack rows
 //                          12..22), D = kDotParts: (rv, ra, r0 segment) x part of
 //                          the steps; the c_slack rows in the first D (R is the sum of all)
 //   xi2       [2][T][12]   double-buffered c_psi;  dx2 [T][12] last increment
 //   lps       [T][12]      lambda_psi
-//   ptp       [8][12]      P^T delta
-//   psp       [4][8][24]   partials of W^T delta (0..10) and P^T delta (12..22) per quarter
-//   bas       [8][12]      Mpsi lam_psi - Mpsi H xi2
+//   ptp       [8][12]      P^T delta of the last heading step
 //   G2        [2T][RS]     residual vectors, row = side*T + trajectory; segments
 //                          rv | ra | r0 | r1 of qp steps
 //   GX        [T][4][qs]   per-step squared residual, heading residual, cost, distance
-//   PS        [T][qp]      delta = psi_t - P xi2 per trajectory
-//   XA        [2T][56][2]  A operand of the position step as TF32 pairs, row =
-//                          side*T + trajectory: lam + coef R (24) | xi1 (24)
-//   NR        [T*q][2]     robot centre of each step when its warp's near list was formed
-//   NM        [24][2]      near-obstacle bit lists per warp (obstacles 0..31, 32..63)
-// The constant block is staged from its offset off_fused on; cst is shifted so
-// that sm + cst + off_x addresses section x.
+//   U         [T][48]      lam + coef R per side (padded), the position step's input
+//   PTD       [T][np][12]  P^T delta over the two steps of each stepper thread
+//   XD        [2][T][12][4][2] xi1 duplicated per coefficient k: (cx, cx, cy, cy,
+//                          cc, cc, cs, cs), both buffers
+//   X2D       [2][T][12][2] xi2 duplicated, both buffers
+// The constant block's shape sections are staged so that sm + cst + off_x
+// addresses section x; the obstacle region starts at cob (off_obt there).
 __host__ __device__ inline Smem smem_layout(const ConstLayout &L, int T)
 {
     Smem s;
     int o = 0;
     s.T = T;
     s.bar = o; o += 4;  // one 8-byte mbarrier at a fixed offset, 16-byte aligned
-    s.cst = o - L.off_fused; o += L.total - L.off_fused;
+    s.cst = o - L.off_fused; o += L.off_obs - L.off_fused;
+    s.cob = o; o += L.total - L.off_obt;
     s.xi1 = o; o += 2 * T * 48;
     s.lam = o; o += 2 * T * 48;
     s.rb = o; o += kRParts * T * 48;
@@ -99,17 +117,15 @@ __host__ __device__ inline Smem smem_layout(const ConstLayout &L, int T)
     s.dx2 = o; o += T * 12;
     s.lps = o; o += T * 12;
     s.ptp = o; o += kMaxTile * 12;
-    s.psp = o; o += kPsiParts * kMaxTile * 24;
-    s.bas = o; o += kMaxTile * 12;
     // RS = 8 mod 32 and qp = 8 mod 16: the 64-bit fragment loads of four
     // neighbouring rows fall on distinct banks
     s.RS = 4 * L.qp + 8;
     s.G2 = o; o += 2 * T * s.RS;
     s.GX = o; o += T * 4 * L.qs;
-    s.PS = o; o += T * L.qp;
-    s.XA = o; o += 2 * T * 56 * 2;
-    s.NR = o; o += 2 * T * L.q;
-    s.NM = o; o += 24 * 2;
+    s.U = o; o += T * 48;
+    s.PTD = o; o += T * ((L.q + 1) / 2) * 12;
+    s.XD = o; o += 2 * T * 12 * 8;
+    s.X2D = o; o += 2 * T * 12 * 2;
     o = (o + 3) & ~3;
     s.total = o;
     return s;
@@ -239,13 +255,6 @@ __device__ __forceinline__ void mma_pairs(float (&d0)[4], float (&d1)[4], float 
     }
 }
 
-__device__ __forceinline__ void st_split(uint2 *dst, float v)
-{
-    uint2 w;
-    split_tf32(v, w.x, w.y);
-    *dst = w;
-}
-
 // The columns of one k-step are permuted so that the two k elements a lane
 // holds (fragment k = t and t + 4) are the adjacent columns 2t, 2t + 1: one
 // 128-bit load brings both (hi, lo) pairs.  A and B use the same permutation,
@@ -257,16 +266,9 @@ __device__ __forceinline__ void ld_pair2(const uint2 *p, uint2 &e0, uint2 &e1)
     e1 = make_uint2(v.z, v.w);
 }
 
-// Row of a fragment lane: lanes past the tile read a row of the same parity
-// (their results are discarded; MMA rows are independent), keeping the
-// neighbouring-row bank pattern.
-__device__ __forceinline__ int frag_row(int g, int count)
-{
-    return g < count ? g : (count > 1 ? (g & 1) : 0);
-}
-
-// The same for 64-bit loads, whose 16-lane wavefronts hold four rows: a row
-// equal to the lane's modulo 4 where the tile has one.
+// Row of a fragment lane for 64-bit loads, whose 16-lane wavefronts hold four
+// rows: lanes past the tile read the row equal to the lane's modulo 4 where the
+// tile has one (their results are discarded; MMA rows are independent).
 __device__ __forceinline__ int frag_row4(int g, int count)
 {
     return g < count ? g : (g & 3) < count ? (g & 3) : 0;
@@ -307,23 +309,6 @@ __device__ __forceinline__ float atan2_heading(float y, float x)
 // Side-row r (0..21) of (c_pos, c_slack) -> padded index within a 24-float side block.
 __device__ __forceinline__ int rowpad(int r) { return r < NV ? r : r + 1; }
 
-__device__ __forceinline__ float dot11(const float *a, const float *b)
-{
-    float s = 0.f;
-#pragma unroll
-    for (int k = 0; k < NV; ++k) s = fmaf(a[k], b[k], s);
-    return s;
-}
-
-__device__ __forceinline__ void load12(float (&r)[12], const float *p)
-{
-    const float4 *v = reinterpret_cast<const float4 *>(p);
-    float4 a = v[0], b = v[1], c = v[2];
-    r[0] = a.x; r[1] = a.y; r[2] = a.z; r[3] = a.w;
-    r[4] = b.x; r[5] = b.y; r[6] = b.z; r[7] = b.w;
-    r[8] = c.x; r[9] = c.y; r[10] = c.z; r[11] = c.w;
-}
-
 // Wrap into (-pi, pi].
 __device__ __forceinline__ float wrap_pi(float a)
 {
@@ -342,126 +327,59 @@ __device__ __forceinline__ Tile tile_of(int i, int B, int ntiles)
     return {int(lo), int(hi - lo)};
 }
 
+
 // ----------------------------------------------------------------- phases
+
+// Position of polynomial block blk (0 c_x, 1 c_c, 2 c_y, 3 c_s) within a
+// duplicated xi1 entry (cx, cx, cy, cy, cc, cc, cs, cs).
+__device__ __forceinline__ int dpos(int blk) { return blk == 0 ? 0 : blk == 2 ? 1 : blk == 1 ? 2 : 3; }
+
+// Writes entry o (padded index blk * 12 + k) of trajectory tt's xi1 into
+// buffer buf, and its duplicate.
+__device__ __forceinline__ void put_xi1(float *sm, const Smem &S, int buf, int tt, int o, float v)
+{
+    sm[S.xi1 + (buf * S.T + tt) * 48 + o] = v;
+    const int blk = o / 12, k = o - 12 * blk;
+    reinterpret_cast<float2 *>(sm + S.XD)[((buf * S.T + tt) * 12 + k) * 4 + dpos(blk)] = make_float2(v, v);
+}
+
+// The same for coefficient k of trajectory tt's xi2.
+__device__ __forceinline__ void put_xi2(float *sm, const Smem &S, int buf, int tt, int k, float v)
+{
+    sm[S.xi2 + (buf * S.T + tt) * 12 + k] = v;
+    reinterpret_cast<float2 *>(sm + S.X2D)[(buf * S.T + tt) * 12 + k] = make_float2(v, v);
+}
 
 // XI1 phase: the multiplier update of the finished iteration, the next xi1 in
 // increment form, the lambda_psi update and the per-trajectory sums.
 //   first: lam' = lam,          xi1' = xi1 + Minv (lam + rho R) - MQ xi1
 //   later: lam' = lam + rho R,  xi1' = xi1 + Minv (lam + 2 rho R) - MQ xi1
 //   post (no solve): lam' = lam + rho R, xi1' = xi1
-// Position step on the tensor cores, one 16-row tile (row = side*8 + trajectory):
-//   D[row][np] = sum_k A[row][k] Bt[np][k],  A = [lam + coef R | xi1],  Bt = [Minv | -Minv Q]
-// on padded indices (k, np in 0..23 per side, 11 and 23 are zero pads), then
-// xi1' = xi1 + D.  The whole block first forms A (split into TF32 pairs) and
-// lam' once; three warp tasks, one per n-tile of 8 output columns, then run
-// the products.
-__device__ void xi1_operand(const KParams &p, float *sm, const Smem &S, const Tile &tl, int cur,
-                            bool first)
-{
-    const float rho = p.L.rho, coef = first ? rho : 2.f * rho;
-    uint2 *XA = reinterpret_cast<uint2 *>(sm + S.XA);
-    // the tile's lam + coef R entries first, then its xi1 entries, so that
-    // the threads summing the partials of R fill whole warps
-    const int nr = tl.count * 48;
-    for (int i = threadIdx.x; i < 2 * nr; i += blockDim.x) {
-        const bool lam_part = i < nr;
-        const int j = lam_part ? i : i - nr;
-        const int tt = j / 48, o = j - 48 * tt, side = o / 24;
-        const int k = lam_part ? o - 24 * side : o - 24 * side + 24;
-        const int src = (cur * p.T + tt) * 48 + o;
-        float v;
-        if (lam_part) {
-            const float lam = sm[S.lam + src], R = rsum(sm, S, tt * 48 + o);
-            v = fmaf(coef, R, lam);
-            sm[S.lam + ((cur ^ 1) * p.T + tt) * 48 + o] = first ? lam : fmaf(rho, R, lam);
-        } else {
-            v = sm[S.xi1 + src];
-        }
-        st_split(XA + (side * S.T + tt) * 56 + k, v);
-    }
-}
-
-__device__ void xi1_mma(const KParams &p, float *sm, const Smem &S, const Tile &tl, int cur)
-{
-    const ConstLayout &L = p.L;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 2, tq = lane & 3;
-    const bool valid = g < tl.count;
-    const int row = frag_row(g, tl.count);
-    const uint2 *XA = reinterpret_cast<const uint2 *>(sm + S.XA);
-    const uint2 *a_lo = XA + row * 56, *a_hi = XA + (S.T + row) * 56;
-    for (int nt = warp; nt < 3; nt += blockDim.x >> 5) {
-        const uint2 *brow = reinterpret_cast<const uint2 *>(sm + S.cst + L.off_xib2) + (nt * 8 + g) * 56;
-        float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f}, d2[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-        for (int ks = 0; ks < 6; ++ks) {
-            const int c0 = ks * 8 + 2 * tq;  // permuted k-step columns
-            uint2 a[4], b0, b1;
-            ld_pair2(a_lo + c0, a[0], a[2]);
-            ld_pair2(a_hi + c0, a[1], a[3]);
-            ld_pair2(brow + c0, b0, b1);
-            mma_pairs<0>(d0, d1, d2, a, b0, b1);
-        }
-        if (valid) {
-            const float *xi = sm + S.xi1 + (cur * p.T + g) * 48;
-            float *xi_n = sm + S.xi1 + ((cur ^ 1) * p.T + g) * 48;
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int c = nt * 8 + 2 * tq + (e & 1);
-                if (c == NV || c == 23) continue;  // pads stay zero
-                const int o = (e >> 1) * 24 + c;
-                xi_n[o] = xi[o] + (d0[e] + d1[e] + d2[e]);
-            }
-        }
-    }
-}
-
+// A first pass forms u = lam + coef R and lam' for every (trajectory, side,
+// row), updates lambda_psi (Eq. update_lambda_psi) and reduces the sums of
+// the last sweep; after a block barrier one thread per output row evaluates
+// xi1' = xi1 + Minv u - MQ xi1 in FP32 (44 x 48 per trajectory: far too small
+// for the tensor cores to pay for their operand traffic).
 __device__ void phase_xi1(const KParams &p, float *sm, const Smem &S, const Tile &tl, int cur,
                           bool first, bool solve, bool sums, bool final_out, int kprev)
 {
     const ConstLayout &L = p.L;
     const float *cst = sm + S.cst;
-    const float rho = L.rho;
+    const float rho = L.rho, coef = first ? rho : 2.f * rho;
     const int Tn = tl.count;
-    // With the position step on the tensor cores (warps 0..2), the remaining
-    // tasks go to the threads after them when the block has enough.
-    const int n_xi = solve ? 0 : Tn * 44, n_lp = Tn * NV, n_sc = sums ? Tn * 4 : 0;
-    const int ntask = n_xi + n_lp + n_sc;
-    int base = 0;
-    if (solve) {
-        xi1_operand(p, sm, S, tl, cur, first);
-        __syncthreads();
-        xi1_mma(p, sm, S, tl, cur);
-        if (int(blockDim.x) >= 96 + ntask) base = 96;
-    }
-    const int stride = int(blockDim.x) - base;
-    for (int task = int(threadIdx.x) - base; task >= 0 && task < ntask; task += stride) {
-        if (task < n_xi) {
-            const int tt = task / 44, rem = task - 44 * tt, side = rem / NS, row = rem - NS * side;
-            const float *lam = sm + S.lam + (cur * p.T + tt) * 48 + 24 * side;
-            const float *xi = sm + S.xi1 + (cur * p.T + tt) * 48 + 24 * side;
-            const int rbase = tt * 48 + 24 * side;
-            float *lam_n = sm + S.lam + ((cur ^ 1) * p.T + tt) * 48 + 24 * side;
-            float *xi_n = sm + S.xi1 + ((cur ^ 1) * p.T + tt) * 48 + 24 * side;
-            const int rp = rowpad(row);
-            float xn = xi[rp];
-            if (solve) {
-                const float coef = first ? rho : 2.f * rho;
-                float a0 = 0.f, a1 = 0.f;
-#pragma unroll
-                for (int c = 0; c < NS; ++c) {
-                    const int cp = rowpad(c);
-                    a0 = fmaf(cst[L.off_mt + c * 24 + row], fmaf(coef, rsum(sm, S, rbase + cp), lam[cp]), a0);
-                    a1 = fmaf(cst[L.off_mq + c * 24 + row], xi[cp], a1);
-                }
-                xn += a0 - a1;
-            }
-            xi_n[rp] = xn;
-            lam_n[rp] = first ? lam[rp] : fmaf(rho, rsum(sm, S, rbase + rp), lam[rp]);
-        } else if (task < n_xi + n_lp) {
-            if (first) continue;
+    const int n_op = Tn * 48, n_lp = first ? 0 : Tn * NV, n_sc = sums ? Tn * 4 : 0;
+    const int ntask = n_op + n_lp + n_sc;
+    for (int task = threadIdx.x; task < ntask; task += blockDim.x) {
+        if (task < n_op) {
+            const int tt = task / 48, o = task - 48 * tt;
+            const int src = (cur * p.T + tt) * 48 + o;
+            const float lam = sm[S.lam + src], R = rsum(sm, S, tt * 48 + o);
+            sm[S.lam + ((cur ^ 1) * p.T + tt) * 48 + o] = first ? lam : fmaf(rho, R, lam);
+            if (solve) sm[S.U + tt * 48 + o] = fmaf(coef, R, lam);
+            else put_xi1(sm, S, cur ^ 1, tt, o, sm[S.xi1 + src]);
+        } else if (task < n_op + n_lp) {
             // P^T (P xi2' - psi_t) = P^T P dxi2 - P^T delta, delta = psi_t - P xi2
-            const int s = task - n_xi, tt = s / NV, k = s - NV * tt;
+            const int s = task - n_op, tt = s / NV, k = s - NV * tt;
             const float *dx2 = sm + S.dx2 + tt * 12;
             float a = 0.f;
 #pragma unroll
@@ -469,7 +387,7 @@ __device__ void phase_xi1(const KParams &p, float *sm, const Smem &S, const Tile
             float *lp = sm + S.lps + tt * 12;
             lp[k] -= L.psi_sign * L.rho_psi * (a - sm[S.ptp + tt * 12 + k]);
         } else {
-            const int s = task - n_xi - n_lp, tt = s >> 2, w = s & 3;
+            const int s = task - n_op - n_lp, tt = s >> 2, w = s & 3;
             const float *gv = sm + S.GX + (tt * 4 + w) * L.qs;
             float v;
             if (w < 3) {
@@ -496,36 +414,25 @@ __device__ void phase_xi1(const KParams &p, float *sm, const Smem &S, const Tile
             }
         }
     }
-}
-
-// Mpsi lam_psi - Mpsi H xi2 for the heading step, row j of trajectory tt
-// (i = tt * NV + j).  Formed after XI1 has updated lam_psi and before the
-// PSI epilogue applies the step: in the PSI phase by warps that have no MMA
-// task when the block has them, else by the whole block in the EVAL phase.
-__device__ __forceinline__ void heading_base(const KParams &p, float *sm, const Smem &S, int i, int cur2)
-{
-    const ConstLayout &L = p.L;
-    const float *cst = sm + S.cst;
-    const int tt = i / NV, j = i - NV * tt;
-    const float *lp = sm + S.lps + tt * 12;
-    const float *x2 = sm + S.xi2 + (cur2 * p.T + tt) * 12;
-    float b0 = 0.f, b1 = 0.f;
+    if (!solve) return;
+    __syncthreads();
+    // one thread per (trajectory, side, row): Minv u - MQ xi1 on the side's
+    // 22 unknowns, both read from their padded blocks (u, xi1 broadcast;
+    // Minv^T and (MQ)^T rows contiguous over the outputs)
+    for (int i = threadIdx.x; i < Tn * 2 * NS; i += blockDim.x) {
+        const int tt = i / (2 * NS), rem = i - 2 * NS * tt, side = rem / NS, row = rem - NS * side;
+        const float *u = sm + S.U + tt * 48 + 24 * side;
+        const float *xi = sm + S.xi1 + (cur * p.T + tt) * 48 + 24 * side;
+        float a0 = 0.f, a1 = 0.f;
 #pragma unroll
-    for (int c = 0; c < NV; ++c) {
-        b0 = fmaf(cst[L.off_mpsi + c * 12 + j], lp[c], b0);
-        b1 = fmaf(cst[L.off_mpsih + c * 12 + j], x2[c], b1);
+        for (int c = 0; c < NS; ++c) {
+            const int cp = rowpad(c);
+            a0 = fmaf(cst[L.off_mt + c * 24 + row], u[cp], a0);
+            a1 = fmaf(cst[L.off_mq + c * 24 + row], xi[cp], a1);
+        }
+        const int rp = rowpad(row);
+        put_xi1(sm, S, cur ^ 1, tt, 24 * side + rp, xi[rp] + (a0 - a1));
     }
-    sm[S.bas + tt * 12 + j] = b0 - b1;
-}
-
-// Warps of the PSI phase: twelve (n-tile, quarter) MMA tasks when the block
-// has twelve warps, and three more forming the heading base when it has
-// fifteen (tile * NV <= 88 rows).
-constexpr int kBaseWarps = 3;
-
-__device__ __forceinline__ bool base_in_psi()
-{
-    return int(blockDim.x >> 5) >= 3 * kPsiParts + kBaseWarps;
 }
 
 // DOT phase on the tensor cores.  One 16-row tile: row = side*8 + trajectory.
@@ -583,214 +490,244 @@ __device__ void phase_dot(const KParams &p, float *sm, const Smem &S, const Tile
     }
 }
 
-// PSI phase on the tensor cores: W^T delta (cols 0..10) and P^T delta (cols
-// 11..21) per trajectory; rows 0..7 = trajectories, rows 8..15 are zero.  The
-// heading step is then applied once per coefficient:
-//   xi2' = xi2 + (Mpsi lam_psi - Mpsi H xi2) + rho W^T delta
-// (the first bracket formed by the base warps of this phase, or in the EVAL
-// phase on a small block), writing xi2' and the increment.
-// Partials over four quarters of the steps (three n-tiles each) are written,
-// the task warps meet at a named barrier, and the first of them sum the
-// partials and apply the step.
-__device__ __forceinline__ void psi_apply(const KParams &p, float *sm, const Smem &S, int g, int c,
-                                          float v, int cur2)
-{
-    if (c < NV) {
-        const float d = fmaf(p.L.rho, v, sm[S.bas + g * 12 + c]);
-        sm[S.xi2 + ((cur2 ^ 1) * p.T + g) * 12 + c] = sm[S.xi2 + (cur2 * p.T + g) * 12 + c] + d;
-        sm[S.dx2 + g * 12 + c] = d;
-    } else if (c < NS) {
-        sm[S.ptp + g * 12 + (c - NV)] = v;
-    }
-}
 
-template <int PR>
+// PSI phase: the heading step of Eq. compute_convex_surrogate in increment
+// form.  With W = P Mpsi^T, W^T delta = Mpsi P^T delta, so the step needs
+// only P^T delta, which every stepper thread has already formed over its two
+// steps in EVAL (its basis rows are in registers).  Warp tt sums trajectory
+// tt's partials in a fixed order (lanes 2k, 2k + 1: the two halves of the
+// steps for coefficient k) and applies
+//   xi2' = xi2 + Mpsi (lam_psi + rho P^T delta) - Mpsi H xi2,
+// writing xi2', the increment and P^T delta (for the lambda_psi update).
 __device__ void phase_psi(const KParams &p, float *sm, const Smem &S, const Tile &tl, int cur2)
 {
     const ConstLayout &L = p.L;
+    const float *cst = sm + S.cst;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 2, tq = lane & 3;
-    const int nks = (L.q + 7) >> 3, per = (nks + kPsiParts - 1) / kPsiParts;
-    // Twelve task warps take one (n-tile, quarter) each; a smaller block has
-    // three, each running its n-tile's four quarters in turn.  Either way every
-    // quarter's partial is formed alone and the four are added in the same
-    // order, so the result does not depend on the block size.
-    const bool split = (blockDim.x >> 5) >= 3 * kPsiParts;
-    const int ntask = split ? 3 * kPsiParts : 3;
-    // warps ntask .. ntask + nbase - 1 form the heading base and hand it to
-    // the epilogue through the named barrier (arrive, no wait)
-    const int nbase = base_in_psi() ? kBaseWarps : 0;
-    const int nbar = 32 * (ntask + nbase);
-    const float *arow = sm + S.PS + frag_row4(g, tl.count) * L.qp;
-    const uint2 z = make_uint2(0u, 0u);
-    if (warp < ntask) {
-        const int nt = warp % 3;
-        const int col = nt * 8 + g;
-        // columns 22, 23 give discarded outputs: read columns of the same parity
-        const uint2 *bcol = col < NV ? reinterpret_cast<const uint2 *>(sm + S.cst + L.off_wcol2) + col * L.qp
-                                     : reinterpret_cast<const uint2 *>(sm + S.cst + L.off_pcol2) +
-                                           (col < NS ? col - NV : col - NV - 8) * L.qp;
-        // one quarter's partial of this warp's n-tile
-        auto quarter = [&](int part) {
-            float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f}, d2[4] = {0.f, 0.f, 0.f, 0.f};
-            const int k0 = part * per, k1 = min(nks, k0 + per);
-#pragma unroll 2
-            for (int ks = k0; ks < k1; ++ks) {
-                const int c0 = ks * 8 + 2 * tq;
-                const float2 av = *reinterpret_cast<const float2 *>(arow + c0);
-                uint2 a[4], b0, b1;
-                split_tf32(av.x, a[0].x, a[0].y);
-                split_tf32(av.y, a[2].x, a[2].y);
-                a[1] = z;
-                a[3] = z;
-                ld_pair2(bcol + c0, b0, b1);
-                mma_pairs<PR>(d0, d1, d2, a, b0, b1);
-            }
-            if (g < tl.count) {
-#pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    const int c = nt * 8 + 2 * tq + e;
-                    if (c < NS) sm[S.psp + (part * kMaxTile + g) * 24 + (c < NV ? c : c + 1)] = d0[e] + d1[e] + d2[e];
-                }
-            }
-        };
-        if (split) {
-            quarter(warp / 3);
-        } else {
-#pragma unroll 1
-            for (int part = 0; part < kPsiParts; ++part) quarter(part);
+    const int np = (L.q + 1) >> 1, nh = (np + 1) >> 1;
+    for (int tt = warp; tt < tl.count; tt += blockDim.x >> 5) {
+        const int k = lane >> 1, half = lane & 1;
+        float s = 0.f;
+        if (k < NV) {
+            const float *pt = sm + S.PTD + (tt * np) * 12 + k;
+            const int j1 = half ? np : nh;
+            for (int j = half ? nh : 0; j < j1; ++j) s += pt[j * 12];
         }
-        // the task and base warps only (barrier 0 is the block's)
-        asm volatile("bar.sync 1, %0;\n" :: "r"(nbar) : "memory");
-        for (int i = threadIdx.x; i < tl.count * NS; i += 32 * ntask) {
-            const int tt = i / NS, c = i - NS * tt, o = c < NV ? c : c + 1;
-            float v = 0.f;
+        const float ptp = s + __shfl_xor_sync(0xffffffffu, s, 1);  // same sum in both lanes
+        const float *lp = sm + S.lps + tt * 12;
+        const float *x2 = sm + S.xi2 + (cur2 * p.T + tt) * 12;
+        float b0 = 0.f, b1 = 0.f;
 #pragma unroll
-            for (int k = 0; k < kPsiParts; ++k) v += sm[S.psp + (k * kMaxTile + tt) * 24 + o];
-            psi_apply(p, sm, S, tt, c, v, cur2);
+        for (int c = 0; c < NV; ++c) {
+            const float pc = __shfl_sync(0xffffffffu, ptp, 2 * c);
+            if (lane < NV) {
+                b0 = fmaf(cst[L.off_mpsi + c * 12 + lane], fmaf(L.rho, pc, lp[c]), b0);
+                b1 = fmaf(cst[L.off_mpsih + c * 12 + lane], x2[c], b1);
+            }
         }
-    } else if (warp < ntask + nbase) {
-        const int i = int(threadIdx.x) - 32 * ntask;
-        if (i < tl.count * NV) heading_base(p, sm, S, i, cur2);
-        __threadfence_block();
-        asm volatile("bar.arrive 1, %0;\n" :: "r"(nbar) : "memory");
+        if (lane < NV) {
+            const float d = b0 - b1;
+            put_xi2(sm, S, cur2 ^ 1, tt, lane, x2[lane] + d);
+            sm[S.dx2 + tt * 12 + lane] = d;
+        }
+        if (half == 0 && k < NV) sm[S.ptp + tt * 12 + k] = ptp;
     }
 }
 
-struct StepRegs {
-    float x, xd, xdd, y, yd, ydd, c, s;
-    float psi_t;     // heading target atan2(s, c), unwrapped
-    float psi_prev;  // heading the unwrap refers to (the previous P xi2)
-    float psi_cur;   // P xi2 of the current coefficients
+// ------------------------------------------------------- paired step work
+//
+// Each stepper thread owns steps t0 = 2 j and t0 + 1 of one trajectory and
+// holds every per-step quantity as a float2 (value at t0, value at t0 + 1).
+// The paired instructions round each component exactly like the scalar
+// instruction would.  When q is odd the last pair has no second step: its
+// basis row is zero and every value it stores for that step is zero.
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 fmul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fadd2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 fsub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+
+// Stores (v.x at t0, v.y at t0 + 1), the second as zero past the horizon.
+__device__ __forceinline__ void st2(float *p, float2 v, bool v1)
+{
+    *reinterpret_cast<float2 *>(p) = make_float2(v.x, v1 ? v.y : 0.f);
+}
+
+// Basis rows of the thread's two steps (Eq. param), kept in registers.
+struct Basis {
+    float2 P[NV], Pd[NV], Pdd[NV];
 };
 
-// EVAL: trajectory values at this thread's step from a padded xi1 block.
-__device__ __forceinline__ void eval_xy(const float *sm, const Smem &S, const ConstLayout &L,
-                                        const float *xi, int t, const float (&Prow)[12],
-                                        StepRegs &r)
+__device__ __forceinline__ void load_basis(const float *sm, const Smem &S, const ConstLayout &L, int t0,
+                                           bool v1, Basis &b)
 {
-    float pd[12], pdd[12], cx[12], cc[12], cy[12], cs[12];
-    load12(pd, sm + S.cst + L.off_prow + (1 * L.q + t) * 12);
-    load12(pdd, sm + S.cst + L.off_prow + (2 * L.q + t) * 12);
-    load12(cx, xi);
-    load12(cc, xi + 12);
-    load12(cy, xi + 24);
-    load12(cs, xi + 36);
-    r.x = dot11(Prow, cx);
-    r.xd = dot11(pd, cx);
-    r.xdd = dot11(pdd, cx);
-    r.c = dot11(Prow, cc);
-    r.y = dot11(Prow, cy);
-    r.yd = dot11(pd, cy);
-    r.ydd = dot11(pdd, cy);
-    r.s = dot11(Prow, cs);
+    const float *r = sm + S.cst + L.off_prow;  // [3][q][12]
+    const int q = L.q, t1 = v1 ? t0 + 1 : t0;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        b.P[k] = f2(r[t0 * 12 + k], v1 ? r[t1 * 12 + k] : 0.f);
+        b.Pd[k] = f2(r[(q + t0) * 12 + k], v1 ? r[(q + t1) * 12 + k] : 0.f);
+        b.Pdd[k] = f2(r[(2 * q + t0) * 12 + k], v1 ? r[(2 * q + t1) * 12 + k] : 0.f);
+    }
 }
 
-// SWEEP: heading at this step, the closed-form xi3/xi4 steps for every
-// (circle, obstacle) pair and the bounds, and the per-step residual vectors
-// (g - F xi1 summed per row block).  g is built from r; F xi1 from ref when
-// PRO (first step of a solve: g from the initial samples, F xi1 from the
-// boundary-consistent reference), else from r as well.  x2 holds the heading
-// coefficients to use.  RES also accumulates the step's squared residual and
-// cost; FIN the smallest squared ellipse distance.
-template <int M, bool LIT, bool RES, bool FIN, bool PRO>
-__device__ __forceinline__ void sweep(float *sm, const Smem &S, const ConstLayout &L,
-                                      const float (&x2)[12], int t, int tt,
-                                      const float (&Prow)[12], StepRegs &r, const StepRegs &ref)
+struct Pair {
+    float2 x, xd, xdd, y, yd, ydd, c, s;
+    float2 psi_t;     // heading target atan2(s, c), unwrapped
+    float2 psi_prev;  // heading the unwrap refers to (the previous P xi2)
+    float2 psi_cur;   // P xi2 of the current coefficients
+};
+
+// Near-obstacle list of the thread's warp (the same in every lane) and the
+// robot centres of the thread's two steps when it was formed.
+struct Near {
+    float2 rx, ry;
+    unsigned list0, list1;  // obstacles 0..31, 32..63
+};
+
+// EVAL: trajectory values at the thread's two steps from trajectory tt's
+// duplicated xi1 in buffer buf.
+__device__ __forceinline__ void eval_pair(const float *sm, const Smem &S, int buf, int tt, const Basis &b,
+                                          Pair &r)
 {
-    const float *cst = sm + S.cst;
-    const float psi = dot11(Prow, x2);
-    float psidd = 0.f;
-    if (RES) {
-        float pdd[12];
-        load12(pdd, cst + L.off_prow + (2 * L.q + t) * 12);
-        psidd = dot11(pdd, x2);
+    const float4 *xd = reinterpret_cast<const float4 *>(sm + S.XD) + (buf * S.T + tt) * 24;
+    float2 x = f2(0.f, 0.f), vx = x, ax = x, c = x, y = x, vy = x, ay = x, s = x;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        const float4 u = xd[2 * k], w = xd[2 * k + 1];  // (cx, cx, cy, cy), (cc, cc, cs, cs)
+        const float2 cx = f2(u.x, u.y), cy = f2(u.z, u.w), cc = f2(w.x, w.y), cs = f2(w.z, w.w);
+        x = ffma2(b.P[k], cx, x);
+        vx = ffma2(b.Pd[k], cx, vx);
+        ax = ffma2(b.Pdd[k], cx, ax);
+        c = ffma2(b.P[k], cc, c);
+        y = ffma2(b.P[k], cy, y);
+        vy = ffma2(b.Pd[k], cy, vy);
+        ay = ffma2(b.Pdd[k], cy, ay);
+        s = ffma2(b.P[k], cs, s);
     }
-    const float pr = psi - kTwoPi * rintf(psi * (1.0f / kTwoPi));
-    const float cp = __cosf(pr), sp = __sinf(pr);
-    const float cf = PRO ? ref.c : r.c, sf = PRO ? ref.s : r.s;   // slack values of F xi1
+    r.x = x;
+    r.xd = vx;
+    r.xdd = ax;
+    r.c = c;
+    r.y = y;
+    r.yd = vy;
+    r.ydd = ay;
+    r.s = s;
+}
+
+// A basis row pair times trajectory tt's duplicated xi2 in buffer buf.
+__device__ __forceinline__ float2 psi_pair(const float *sm, const Smem &S, int buf, int tt, const float2 (&b)[NV])
+{
+    const float4 *x2 = reinterpret_cast<const float4 *>(sm + S.X2D) + (buf * S.T + tt) * 6;
+    float2 s = f2(0.f, 0.f);
+#pragma unroll
+    for (int k2 = 0; k2 < 6; ++k2) {
+        const float4 u = x2[k2];
+        s = ffma2(b[2 * k2], f2(u.x, u.y), s);
+        if (2 * k2 + 1 < NV) s = ffma2(b[2 * k2 + 1], f2(u.z, u.w), s);
+    }
+    return s;
+}
+
+// Printed alpha = atan2(yt, xt) (alpha_mode = 1) for one step: the offset
+// (a d cos, b d sin) - (xt, yt) with d = max(1, rho (a xt^2 + b yt^2) /
+// (a^2 xt^2 + b^2 yt^2)), rho = |(xt, yt)|, scaled back by (1/a, 1/b).
+__device__ __forceinline__ void literal_offset(float xh, float yh, float a, float b, float ia, float ib,
+                                               float &tx, float &ty)
+{
+    const float xt = a * xh, yt = b * yh;
+    const float r2 = fmaf(xt, xt, yt * yt);
+    const float u = a * xt, v = b * yt;
+    const float den = fmaf(u, u, v * v);
+    if (r2 > 0.f) {
+        const float ir = rsqrtf(r2);
+        const float d = fmaxf(1.f, r2 * ir * fmaf(a, xt * xt, b * yt * yt) / den);
+        tx = (d * ir * u - xt) * ia;
+        ty = (d * ir * v - yt) * ib;
+    } else {
+        tx = 1.f;  // alpha = atan2(0, 0) = 0, d = 1: point (a, 0)
+        ty = 0.f;
+    }
+}
+
+// SWEEP: heading at the thread's steps, the closed-form xi3/xi4 steps for
+// every (circle, obstacle) pair and the bounds, and the per-step residual
+// vectors (g - F xi1 summed per row block).  g is built from r; F xi1 from
+// ref when PRO (first step of a solve: g from the initial samples, F xi1 from
+// the boundary-consistent reference), else from r as well.  x2buf selects the
+// heading coefficients to use.  RES also writes the steps' squared residual
+// and cost; FIN the smallest squared ellipse distance.
+template <int M, bool LIT, bool RES, bool FIN, bool PRO>
+__device__ __forceinline__ void sweep_pair(float *sm, const Smem &S, const ConstLayout &L, const Basis &b,
+                                           int x2buf, int tt, int t0, bool v1, Pair &r, const Pair &ref,
+                                           Near &nl)
+{
+    const float2 psi = psi_pair(sm, S, x2buf, tt, b.P);
+    float2 psidd = f2(0.f, 0.f);
+    if (RES) psidd = psi_pair(sm, S, x2buf, tt, b.Pdd);
+    float2 pr;
+    pr.x = psi.x - kTwoPi * rintf(psi.x * (1.0f / kTwoPi));
+    pr.y = psi.y - kTwoPi * rintf(psi.y * (1.0f / kTwoPi));
+    const float2 cp = f2(__cosf(pr.x), __cosf(pr.y)), sp = f2(__sinf(pr.x), __sinf(pr.y));
+    const float2 cf = PRO ? ref.c : r.c, sf = PRO ? ref.s : r.s;  // slack values of F xi1
 
     // velocity and acceleration: project onto the disc of radius v_max / a_max
-    const float v2 = fmaf(r.xd, r.xd, r.yd * r.yd);
-    const float sv = fminf(1.f, L.v_max * rsqrtf(v2));
-    const float a2 = fmaf(r.xdd, r.xdd, r.ydd * r.ydd);
-    const float sa = fminf(1.f, L.a_max * rsqrtf(a2));
+    const float2 v2 = ffma2(r.xd, r.xd, fmul2(r.yd, r.yd));
+    const float2 sv = f2(fminf(1.f, L.v_max * rsqrtf(v2.x)), fminf(1.f, L.v_max * rsqrtf(v2.y)));
+    const float2 a2 = ffma2(r.xdd, r.xdd, fmul2(r.ydd, r.ydd));
+    const float2 sa = f2(fminf(1.f, L.a_max * rsqrtf(a2.x)), fminf(1.f, L.a_max * rsqrtf(a2.y)));
 
-    float X[M], Y[M], ax[M], ay[M], ee[M];
+    float2 X[M], Y[M], ax[M], ay[M], ee[M];
 #pragma unroll
     for (int i = 0; i < M; ++i) {
-        X[i] = fmaf(L.r[i], cp, r.x);
-        Y[i] = fmaf(L.r[i], sp, r.y);
-        ax[i] = 0.f;
-        ay[i] = 0.f;
-        ee[i] = 0.f;
+        const float2 ri = dup2(L.r[i]);
+        X[i] = ffma2(ri, cp, r.x);
+        Y[i] = ffma2(ri, sp, r.y);
+        ax[i] = f2(0.f, 0.f);
+        ay[i] = f2(0.f, 0.f);
+        ee[i] = f2(0.f, 0.f);
     }
-    float dmin = 3.0e38f;
-    const float2 *obs = reinterpret_cast<const float2 *>(cst + L.off_obs);
-    const float4 *obc = reinterpret_cast<const float4 *>(cst + L.off_obc);
-    const float *obt = cst + L.off_obt;
+    float2 dmin = f2(3.0e38f, 3.0e38f);
+    const float *obt = sm + S.cob;
+    const int hq = L.qs >> 1;
+    const float4 *obs2 = reinterpret_cast<const float4 *>(sm + S.cob + (L.off_obs2 - L.off_obt)) + (t0 >> 1);
+    const float4 *obc2 = reinterpret_cast<const float4 *>(sm + S.cob + (L.off_obc2 - L.off_obt));
     const int n = L.n;
-    // One (circle, obstacle) pair of this step.
+    // One (circle, obstacle) pair at both steps.
     auto pair = [&](int j) {
-        const float2 o = obs[j * L.qs + t];   // (x_j(t)/a_j, y_j(t)/b_j)
-        const float4 c = obc[j];              // (1/a_j, 1/b_j, a_j, b_j)
+        const float4 o = obs2[j * hq];                          // -x/a at t0, t1; -y/b at t0, t1
+        const float4 ci = obc2[2 * j], ca = obc2[2 * j + 1];    // (1/a, 1/a, 1/b, 1/b), (a, a, b, b)
+        const float2 ox = f2(o.x, o.y), oy = f2(o.z, o.w);
+        const float2 ia = f2(ci.x, ci.y), ib = f2(ci.z, ci.w), aa = f2(ca.x, ca.y), bb = f2(ca.z, ca.w);
 #pragma unroll
         for (int i = 0; i < M; ++i) {
-            const float xh = fmaf(X[i], c.x, -o.x);   // (x + r_i cos psi - x_j) / a_j
-            const float yh = fmaf(Y[i], c.y, -o.y);
-            const float D = fmaf(xh, xh, fmaf(yh, yh, 1e-30f));
-            float tx, ty;
+            const float2 xh = ffma2(X[i], ia, ox);  // (x + r_i cos psi - x_j) / a_j
+            const float2 yh = ffma2(Y[i], ib, oy);
+            const float2 D = ffma2(xh, xh, ffma2(yh, yh, dup2(1e-30f)));
+            float2 tx, ty;
             if (!LIT) {
-                const float h = fmaxf(rsqrtf(D), 1.f) - 1.f;  // max(1, 1/d) - 1
-                tx = xh * h;
-                ty = yh * h;
+                const float2 h = f2(fmaxf(rsqrtf(D.x), 1.f) - 1.f, fmaxf(rsqrtf(D.y), 1.f) - 1.f);  // max(1, 1/d) - 1
+                tx = fmul2(xh, h);
+                ty = fmul2(yh, h);
             } else {
-                // printed alpha = atan2(yt, xt): the point (a d cos, b d sin) with
-                // d = max(1, rho (a xt^2 + b yt^2) / (a^2 xt^2 + b^2 yt^2)), rho = |(xt, yt)|
-                const float xt = c.z * xh, yt = c.w * yh;
-                const float r2 = fmaf(xt, xt, yt * yt);
-                const float u = c.z * xt, v = c.w * yt;
-                const float den = fmaf(u, u, v * v);
-                if (r2 > 0.f) {
-                    const float ir = rsqrtf(r2);
-                    const float d = fmaxf(1.f, r2 * ir * fmaf(c.z, xt * xt, c.w * yt * yt) / den);
-                    tx = (d * ir * u - xt) * c.x;  // offset, scaled back by 1/a (e = a tx)
-                    ty = (d * ir * v - yt) * c.y;
-                } else {
-                    tx = 1.f;  // alpha = atan2(0, 0) = 0, d = 1: point (a, 0)
-                    ty = 0.f;
-                }
+                literal_offset(xh.x, yh.x, ca.x, ca.z, ci.x, ci.z, tx.x, ty.x);
+                literal_offset(xh.y, yh.y, ca.x, ca.z, ci.x, ci.z, tx.y, ty.y);
             }
             if (RES) {
-                const float ex = c.z * tx, ey = c.w * ty;
-                ax[i] += ex;
-                ay[i] += ey;
-                ee[i] = fmaf(ex, ex, fmaf(ey, ey, ee[i]));
+                const float2 ex = fmul2(aa, tx), ey = fmul2(bb, ty);
+                ax[i] = fadd2(ax[i], ex);
+                ay[i] = fadd2(ay[i], ey);
+                ee[i] = ffma2(ex, ex, ffma2(ey, ey, ee[i]));
             } else {
-                ax[i] = fmaf(c.z, tx, ax[i]);  // e_ij = projected point - (xt, yt)
-                ay[i] = fmaf(c.w, ty, ay[i]);
+                ax[i] = ffma2(aa, tx, ax[i]);  // e_ij = projected point - (xt, yt)
+                ay[i] = ffma2(bb, ty, ay[i]);
             }
-            if (FIN) dmin = fminf(dmin, D);
+            if (FIN) {
+                dmin.x = fminf(dmin.x, D.x);
+                dmin.y = fminf(dmin.y, D.y);
+            }
         }
     };
     if (!LIT && !FIN) {
@@ -803,109 +740,122 @@ __device__ __forceinline__ void sweep(float *sm, const Smem &S, const ConstLayou
         // only when one of its centres has moved farther than the margin;
         // then only the pairs of listed obstacles are visited.
         const unsigned act = __activemask();
-        float2 *ref = reinterpret_cast<float2 *>(sm + S.NR) + tt * L.q + t;
-        unsigned *list = reinterpret_cast<unsigned *>(sm + S.NM) + 2 * (threadIdx.x >> 5);
-        const float2 c0 = *ref;
-        const float mx = r.x - c0.x, my = r.y - c0.y;
-        if (__any_sync(act, fmaf(mx, mx, my * my) > kNearMargin * kNearMargin)) {
-            for (int j0 = 0; j0 < n; j0 += 32) {
-                const int jn = min(32, n - j0);
+        const float2 mx = fsub2(r.x, nl.rx), my = fsub2(r.y, nl.ry);
+        const float2 m2 = ffma2(mx, mx, fmul2(my, my));
+        constexpr float lim = kNearMargin * kNearMargin;
+        if (__any_sync(act, m2.x > lim || (v1 && m2.y > lim))) {
+#pragma unroll
+            for (int blk = 0; blk < 2; ++blk) {
+                const int j0 = 32 * blk, jn = min(32, n - j0);
                 unsigned near = 0u;
                 for (int jj = 0; jj < jn; ++jj) {
                     const int j = j0 + jj;
-                    const float2 o = obs[j * L.qs + t];
-                    const float4 c = obc[j];
-                    const float u0 = fmaf(r.x, c.x, -o.x), v0 = fmaf(r.y, c.y, -o.y);
-                    near |= (fmaf(u0, u0, v0 * v0) < obt[j] ? 1u : 0u) << jj;
+                    const float4 o = obs2[j * hq];
+                    const float4 ci = obc2[2 * j];
+                    const float2 u0 = ffma2(r.x, f2(ci.x, ci.y), f2(o.x, o.y));
+                    const float2 w0 = ffma2(r.y, f2(ci.z, ci.w), f2(o.z, o.w));
+                    const float2 d2 = ffma2(u0, u0, fmul2(w0, w0));
+                    const float th = obt[j];
+                    near |= (d2.x < th || (v1 && d2.y < th) ? 1u : 0u) << jj;
                 }
                 near = __reduce_or_sync(act, near);
-                if ((threadIdx.x & 31) == 0) list[j0 >> 5] = near;
+                if (blk == 0) nl.list0 = near;
+                else nl.list1 = near;
             }
-            *ref = make_float2(r.x, r.y);
-            __syncwarp(act);
+            nl.rx = r.x;
+            nl.ry = r.y;
         }
-        for (int j0 = 0; j0 < n; j0 += 32) {
-            unsigned near = list[j0 >> 5];
+#pragma unroll
+        for (int blk = 0; blk < 2; ++blk) {
+            unsigned near = blk == 0 ? nl.list0 : nl.list1;
             while (near) {
                 const int jj = __ffs(near) - 1;
                 near &= near - 1u;
-                pair(j0 + jj);
+                pair(32 * blk + jj);
             }
         }
     } else {
         for (int j = 0; j < n; ++j) pair(j);
     }
     // Obstacle rows: g_ij - (x + r_i c) = r_i (cos psi - c) + e_ij (+ x - x_ref in PRO)
-    const float fn = float(n);
-    const float dxp = PRO ? r.x - ref.x : 0.f, dyp = PRO ? r.y - ref.y : 0.f;
-    const float dcx = cp - cf, dsy = sp - sf;
-    float r0x = 0.f, r1x = 0.f, r0y = 0.f, r1y = 0.f, rob = 0.f;
+    const float2 fn = dup2(float(n));
+    const float2 dxp = PRO ? fsub2(r.x, ref.x) : f2(0.f, 0.f), dyp = PRO ? fsub2(r.y, ref.y) : f2(0.f, 0.f);
+    const float2 dcx = fsub2(cp, cf), dsy = fsub2(sp, sf);
+    float2 r0x = f2(0.f, 0.f), r1x = r0x, r0y = r0x, r1y = r0x, rob = r0x;
 #pragma unroll
     for (int i = 0; i < M; ++i) {
-        const float bx = fn * fmaf(L.r[i], dcx, dxp) + ax[i];
-        const float by = fn * fmaf(L.r[i], dsy, dyp) + ay[i];
-        r0x += bx;
-        r0y += by;
-        r1x = fmaf(L.r[i], bx, r1x);
-        r1y = fmaf(L.r[i], by, r1y);
+        const float2 ri = dup2(L.r[i]);
+        const float2 bx = ffma2(fn, ffma2(ri, dcx, dxp), ax[i]);
+        const float2 by = ffma2(fn, ffma2(ri, dsy, dyp), ay[i]);
+        r0x = fadd2(r0x, bx);
+        r0y = fadd2(r0y, by);
+        r1x = ffma2(ri, bx, r1x);
+        r1y = ffma2(ri, by, r1y);
         if (RES) {
             // sum_j (r_i (c - cos psi) - e_ij)^2, expanded
-            const float dx = L.r[i] * dcx, dy = L.r[i] * dsy;
-            rob += fn * fmaf(dx, dx, dy * dy) + 2.f * fmaf(dx, ax[i], dy * ay[i]) + ee[i];
+            const float2 dx = fmul2(ri, dcx), dy = fmul2(ri, dsy);
+            const float2 sq = fmul2(fn, ffma2(dx, dx, fmul2(dy, dy)));
+            const float2 cr = fmul2(dup2(2.f), ffma2(dx, ax[i], fmul2(dy, ay[i])));
+            rob = fadd2(rob, fadd2(fadd2(sq, cr), ee[i]));
         }
     }
-    const int qs = L.qs;
-    float *Gx = sm + S.G2 + tt * S.RS + t;   // side x: row tt
-    float *Gy = Gx + S.T * S.RS;             // side y: row T + tt
-    const float svm = sv - 1.f, sam = sa - 1.f;
+    const int qs = L.qs, qp = L.qp;
+    float *Gx = sm + S.G2 + tt * S.RS + t0;   // side x: row tt
+    float *Gy = Gx + S.T * S.RS;              // side y: row T + tt
+    const float2 svm = f2(sv.x - 1.f, sv.y - 1.f), sam = f2(sa.x - 1.f, sa.y - 1.f);
     // v and a rows: projected value - F xi1 value
-    const int qp = L.qp;
-    Gx[0] = PRO ? fmaf(r.xd, svm, r.xd - ref.xd) : r.xd * svm;
-    Gx[qp] = PRO ? fmaf(r.xdd, sam, r.xdd - ref.xdd) : r.xdd * sam;
-    Gx[2 * qp] = r0x;
-    Gx[3 * qp] = r1x + dcx;
-    Gy[0] = PRO ? fmaf(r.yd, svm, r.yd - ref.yd) : r.yd * svm;
-    Gy[qp] = PRO ? fmaf(r.ydd, sam, r.ydd - ref.ydd) : r.ydd * sam;
-    Gy[2 * qp] = r0y;
-    Gy[3 * qp] = r1y + dsy;
-    float *GX = sm + S.GX + tt * 4 * qs + t;
+    st2(Gx, PRO ? ffma2(r.xd, svm, fsub2(r.xd, ref.xd)) : fmul2(r.xd, svm), v1);
+    st2(Gx + qp, PRO ? ffma2(r.xdd, sam, fsub2(r.xdd, ref.xdd)) : fmul2(r.xdd, sam), v1);
+    st2(Gx + 2 * qp, r0x, v1);
+    st2(Gx + 3 * qp, fadd2(r1x, dcx), v1);
+    st2(Gy, PRO ? ffma2(r.yd, svm, fsub2(r.yd, ref.yd)) : fmul2(r.yd, svm), v1);
+    st2(Gy + qp, PRO ? ffma2(r.ydd, sam, fsub2(r.ydd, ref.ydd)) : fmul2(r.ydd, sam), v1);
+    st2(Gy + 2 * qp, r0y, v1);
+    st2(Gy + 3 * qp, fadd2(r1y, dsy), v1);
+    float *GX = sm + S.GX + tt * 4 * qs + t0;
     if (RES) {
-        GX[0] = v2 * svm * svm + a2 * sam * sam + rob + dcx * dcx + dsy * dsy;
-        const float dp = psi - r.psi_t;
-        GX[qs] = dp * dp;
-        GX[2 * qs] = fmaf(r.xdd, r.xdd, fmaf(r.ydd, r.ydd, psidd * psidd));
+        const float2 bnd = ffma2(fmul2(v2, svm), svm, fmul2(fmul2(a2, sam), sam));
+        const float2 sl = ffma2(dcx, dcx, fmul2(dsy, dsy));
+        st2(GX, fadd2(fadd2(bnd, rob), sl), v1);
+        const float2 dp = fsub2(psi, r.psi_t);
+        st2(GX + qs, fmul2(dp, dp), v1);
+        st2(GX + 2 * qs, ffma2(r.xdd, r.xdd, ffma2(r.ydd, r.ydd, fmul2(psidd, psidd))), v1);
     }
-    if (FIN) GX[3 * qs] = dmin;
+    if (FIN) st2(GX + 3 * qs, dmin, v1);
     r.psi_prev = psi;
     r.psi_cur = psi;
 }
 
 template <int M, bool LIT>
-__device__ void sweep_dispatch(float *sm, const Smem &S, const ConstLayout &L, const float (&x2)[12],
-                               int tt, int t, const float (&Prow)[12], StepRegs &r, bool res,
-                               bool fin)
+__device__ void sweep_dispatch(float *sm, const Smem &S, const ConstLayout &L, const Basis &b, int x2buf,
+                               int tt, int t0, bool v1, Pair &r, Near &nl, bool res, bool fin)
 {
-    if (fin) sweep<M, LIT, true, true, false>(sm, S, L, x2, t, tt, Prow, r, r);
-    else if (res) sweep<M, LIT, true, false, false>(sm, S, L, x2, t, tt, Prow, r, r);
-    else sweep<M, LIT, false, false, false>(sm, S, L, x2, t, tt, Prow, r, r);
+    if (fin) sweep_pair<M, LIT, true, true, false>(sm, S, L, b, x2buf, tt, t0, v1, r, r, nl);
+    else if (res) sweep_pair<M, LIT, true, false, false>(sm, S, L, b, x2buf, tt, t0, v1, r, r, nl);
+    else sweep_pair<M, LIT, false, false, false>(sm, S, L, b, x2buf, tt, t0, v1, r, r, nl);
 }
 
-// Stage a problem's constant block into shared memory with one bulk async
-// copy and zero the rest of the dynamic area (the padding of the per-step
-// arrays past q, and the unused rows of the MMA tiles, must read as zero).
-// The wait on the mbarrier is bounded, and the block agrees on its outcome
-// before anyone leaves, so no thread is left waiting at a barrier.
+// Stage a problem's constant block into shared memory with two bulk async
+// copies (the shape sections, then the near thresholds and the paired
+// obstacle sections) and zero the rest of the dynamic area (the padding of
+// the per-step arrays past q, and the unused rows of the MMA tiles, must read
+// as zero).  The wait on the mbarrier is bounded, and the block agrees on its
+// outcome before anyone leaves, so no thread is left waiting at a barrier.
 __device__ bool stage_constants(const KParams &p, float *sm, const Smem &S, uint64_t *bar,
                                 uint32_t parity)
 {
     if (threadIdx.x == 0) {
-        const uint32_t bytes = uint32_t(p.L.total - p.L.off_fused) * 4u;
+        const ConstLayout &L = p.L;
+        const uint32_t b0 = uint32_t(L.off_obs - L.off_fused) * 4u, b1 = uint32_t(L.total - L.off_obt) * 4u;
         // order the block's earlier generic-proxy accesses of this area
-        // before the asynchronous copy overwrites it
+        // before the asynchronous copies overwrite it
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n"
-                     :: "r"(smem_u32(bar)), "r"(bytes) : "memory");
-        if (!p.L.diag_stall) bulk_load(sm + S.cst + p.L.off_fused, p.cblob + p.L.off_fused, bytes, bar);
+                     :: "r"(smem_u32(bar)), "r"(b0 + b1) : "memory");
+        if (!L.diag_stall) {
+            bulk_load(sm + S.cst + L.off_fused, p.cblob + L.off_fused, b0, bar);
+            if (b1) bulk_load(sm + S.cob, p.cblob + L.off_obt, b1, bar);
+        }
     }
     for (int i = S.xi1 + threadIdx.x; i < S.total; i += blockDim.x) sm[i] = 0.f;
     int ok = 0;
@@ -937,52 +887,49 @@ __device__ void run_tile(const KParams &p, float *sm, const Smem &S, const Tile 
     for (int i = threadIdx.x; i < Tn * STATE; i += blockDim.x) {
         const int tt = i / STATE, e = i - STATE * tt;
         const float v = p.state[(size_t)tl.first * STATE + i];
-        if (e < 44) sm[S.xi1 + (p.T + tt) * 48 + (e / NV) * 12 + e % NV] = v;
-        else if (e < 55) sm[S.xi2 + (p.T + tt) * 12 + (e - 44)] = v;
+        if (e < 44) put_xi1(sm, S, 1, tt, (e / NV) * 12 + e % NV, v);
+        else if (e < 55) put_xi2(sm, S, 1, tt, e - 44, v);
         else if (e < 99) sm[S.lam + tt * 48 + ((e - 55) / NV) * 12 + (e - 55) % NV] = v;
         else sm[S.lps + tt * 12 + (e - 99)] = v;
     }
     for (int i = threadIdx.x; i < kRParts * p.T * 48; i += blockDim.x) sm[S.rb + i] = 0.f;
-    // no near lists yet: a reference far away makes every warp form its list
-    for (int i = threadIdx.x; i < 2 * p.T * L.q; i += blockDim.x) sm[S.NR + i] = 3.0e18f;
     __syncthreads();
     // Reference xi1, xi2 into buffer 0: boundary control points from the
     // boundary conditions on every block that has boundary rows, the rest as given.
     for (int i = threadIdx.x; i < Tn * 55; i += blockDim.x) {
         const int tt = i / 55, e = i - 55 * tt, blk = e / NV, k = e - NV * blk;
         const bool has_bc = (blk == 0 || blk == 2 || blk == 4 || L.cs_boundary);
-        float *src = blk < 4 ? sm + S.xi1 + (p.T + tt) * 48 + blk * 12 : sm + S.xi2 + (p.T + tt) * 12;
-        float *dst = blk < 4 ? sm + S.xi1 + tt * 48 + blk * 12 : sm + S.xi2 + tt * 12;
-        float v = src[k];
+        float v = blk < 4 ? sm[S.xi1 + (p.T + tt) * 48 + blk * 12 + k] : sm[S.xi2 + (p.T + tt) * 12 + k];
         if (has_bc && k <= 2) v = sm[S.cst + L.off_ends + blk * 8 + k];
         if (has_bc && k >= 8) v = sm[S.cst + L.off_ends + blk * 8 + (k - 5)];
-        dst[k] = v;
+        if (blk < 4) put_xi1(sm, S, 0, tt, blk * 12 + k, v);
+        else put_xi2(sm, S, 0, tt, k, v);
     }
     __syncthreads();
 
-    const int tid = threadIdx.x;
-    const bool stepper = tid < Tn * L.q;
-    const int tt = stepper ? tid / L.q : 0;
-    const int t = stepper ? tid - tt * L.q : 0;
-    // The thread's basis row P[t, :] is reloaded where it is used, so it does
-    // not occupy registers through the tensor-core phases.
-    const float *prow = sm + S.cst + L.off_prow + t * 12;
-    StepRegs r;
-    r.psi_t = 0.f;
+    // Stepper threads: trajectory tt, steps t0 and t0 + 1.
+    const int tpt = pair_threads(L.q), np = (L.q + 1) >> 1;
+    const int tt = int(threadIdx.x) / tpt, jp = int(threadIdx.x) - tt * tpt;
+    const bool stepper = tt < Tn && jp < np;
+    const int t0 = 2 * jp;
+    const bool v1 = stepper && t0 + 1 < L.q;
+    Basis b;
+    Pair r;
+    Near nl;
     int cur = 0, cur2 = 0;
 
     // Step 1 of Sec. III-D: xi3, xi4 and g from the initial samples, the
     // residual against the reference.
     if (stepper) {
-        StepRegs ref;
-        float x2[12], Prow[12];
-        load12(Prow, prow);
-        eval_xy(sm, S, L, sm + S.xi1 + (p.T + tt) * 48, t, Prow, r);
-        eval_xy(sm, S, L, sm + S.xi1 + tt * 48, t, Prow, ref);
-        load12(x2, sm + S.xi2 + (p.T + tt) * 12);
-        sweep<M, LIT, false, false, true>(sm, S, L, x2, t, tt, Prow, r, ref);
-        load12(x2, sm + S.xi2 + tt * 12);
-        r.psi_cur = dot11(Prow, x2);  // heading of the reference c_psi
+        load_basis(sm, S, L, t0, v1, b);
+        nl.rx = nl.ry = f2(3.0e18f, 3.0e18f);  // no near list yet: every warp forms one
+        nl.list0 = nl.list1 = 0u;
+        Pair ref;
+        eval_pair(sm, S, 1, tt, b, r);
+        eval_pair(sm, S, 0, tt, b, ref);
+        r.psi_t = f2(0.f, 0.f);
+        sweep_pair<M, LIT, false, false, true>(sm, S, L, b, 1, tt, t0, v1, r, ref, nl);
+        r.psi_cur = psi_pair(sm, S, 0, tt, b.P);  // heading of the reference c_psi
     }
     __syncthreads();
     phase_dot<PR>(p, sm, S, tl);
@@ -995,26 +942,30 @@ __device__ void run_tile(const KParams &p, float *sm, const Smem &S, const Tile 
         cur ^= 1;
         __syncthreads();
         if (stepper) {
-            float Prow[12];
-            load12(Prow, prow);
-            eval_xy(sm, S, L, sm + S.xi1 + (cur * p.T + tt) * 48, t, Prow, r);
+            eval_pair(sm, S, cur, tt, b, r);
             // psi_t = psi + wrap(atan2(s, c) - psi), psi the previous heading;
             // the heading step works on delta = psi_t - P xi2
-            r.psi_t = r.psi_prev + wrap_pi(atan2_heading(r.s, r.c) - r.psi_prev);
-            sm[S.PS + tt * L.qp + t] = r.psi_t - r.psi_cur;
+            r.psi_t.x = r.psi_prev.x + wrap_pi(atan2_heading(r.s.x, r.c.x) - r.psi_prev.x);
+            r.psi_t.y = r.psi_prev.y + wrap_pi(atan2_heading(r.s.y, r.c.y) - r.psi_prev.y);
+            const float2 dl = fsub2(r.psi_t, r.psi_cur);
+            const float2 dd = f2(dl.x, v1 ? dl.y : 0.f);
+            // this pair's share of P^T delta (the second step's basis row is zero past q)
+            float pk[12];
+#pragma unroll
+            for (int k = 0; k < NV; ++k) {
+                const float2 m = fmul2(b.P[k], dd);
+                pk[k] = m.x + m.y;
+            }
+            pk[11] = 0.f;
+            float4 *dst = reinterpret_cast<float4 *>(sm + S.PTD + (tt * np + jp) * 12);
+            dst[0] = make_float4(pk[0], pk[1], pk[2], pk[3]);
+            dst[1] = make_float4(pk[4], pk[5], pk[6], pk[7]);
+            dst[2] = make_float4(pk[8], pk[9], pk[10], pk[11]);
         }
-        if (!base_in_psi())
-            for (int i = threadIdx.x; i < Tn * NV; i += blockDim.x) heading_base(p, sm, S, i, cur2);
         __syncthreads();
-        phase_psi<PR>(p, sm, S, tl, cur2);
+        phase_psi(p, sm, S, tl, cur2);
         __syncthreads();
-        if (stepper) {
-            float x2[12];
-            load12(x2, sm + S.xi2 + ((cur2 ^ 1) * p.T + tt) * 12);  // xi2' from the PSI phase
-            float Prow[12];
-            load12(Prow, prow);
-            sweep_dispatch<M, LIT>(sm, S, L, x2, tt, t, Prow, r, res, k == p.iters - 1);
-        }
+        if (stepper) sweep_dispatch<M, LIT>(sm, S, L, b, cur2 ^ 1, tt, t0, v1, r, nl, res, k == p.iters - 1);
         cur2 ^= 1;
         __syncthreads();
         phase_dot<PR>(p, sm, S, tl);
@@ -1114,7 +1065,7 @@ size_t fused_smem_bytes(const ConstLayout &L, int tile)
 
 int fused_max_tile(const ConstLayout &L)
 {
-    int tmax = kMaxThreads / (L.q > 88 ? L.q : 88);
+    int tmax = kMaxThreads / pair_threads(L.q);
     if (tmax > kMaxTile) tmax = kMaxTile;
     while (tmax > 1 && fused_smem_bytes(L, tmax) > 227 * 1024) --tmax;
     return tmax < 1 ? 1 : tmax;
@@ -1124,7 +1075,7 @@ int fused_max_threads() { return kMaxThreads; }
 
 int group_tile(const ConstLayout &L, int threads)
 {
-    int t = threads / (L.q > 88 ? L.q : 88);
+    int t = threads / pair_threads(L.q);
     if (t > kMaxTile) t = kMaxTile;
     while (t >= 1 && fused_smem_bytes(L, t) > kGroupSmemMax) --t;
     return t < 1 ? 0 : t;
@@ -1250,11 +1201,12 @@ int launch_fused(const SolveArgs &a, void *stream, int *launches)
     if (sms < 1) return -2;
     const ConstLayout &L = a.L;
     int T = a.tile > 0 ? a.tile : fused_auto_tile(L, a.B, sms);
-    const int tq = T * (L.q > 88 ? L.q : 88);
+    const int tq = T * pair_threads(L.q);
     if (tq > kMaxThreads || T < 1 || T > kMaxTile) return -1;
     const size_t smem = fused_smem_bytes(L, T);
     if (smem > 227 * 1024) return -1;
-    const int threads = (tq + 31) & ~31;
+    // twelve warps whatever the tile: the tensor-core phases run all their tasks at once
+    const int threads = kMaxThreads;
     const int ntiles = (a.B + T - 1) / T;
     KParams p;
     p.cblob = a.cblob;

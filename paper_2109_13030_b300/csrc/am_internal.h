@@ -90,14 +90,12 @@ struct ConstLayout {
     int qp;                   // stride (in pairs) of the split per-step columns
     int off_pcol;             // [3][NV][qs]  P, Pd, Pdd columns (FP32, plain loop)
     int off_wcol;             // [NV][qs]     W = P Mpsi^T, columns (FP32, plain loop)
-    int off_fused;            // start of the part the fused kernel stages:
+    int off_fused;            // start of the part the fused kernel stages, in two regions:
+                              // [off_fused, off_obs) and [off_obt, total)
     int off_prow;             // [3][q][12]   P, Pd, Pdd rows (padded to 12)
     int off_pcol2;            // [3][NV][qp][2] P, Pd, Pdd columns as TF32 (hi, lo) pairs
-    int off_wcol2;            // [NV][qp][2]  W columns as TF32 (hi, lo) pairs
     int off_mt;               // [NS][24]     Minv^T
     int off_mq;               // [NS][24]     (Minv blockdiag(H, H))^T
-    int off_xib2;             // [24][56][2]  [Minv | -Minv Q] on padded indices, row = output,
-                              //              as TF32 (hi, lo) pairs
     int off_ends;             // [5][8]       boundary control points per block (xi1 blocks, c_psi)
     int off_kb;               // [2][24]      kb (x side, y side)
     int off_mpsi;             // [NV][12]     Mpsi^T
@@ -107,6 +105,9 @@ struct ConstLayout {
     int off_obs;              // [n][qs][2]   (x_j(t)/a_j, y_j(t)/b_j) pairs
     int off_obc;              // [n][4]       1/a_j, 1/b_j, a_j, b_j (inflated)
     int off_obt;              // [n]          near threshold (1 + (r_max + margin) max(1/a_j, 1/b_j))^2
+    int off_obs2;             // [n][qs/2][4] per pair of steps (t, t + 1), t even: -x_j/a_j at t, t + 1,
+                              //              then -y_j/b_j at t, t + 1 (the fused kernel's paired form)
+    int off_obc2;             // [n][8]       1/a_j, 1/a_j, 1/b_j, 1/b_j, a_j, a_j, b_j, b_j
     int total;                // floats, multiple of 4
     float rho, rho_psi, v_max, a_max;
     float r[MAXM];

@@ -389,10 +389,8 @@ ConstLayout make_layout(int q, int m, int n)
     L.off_fused = o;
     L.off_prow = o; o = align4(o + 3 * q * 12);
     L.off_pcol2 = o; o = align4(o + 3 * NV * 2 * qp);
-    L.off_wcol2 = o; o = align4(o + NV * 2 * qp);
     L.off_mt = o; o = align4(o + NS * 24);
     L.off_mq = o; o = align4(o + NS * 24);
-    L.off_xib2 = o; o = align4(o + 24 * 2 * 56);
     L.off_ends = o; o = align4(o + 5 * 8);
     L.off_kb = o; o = align4(o + 2 * 24);
     L.off_mpsi = o; o = align4(o + NV * 12);
@@ -402,6 +400,8 @@ ConstLayout make_layout(int q, int m, int n)
     L.off_obs = o; o = align4(o + n * 2 * qs);
     L.off_obc = o; o = align4(o + n * 4);
     L.off_obt = o; o = align4(o + n);
+    L.off_obs2 = o; o = align4(o + n * 2 * qs);
+    L.off_obc2 = o; o = align4(o + n * 8);
     L.total = o;
     return L;
 }
@@ -451,22 +451,11 @@ void fill_constants(const HostSetup &S, const ProblemParams &pp, const ConstLayo
         for (int k = 0; k < NV; ++k) {
             const float w = float(S.W[t * NV + k]);
             blob[L.off_wcol + k * qs + t] = w;
-            put_split(blob, L.off_wcol2 + 2 * (k * L.qp + t), w);
         }
     for (int a = 0; a < NS; ++a)
         for (int b = 0; b < NS; ++b) {
             blob[L.off_mt + b * 24 + a] = float(S.Minv[a][b]);
             blob[L.off_mq + b * 24 + a] = float(S.MQ[a][b]);
-        }
-    // Tensor-core operand of the position step: row np (padded output index,
-    // 11 and 23 are pads), column kp < 24 multiplies lam + coef R, kp >= 24
-    // multiplies xi1 (both on padded indices).
-    auto unpad = [](int i) { return i < NV ? i : (i == NV || i == 2 * NV + 1) ? -1 : i - 1; };
-    for (int np = 0; np < 24; ++np)
-        for (int kp = 0; kp < 48; ++kp) {
-            const int a = unpad(np), b = unpad(kp % 24);
-            if (a < 0 || b < 0) continue;
-            put_split(blob, L.off_xib2 + 2 * (np * 56 + kp), float(kp < 24 ? S.Minv[a][b] : -S.MQ[a][b]));
         }
     for (int blk = 0; blk < 5; ++blk)
         for (int e = 0; e < 6; ++e) blob[L.off_ends + blk * 8 + e] = float(S.ends[blk][e]);

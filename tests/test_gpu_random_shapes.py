@@ -64,7 +64,7 @@ def test_random_group_mix(seed):
         pbs.append(W.make_shape(int(rng.integers(0, 10 ** 6)), B=int(rng.choice([1, 5, 64, 300])), q=q,
                                 n=int(rng.integers(1, 33)), m=int(rng.integers(1, 5))))
     probs = [T.Problem(pb).init_state(pb["init"].astype(np.float32)) for pb in pbs]
-    G = T.Group(probs, threads=int(rng.choice([0, 256, 512, 768])))
+    G = T.Group(probs, threads=int(rng.choice([0, 128, 256, 384])))
     G.solve(10)
     for pb, P in zip(pbs, probs):
         check(pb, P.state(), rng, k=4)
