@@ -70,6 +70,53 @@ def measured_traffic():
     return int(t.group(1).replace(",", "")) + int(t.group(2).replace(",", ""))
 
 
+def sig(x, n: int = 4):
+    """x rounded to n significant digits (None and non-numbers unchanged)."""
+    if isinstance(x, bool) or not isinstance(x, (int, float)) or x == 0 or not np.isfinite(x):
+        return x
+    return float(f"{x:.{n}g}")
+
+
+def compact(d):
+    """Every float in a nested dict/list rounded to 4 significant digits."""
+    if isinstance(d, dict):
+        return {k: compact(v) for k, v in d.items()}
+    if isinstance(d, list):
+        return [compact(v) for v in d]
+    return sig(d) if isinstance(d, float) else d
+
+
+def summary_sections(extra: dict) -> dict:
+    """Short forms of the single-GPU sections, so that the whole JSON line stays
+    within a few kilobytes: throughput and times, p50/p99 per serving mode."""
+    out = {}
+    if "uneven" in extra:
+        u = extra["uneven"]
+        out["uneven"] = {"value": u["value"], "ms": u["ms_per_solve"], "precision": u.get("precision", "fp32"),
+                         "threads": u["threads"], "launches": u["launches_per_solve"],
+                         "per_problem_value": u["one_launch_per_problem"]["value"],
+                         "per_problem_ms": u["one_launch_per_problem"]["ms_per_solve"]}
+        if "bf16" in u:
+            out["uneven"]["bf16_value"] = u["bf16"]["value"]
+            out["uneven"]["bf16_ms"] = u["bf16"]["ms_per_solve"]
+    if "precision" in extra:
+        pr = extra["precision"]
+        out["precision_b4096"] = {k: {"value": v["value"], **({"dev10": v["coef_dev_vs_fp32_after_10"]["max"]}
+                                                              if "coef_dev_vs_fp32_after_10" in v else {})}
+                                  for k, v in pr.items() if isinstance(v, dict)}
+    if "serving" in extra:
+        sv = extra["serving"]
+        pq = lambda r: [r["p50_ms"], r["p99_ms"]]
+        out["serving_p50_p99_ms"] = {
+            "400/s": {"batched": pq(sv["batched"]), "seq_fused": pq(sv["sequential_fused"]),
+                      "seq_plain": pq(sv["sequential_plain_fp32_loop"])},
+            "2500/s": {"batched": pq(sv["high_load"]["batched"]),
+                       "seq_fused": pq(sv["high_load"]["sequential_fused"])}}
+        out["serving_mean_batch"] = {"400/s": sv["batched"]["mean_batch"],
+                                     "2500/s": sv["high_load"]["batched"]["mean_batch"]}
+    return out
+
+
 def peak_fp32_tflops(sms: int = 148, clock_mhz: float = 2032.0) -> float:
     """FP32 FMA peak: SMs x 128 lanes x 2 flops x clock."""
     return sms * 128 * 2 * clock_mhz * 1e6 / 1e12
@@ -209,7 +256,32 @@ def bench_uneven(TJ, W, torch, dev, flush, steps: int, iters: int = 100) -> dict
     G.close()
     for P in probs:
         P.close()
+    # the same mix with the contraction R in one BF16 tensor-core product
+    # (the uneven-batching configuration's precision form)
+    probs = [TJ.Problem(pb, precision=TJ.AM_BF16) for pb in pbs]
+    reset()
+    G = TJ.Group(probs)
+    G.autotune(iters, stream=side)
+    for _ in range(2):
+        reset()
+        G.solve(iters, stream=side)
+    torch.cuda.synchronize()
+    bms = []
+    for i in range(steps):
+        flush.fill_(float(i))
+        reset()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(side)
+        G.solve(iters, stream=side)
+        e1.record(side)
+        torch.cuda.synchronize()
+        bms.append(e0.elapsed_time(e1))
+    b_ms = statistics.mean(bms)
+    G.close()
+    for P in probs:
+        P.close()
     return {"metric": "trajectory-AM-iterations/sec over 64 mixed problems", "value": total * iters / (g_ms / 1e3),
+            "bf16": {"value": total * iters / (b_ms / 1e3), "unit": UNIT, "ms_per_solve": b_ms},
             "unit": UNIT, "ms_per_solve": g_ms, "problems": len(pbs), "trajectories": total,
             "iterations": iters, "work_items": items, "threads": threads, "launches_per_solve": launches,
             "achieved_tflops": flops / (g_ms / 1e3) / 1e12,
@@ -428,7 +500,8 @@ def main():
     ap.add_argument("--uneven-steps", type=int, default=3)
     ap.add_argument("--precision-steps", type=int, default=3)
     ap.add_argument("--jsonl", default=None, help="also append the JSON line to this file")
-    ap.add_argument("--mpc-episodes", type=int, default=20, help="closed-loop episodes per crowd benchmark (0: skip)")
+    ap.add_argument("--mpc-episodes", type=int, default=0,
+                    help="closed-loop episodes per crowd benchmark (0: skip; the study takes minutes)")
     ap.add_argument("--cem-episodes", type=int, default=5, help="of those, episodes per benchmark for the CEM rows")
     ap.add_argument("--mpc-seconds", type=float, default=20.0, help="closed-loop episode length (s)")
     ap.add_argument("--profile-plain", type=int, default=0, metavar="B",
@@ -436,6 +509,9 @@ def main():
                          "plain loop and exit (no JSON line)")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-plain-seconds", type=float, default=2.0)
+    ap.add_argument("--detail", action="store_true",
+                    help="add the full single-GPU sections (workload strings, every serving statistic) "
+                         "under 'detail'; by default the line carries their short forms only")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -597,33 +673,33 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "paper-shaped: B=1000 per GPU, q=100 steps over 10 s, degree-10 Bernstein, "
-                                   "m=3 circles (r=-0.4,0,0.4), 10 moving ellipses, 100 AM iterations, "
-                                   "rho=1, then best-trajectory selection",
-                       "parallelism": (f"batch of {B * world} sharded x{world}: no exchange during the "
-                                       "iterations, one best-key all-gather + coefficient broadcast per step"
+            "config": {"workload": "paper-shaped: B=1000/GPU, q=100 over 10 s, degree-10 Bernstein, m=3 circles, "
+                                   "10 moving ellipses, 100 AM iterations, rho=1, then the best selection",
+                       "parallelism": (f"batch of {B * world} sharded x{world}; best-key all-gather per step"
                                        if world > 1 else "single GPU"),
                        "l2": "512 MiB buffer rewritten between timed steps",
-                       "kernel": "fused persistent (1 launch per solve)"},
+                       "kernel": "fused persistent, 1 launch per solve"},
             "gpu_launches": launches_per_step * args.steps,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": measured_traffic(),
-                         "kernel": "am_fused_kernel",
-                         "flops_per_launch": flops,
-                         "peak_basis": "derived FP32 FMA peak: SMs x 128 lanes x 2 x 2032 MHz",
-                         "kernel_ms": kern_avg},
+                         "kernel": "am_fused_kernel", "kernel_ms": kern_avg, "flops_per_launch": flops,
+                         "peak_basis": "derived FP32 peak: SMs x 128 lanes x 2 x 2032 MHz"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": B * 33 * 4,
                     "d2h_bytes_per_step": B * 4 * 4 + 36 * 4},
             "clocks": clocks,
-            "comparators": {"plain_fp32_loop": {"value": B * ITERS / (statistics.mean(plain_ms) / 1e3),
-                                                "unit": UNIT, "ms_per_solve": statistics.mean(plain_ms),
-                                                "launches_per_solve": plain_launches,
-                                                "final_residual_median": plain_res}},
-            "final_residual_median": fused_res,
         }
-        line.update(extra)
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(pb, B, ITERS)
+        line["plain_fp32_loop"] = {"value": B * ITERS / (statistics.mean(plain_ms) / 1e3),
+                                   "ms": statistics.mean(plain_ms), "launches": plain_launches,
+                                   "res_median": plain_res}
+        line["fused_res_median"] = fused_res
+        line.update(summary_sections(extra))
+        if "closed_loop" in extra:
+            line["closed_loop"] = extra.pop("closed_loop")
+        if args.detail:
+            line["detail"] = extra
+        line = compact(line)
         print(json.dumps(line), flush=True)
         if args.jsonl:
             with open(args.jsonl, "a") as f:

@@ -55,12 +55,13 @@ extern "C" {
 #define AM_HOST 0
 #define AM_DEVICE 1
 
-/* Precision of the fused kernel's contractions over the time grid (R =
- * F^T (g - F xi1), W^T delta, P^T delta): AM_FP32 takes three TF32
- * tensor-core products per product (hi*hi + hi*lo + lo*hi, FP32 accuracy);
- * AM_TF32 and AM_BF16 take one product of operands rounded to TF32 or BF16
- * (the reduced-precision form; the position step keeps three products).
- * The plain kernel, groups and the allocation-free entry run FP32 only. */
+/* Precision of the fused kernel's tensor-core contraction over the time grid
+ * (R = F^T (g - F xi1)): AM_FP32 takes three TF32 products per product
+ * (hi*hi + hi*lo + lo*hi, FP32 accuracy); AM_TF32 and AM_BF16 take one
+ * product of operands rounded to TF32 or BF16 (the reduced-precision form).
+ * The position and heading steps are FP32 in every form.  Groups run each
+ * problem in its own precision; the plain kernel and the allocation-free
+ * entry run FP32 only. */
 #define AM_FP32 0
 #define AM_TF32 1
 #define AM_BF16 2

@@ -690,12 +690,14 @@ int upload_work(am_group *g, cudaStream_t st)
 {
     const std::vector<int> act = active_list(g);
     const size_t np = g->h_probs.size();
-    const size_t o_probs = 64, o_items = o_probs + ((sizeof(FusedProblem) * np + 15) & ~size_t(15));
+    // header: item count per variant, then list offset per variant
+    const size_t o_probs = (2 * sizeof(int) * kGroupVariants + 63) & ~size_t(63);
+    const size_t o_items = o_probs + ((sizeof(FusedProblem) * np + 15) & ~size_t(15));
     const size_t o_list = o_items + sizeof(int) * g->h_items.size();
     const size_t bytes = o_list + sizeof(int) * act.size();
     std::vector<char> buf(bytes, 0);
     std::memcpy(buf.data(), g->count, sizeof(g->count));
-    std::memcpy(buf.data() + 32, g->offset, sizeof(g->offset));
+    std::memcpy(buf.data() + sizeof(int) * kGroupVariants, g->offset, sizeof(g->offset));
     std::memcpy(buf.data() + o_probs, g->h_probs.data(), sizeof(FusedProblem) * np);
     std::memcpy(buf.data() + o_items, g->h_items.data(), sizeof(int) * g->h_items.size());
     std::memcpy(buf.data() + o_list, act.data(), sizeof(int) * act.size());
@@ -1096,7 +1098,6 @@ int am_group_create(am_problem *const *problems, int count, am_group **out)
     *out = nullptr;
     for (int i = 0; i < count; ++i) {
         if (!problems[i]) return fail(AM_ERR_ARG, "null problem %d", i);
-        if (problems[i]->pp.precision != AM_FP32) return fail(AM_ERR_ARG, "problem %d: groups run in FP32", i);
     }
     am_group *g = new (std::nothrow) am_group;
     if (!g) return fail(AM_ERR_ARG, "out of host memory");

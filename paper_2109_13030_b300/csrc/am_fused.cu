@@ -1004,23 +1004,25 @@ __global__ void __launch_bounds__(kMaxThreads, 1) am_fused_kernel(KParams p)
 
 // Uneven batching: persistent launches over the tiles of many problems of
 // different batch size, horizon, obstacle and circle counts, one kernel per
-// variant (circle count M, alpha form LIT) so that each is compiled on its
-// own (the variants inlined into one kernel spill registers).  The variant
+// variant (precision form PR, circle count M, alpha form LIT) so that each is
+// compiled on its own (the variants inlined into one kernel spill registers).
+// PR selects the DOT phase's tensor-core products as in the single-problem
+// kernel, so a problem gives the same bits alone and in a group.  The variant
 // kernels of one solve run concurrently; CTAs take work items (problem,
 // tile) of their variant from a list in order, through one atomic counter
 // per variant, and re-stage constants whenever they move to another problem.
 // The lists, their lengths and offsets live in device memory, so a captured
 // launch stays valid when the set of problems it advances changes.
-//   head[v]: number of items of variant v; head[8 + v]: offset of its list
+//   head[v]: number of items of variant v; head[kGroupVariants + v]: offset of its list
 //   ctl[2 v]: its work counter (zeroed before the launch); ctl[2 v + 1]: status
-template <int M, bool LIT>
+template <int M, bool LIT, int PR>
 __global__ void __launch_bounds__(kMaxThreads, 1)
 am_group_kernel(const KParams *probs, const int *items, const int *head, int *ctl)
 {
-    constexpr int v = M * 2 + (LIT ? 1 : 0) - 2;
+    constexpr int v = PR * 8 + M * 2 + (LIT ? 1 : 0) - 2;
     int *counter = ctl + 2 * v;
     const int nitems = head[v];
-    const int *list = items + 2 * head[8 + v];
+    const int *list = items + 2 * head[kGroupVariants + v];
     extern __shared__ __align__(128) float sm[];
     __shared__ KParams kp;
     __shared__ int s_item;
@@ -1047,7 +1049,7 @@ am_group_kernel(const KParams *probs, const int *items, const int *head, int *ct
             parity ^= 1u;
             cur = item.x;
         }
-        run_tile<M, LIT>(kp, sm, smem_layout(kp.L, kp.T), tile_of(item.y, kp.B, kp.ntiles));
+        run_tile<M, LIT, PR>(kp, sm, smem_layout(kp.L, kp.T), tile_of(item.y, kp.B, kp.ntiles));
         __syncthreads();
     }
 }
@@ -1095,25 +1097,30 @@ int launch_group(const GroupLaunch &g, void *stream, int *launches, const char *
         return -2;
     }
     switch (g.variant) {
-#define AM_GCASE(MM, LL)                                                                        \
-    case MM * 2 + LL - 2:                                                                       \
-        e = cudaFuncSetAttribute(am_group_kernel<MM, LL>,                                       \
+#define AM_GCASE(MM, LL, PP)                                                                    \
+    case PP * 8 + MM * 2 + LL - 2:                                                              \
+        e = cudaFuncSetAttribute(am_group_kernel<MM, LL, PP>,                                   \
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, int(g.smem));     \
         if (e != cudaSuccess) {                                                                 \
             *why = cudaGetErrorString(e);                                                       \
             return -2;                                                                          \
         }                                                                                       \
-        am_group_kernel<MM, LL><<<g.grid, g.threads, g.smem, st>>>(g.d_probs, g.d_items, g.d_head, \
-                                                                   g.d_ctl);                   \
+        am_group_kernel<MM, LL, PP><<<g.grid, g.threads, g.smem, st>>>(g.d_probs, g.d_items,    \
+                                                                       g.d_head, g.d_ctl);      \
         break;
-        AM_GCASE(1, 0)
-        AM_GCASE(1, 1)
-        AM_GCASE(2, 0)
-        AM_GCASE(2, 1)
-        AM_GCASE(3, 0)
-        AM_GCASE(3, 1)
-        AM_GCASE(4, 0)
-        AM_GCASE(4, 1)
+#define AM_GCASES(PP)                                                                           \
+        AM_GCASE(1, 0, PP)                                                                      \
+        AM_GCASE(1, 1, PP)                                                                      \
+        AM_GCASE(2, 0, PP)                                                                      \
+        AM_GCASE(2, 1, PP)                                                                      \
+        AM_GCASE(3, 0, PP)                                                                      \
+        AM_GCASE(3, 1, PP)                                                                      \
+        AM_GCASE(4, 0, PP)                                                                      \
+        AM_GCASE(4, 1, PP)
+        AM_GCASES(0)
+        AM_GCASES(1)
+        AM_GCASES(2)
+#undef AM_GCASES
 #undef AM_GCASE
     default:
         return -1;
@@ -1127,7 +1134,7 @@ int launch_group(const GroupLaunch &g, void *stream, int *launches, const char *
     return 0;
 }
 
-int group_variant(const ConstLayout &L) { return L.m * 2 + (L.alpha_mode ? 1 : 0) - 2; }
+int group_variant(const ConstLayout &L) { return L.precision * 8 + L.m * 2 + (L.alpha_mode ? 1 : 0) - 2; }
 
 int fused_auto_tile(const ConstLayout &L, int B, int num_sms)
 {

@@ -161,14 +161,15 @@ constexpr float kNearMargin = 0.6f;
 // Grouped launch: many problems' tiles in persistent kernels, one kernel per
 // variant (circle count, alpha form) present; the variant kernels of one
 // solve run concurrently.
-constexpr int kGroupVariants = 8;
+constexpr int kGroupVariants = 24;  // precision (3) x circle count (4) x alpha form (2)
 struct GroupLaunch {
     const FusedProblem *d_probs;  // device array, one per problem
     const int *d_items;           // device array of (problem, tile) pairs, all variants
-    const int *d_head;            // device: item count per variant [8], list offset per variant [8]
+    const int *d_head;            // device: item count per variant [kGroupVariants], then list
+                                  // offset per variant [kGroupVariants]
     int *d_ctl;                   // device {work counter, status} per variant; the
                                   // variant's counter is zeroed by launch_group
-    int variant;                  // m * 2 + alpha_mode - 2
+    int variant;                  // precision * 8 + m * 2 + alpha_mode - 2
     int threads;
     size_t smem;
     int grid;

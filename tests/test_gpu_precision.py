@@ -1,10 +1,9 @@
 """Reduced-precision forms (AM_TF32, AM_BF16) on the 4096-trajectory
 paper-shaped workload, against the FP64 oracle on sampled trajectories.
 
-In these forms the contractions over the time grid (R = F^T (g - F xi1), and
-W^T delta, P^T delta of the heading step) take one tensor-core product of
-operands rounded to TF32 (unit roundoff u = 2^-11) or BF16 (u = 2^-8); the
-position step keeps its three TF32 products.  The error is a reported
+In these forms the tensor-core contraction over the time grid, R = F^T (g -
+F xi1), takes one product of operands rounded to TF32 (unit roundoff u =
+2^-11) or BF16 (u = 2^-8); the position and heading steps stay FP32.  The error is a reported
 property of the form, not an FP32 parity bar: after 10 iterations the
 coefficients are measured within ~7 u (TF32) and ~17 u (BF16) of the oracle
 and the cost within ~1 u and ~2.5 u.  The bounds below are 30 u on
@@ -65,15 +64,11 @@ def test_fp32_form_on_the_same_workload(workload):
         assert coef_err(g[key][idx], o[key]).max() <= COEF_TOL
 
 
-def test_reduced_precision_only_on_the_fused_kernel():
+def test_reduced_precision_not_on_the_plain_kernel():
     T = tj()
     pb = W.make_problem("tiny", 0)
     P = T.Problem(pb, precision=T.AM_TF32, kernel=T.AM_KERNEL_PLAIN)
     with pytest.raises(T.TrajamError) as e:
         P.solve(pb["init"].astype(np.float32), 5)
     assert e.value.code == T.AM_ERR_ARG
-    P.close()
-    P = T.Problem(pb, precision=T.AM_BF16)
-    with pytest.raises(T.TrajamError):
-        T.Group([P])
     P.close()
