@@ -340,13 +340,18 @@ AM_API void am_group_destroy(am_group *g);
  * iterations).  A scene is a problem whose state (xi, lambda) stays resident
  * on the device between requests.  A worker thread serves requests in
  * rounds: a round takes at most one pending request per scene (oldest
- * first), applies each request's updates (start state, obstacle tracks),
- * advances the scenes by `iters` iterations -- all of them in one grouped
- * launch (AM_SRV_BATCHED; a round of one request uses the scene's own
- * kernel), or one request per round with the scene's own kernel
- * (AM_SRV_SEQUENTIAL, the comparator) -- selects each scene's best
- * trajectory and completes the requests.  Requests that arrive during a
- * round wait for the next one (continuous batching by rounds).
+ * first) among the scenes not already in flight, applies each request's
+ * updates (start state, obstacle tracks), advances the scenes by `iters`
+ * iterations -- all of them in one grouped launch (AM_SRV_BATCHED; a round
+ * of one request uses the scene's own kernel), or one request per round
+ * with the scene's own kernel (AM_SRV_SEQUENTIAL, the comparator) --
+ * selects each scene's best trajectory and completes the requests.  Up to
+ * `lanes` rounds are in flight at once, each on its own stream: the worker
+ * issues a round without waiting for it, polls the rounds in flight, and
+ * admits requests that arrive meanwhile into the next free lane, so their
+ * work starts while earlier rounds are still on the GPU (continuous
+ * batching).  A request's result does not depend on the round or lane it
+ * was served in.
  *
  * Scenes are admitted while the device bytes they hold (am_scene_bytes)
  * stay within the budget; am_server_add_scene returns AM_ERR_BUDGET beyond
@@ -364,6 +369,8 @@ typedef struct {
     int mode;               /* AM_SRV_BATCHED | AM_SRV_SEQUENTIAL              */
     int max_batch;          /* requests per round (0 = up to one per scene)    */
     int max_pending;        /* queue bound (0 = 65536)                         */
+    int lanes;              /* rounds in flight (0 = 2 batched, 1 sequential;
+                               at most 8); AM_SRV_SEQUENTIAL takes 1          */
 } am_server_desc;
 
 #define AM_REQ_GOAL 1       /* am_request.flags: replace the goal state        */

@@ -555,7 +555,7 @@ struct am_group {
     int threads = 0;          // block size; 0 = tuned or the kernel maximum
     bool use_graph = true;
     // One upload region per solve, device and pinned host copies:
-    //   [count per variant (8), list offset per variant (8)] [descriptors]
+    //   [count per variant, list offset per variant] [descriptors]
     //   [work items of every variant] [active list]
     char *d_up = nullptr, *h_up = nullptr;
     size_t up_cap = 0, h_up_cap = 0;
@@ -1213,6 +1213,50 @@ int am_group_get_best(am_group *g, float *out, int mem, void *stream)
         if (g->h_status[2 * v + 1]) return fail(AM_ERR_TIMEOUT, "a kernel of the group gave up a bounded wait");
     return AM_OK;
 }
+
+}  // extern "C"
+
+namespace trajam {
+
+int group_best_async(::am_group *g, float *h_out, void *stream)
+{
+    const std::vector<int> act = active_list(g);
+    if (!g->d_up || act != g->solved_list) return fail(AM_ERR_STATE, "no group solve of this active list");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = ensure(g->d_bests, g->bests_cap, 36 * act.size(), "best records");
+    if (rc) return rc;
+    if (launch_group_argmin(g->d_probs, g->d_list, int(act.size()), g->d_bests, st, &g->launches))
+        return fail(AM_ERR_CUDA, "best selection launch failed");
+    CK(cudaMemcpyAsync(h_out, g->d_bests, sizeof(float) * 36 * act.size(), cudaMemcpyDeviceToHost, st), "best copy");
+    CK(cudaMemcpyAsync(g->h_status, g->d_ctl, 2 * kGroupVariants * sizeof(int), cudaMemcpyDeviceToHost, st),
+       "status copy");
+    return AM_OK;
+}
+
+int group_status(const ::am_group *g)
+{
+    for (int v = 0; v < kGroupVariants; ++v)
+        if (g->h_status[2 * v + 1]) return fail(AM_ERR_TIMEOUT, "a kernel of the group gave up a bounded wait");
+    return AM_OK;
+}
+
+int problem_status_async(::am_problem *h, void *stream)
+{
+    int *h_err = reinterpret_cast<int *>(h->h_best + 40);
+    CK(cudaMemcpyAsync(h_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, static_cast<cudaStream_t>(stream)),
+       "status read");
+    return AM_OK;
+}
+
+int problem_status(const ::am_problem *h)
+{
+    const int err = reinterpret_cast<const int *>(h->h_best + 40)[0];
+    return err ? fail(AM_ERR_TIMEOUT, "a kernel gave up a bounded wait (status %d)", err) : AM_OK;
+}
+
+}  // namespace trajam
+
+extern "C" {
 
 int am_group_autotune(am_group *g, int iters, void *stream, int *threads_out, float *ms_out)
 {

@@ -8,6 +8,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 struct am_problem;
+struct am_group;
 
 namespace trajam {
 
@@ -242,6 +243,15 @@ void shift_matrix(double s, double S[121]);
 
 int launch_init_state(float *state, const float *init, const float *warm, int B, void *stream,
                       int *launches);
+// Queues the best selection of a group's last solve on st and copies the
+// records (36 floats per active problem) and the kernels' status words into
+// pinned host memory, without waiting; group_status reads those status words
+// once the stream has passed that point.
+int group_best_async(::am_group *g, float *h_out, void *st);
+int group_status(const ::am_group *g);
+// The same for one problem's status word (into the handle's pinned area).
+int problem_status_async(::am_problem *h, void *st);
+int problem_status(const ::am_problem *h);
 // Handle accessors for entry points outside the C-ABI file.
 int handle_constants(const ::am_problem *h, const float **cblob, ConstLayout *L);
 int report_error(int code, const char *msg);

@@ -1,6 +1,8 @@
 // Re-planning server (include/trajam.h, "serving"): resident warm-started
-// scenes, HBM-budget admission, a worker thread that serves requests in
-// rounds of continuous batching through one grouped launch per round.
+// scenes, HBM-budget admission, and a worker thread that keeps up to `lanes`
+// rounds of continuous batching in flight, each a grouped launch (or a
+// scene's own kernel) on its own stream, admitting new requests while
+// earlier rounds run.
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -44,16 +46,35 @@ struct Scene {
     float best[33];
 };
 
+// One round in flight: its stream, group (a grouped launch touches the
+// group's own device buffers, so each lane has one), pinned best records and
+// completion event.
+struct Lane {
+    cudaStream_t st = nullptr;
+    am_group *g = nullptr;
+    float *h_bests = nullptr;  // 36 floats per request of the round
+    cudaEvent_t ev = nullptr;
+    std::vector<Request> batch;
+    bool busy = false, grouped = false;
+    bool dead = false;  // its round ran out of time: the stream may still write, never reused
+    int rc = AM_OK;
+    double t_start = 0;
+};
+
+constexpr int kMaxLanes = 8;
+// A round still running after this long completes with AM_ERR_TIMEOUT.
+constexpr double kRoundLimitS = 60.0;
+
 }  // namespace
 
 struct am_server {
     am_server_desc d;
     int device = 0;
-    cudaStream_t st = nullptr;
+    cudaStream_t st = nullptr;   // scene admission (cold starts) and autotuning
     std::vector<Scene> scenes;
     size_t used = 0;
-    am_group *g = nullptr;
-    float *h_bests = nullptr;  // pinned, 36 floats per scene
+    std::vector<Lane> lanes;
+    std::vector<char> in_flight;  // per scene
     std::thread worker;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -87,102 +108,173 @@ int update_boundary(Scene &sc, const am_request &r)
     return am_set_boundary(sc.h, x, y, psi);
 }
 
-// One round: updates, solve, best selection.  Fills best records (36 floats
-// per request, in batch order) or returns an error code.
-int serve_round(am_server *s, std::vector<Request> &batch)
+// Queues one round on the lane's stream: each request's updates, the solve
+// (one grouped launch for several scenes, a scene's own kernel for one, one
+// solve per request in the sequential mode), the best selection and the
+// copy of the best records and status words to pinned memory, then the
+// lane's event.  Nothing here waits for the device.
+void issue_round(am_server *s, Lane &ln)
 {
     int rc = AM_OK;
-    for (auto &q : batch) {
+    ln.t_start = now_s();
+    for (auto &q : ln.batch) {
         Scene &sc = s->scenes[q.r.scene];
-        rc = am_set_stream(sc.h, s->st);
+        rc = am_set_stream(sc.h, ln.st);
         if (!rc && !q.xo.empty()) rc = problem_update_tracks(sc.h, q.xo.data(), q.yo.data());
         if (!rc) rc = update_boundary(sc, q.r);
-        if (!rc && (q.r.flags & AM_REQ_RESAMPLE)) rc = am_resample(sc.h, q.r.seed, q.r.sigma, s->st);
+        if (!rc && (q.r.flags & AM_REQ_RESAMPLE)) rc = am_resample(sc.h, q.r.seed, q.r.sigma, ln.st);
         else if (!rc && (q.r.flags & AM_REQ_SHIFT) && q.r.advance > 0 && sc.has_best)
-            rc = am_shift(sc.h, q.r.advance, s->st);  // re-timed together with the start state
-        if (!rc && (q.r.flags & AM_REQ_SCALE_LAMBDA)) rc = am_scale_multipliers(sc.h, q.r.lambda_scale, s->st);
-        if (rc) return rc;
+            rc = am_shift(sc.h, q.r.advance, ln.st);  // re-timed together with the start state
+        if (!rc && (q.r.flags & AM_REQ_SCALE_LAMBDA)) rc = am_scale_multipliers(sc.h, q.r.lambda_scale, ln.st);
+        if (rc) break;
     }
-    // A round of several requests goes through one grouped launch; a round of
-    // one takes the single-problem kernel, whose tile and block size are
-    // chosen for that problem alone (the per-tile code is the same).
-    if (s->d.mode == AM_SRV_BATCHED && batch.size() > 1) {
+    ln.grouped = !rc && s->d.mode == AM_SRV_BATCHED && ln.batch.size() > 1;
+    if (ln.grouped) {
         std::vector<int> act;
-        for (auto &q : batch) act.push_back(q.r.scene);
-        rc = am_group_set_active(s->g, act.data(), int(act.size()));
-        if (!rc) rc = am_group_solve(s->g, s->d.iters, s->st);
-        if (!rc) rc = am_group_get_best(s->g, s->h_bests, AM_HOST, s->st);
-        return rc;
+        for (auto &q : ln.batch) act.push_back(q.r.scene);
+        rc = am_group_set_active(ln.g, act.data(), int(act.size()));
+        if (!rc) rc = am_group_solve(ln.g, s->d.iters, ln.st);
+        if (!rc) rc = group_best_async(ln.g, ln.h_bests, ln.st);
+    } else {
+        for (size_t k = 0; k < ln.batch.size() && !rc; ++k) {
+            Scene &sc = s->scenes[ln.batch[k].r.scene];
+            rc = am_solve_batch(sc.h, sc.B, nullptr, nullptr, s->d.iters, ln.st, AM_DEVICE);
+            if (!rc) rc = am_get_best_async(sc.h, ln.h_bests + 36 * k, AM_HOST, ln.st);
+            if (!rc) rc = problem_status_async(sc.h, ln.st);
+        }
     }
-    for (size_t k = 0; k < batch.size() && !rc; ++k) {
-        Scene &sc = s->scenes[batch[k].r.scene];
-        float *o = s->h_bests + 36 * k;
-        int idx = 0;
-        rc = am_solve_batch(sc.h, sc.B, nullptr, nullptr, s->d.iters, s->st, AM_DEVICE);
-        if (!rc) rc = am_get_best(sc.h, o + 3, &o[1], &o[2], &idx);
-        o[0] = float(idx);
+    if (cudaEventRecord(ln.ev, ln.st) != cudaSuccess && !rc) rc = AM_ERR_CUDA;
+    ln.rc = rc;
+    ln.busy = true;
+}
+
+// Completes a finished round (its event passed, or it failed): results,
+// the scenes' last best plans, and the scenes leave the in-flight set.
+void complete_round(am_server *s, Lane &ln, int rc)
+{
+    if (!rc && ln.grouped) rc = group_status(ln.g);
+    if (!rc && !ln.grouped)
+        for (auto &q : ln.batch)
+            if (!rc) rc = problem_status(s->scenes[q.r.scene].h);
+    const double t_done = now_s();
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (size_t k = 0; k < ln.batch.size(); ++k) {
+        Request &q = ln.batch[k];
+        am_result r;
+        std::memset(&r, 0, sizeof(r));
+        r.status = rc;
+        r.t_submit = q.t_submit;
+        r.t_start = ln.t_start;
+        r.t_done = t_done;
+        r.round = s->rounds;
+        r.batch = int(ln.batch.size());
+        if (!rc) {
+            const float *o = ln.h_bests + 36 * k;
+            r.index = int(o[0]);
+            r.cost = o[1];
+            r.residual = o[2];
+            std::memcpy(r.coeffs, o + 3, sizeof(r.coeffs));
+            if (!std::isfinite(r.cost)) {
+                r.status = AM_ERR_NAN;  // every trajectory of the scene is non-finite
+            } else {
+                Scene &sc = s->scenes[q.r.scene];
+                std::memcpy(sc.best, r.coeffs, sizeof(sc.best));
+                sc.has_best = true;
+            }
+        }
+        s->in_flight[q.r.scene] = 0;
+        s->done[q.ticket] = r;
+        ++s->completed;
     }
-    return rc;
+    ++s->rounds;
+    ln.batch.clear();
+    ln.busy = false;
+    s->cv_done.notify_all();
+}
+
+// Takes the next round's requests: at most one per scene, oldest first,
+// scenes in flight skipped.  Called with the lock held.
+void take_batch(am_server *s, std::vector<Request> &batch, std::vector<char> &taken)
+{
+    const size_t nsc = s->scenes.size();
+    size_t limit = s->d.mode == AM_SRV_SEQUENTIAL ? 1 : nsc;
+    if (s->d.max_batch > 0 && size_t(s->d.max_batch) < limit) limit = size_t(s->d.max_batch);
+    std::fill(taken.begin(), taken.end(), 0);
+    for (auto it = s->pending.begin(); it != s->pending.end() && batch.size() < limit;) {
+        const int sc = it->r.scene;
+        if (!taken[sc] && !s->in_flight[sc]) {
+            taken[sc] = 1;
+            s->in_flight[sc] = 1;
+            batch.push_back(std::move(*it));
+            it = s->pending.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+
+bool admissible(const am_server *s)
+{
+    for (const Request &q : s->pending)
+        if (!s->in_flight[q.r.scene]) return true;
+    return false;
 }
 
 void worker_main(am_server *s)
 {
     cudaSetDevice(s->device);
-    const size_t nsc = s->scenes.size();
-    std::vector<Request> batch;
-    std::vector<char> taken(nsc);
+    std::vector<char> taken(s->scenes.size());
+    bool stopping = false;
     for (;;) {
-        batch.clear();
-        {
-            std::unique_lock<std::mutex> lk(s->mu);
-            s->cv_work.wait(lk, [&] { return s->stop || !s->pending.empty(); });
-            if (s->stop) break;
-            size_t limit = s->d.mode == AM_SRV_SEQUENTIAL ? 1 : nsc;
-            if (s->d.max_batch > 0 && size_t(s->d.max_batch) < limit) limit = size_t(s->d.max_batch);
-            std::fill(taken.begin(), taken.end(), 0);
-            for (auto it = s->pending.begin(); it != s->pending.end() && batch.size() < limit;) {
-                if (!taken[it->r.scene]) {
-                    taken[it->r.scene] = 1;
-                    batch.push_back(std::move(*it));
-                    it = s->pending.erase(it);
+        bool busy = false, progressed = false;
+        // rounds that finished (or ran out of time) complete first
+        for (Lane &ln : s->lanes) {
+            if (!ln.busy) continue;
+            const cudaError_t e = cudaEventQuery(ln.ev);
+            if (e == cudaErrorNotReady) {
+                if (now_s() - ln.t_start > kRoundLimitS) {
+                    complete_round(s, ln, AM_ERR_TIMEOUT);
+                    ln.dead = true;
+                    progressed = true;
                 } else {
-                    ++it;
+                    busy = true;
                 }
+                continue;
+            }
+            complete_round(s, ln, e == cudaSuccess ? ln.rc : AM_ERR_CUDA);
+            progressed = true;
+        }
+        // then every free lane takes a round of what is admissible
+        if (!stopping) {
+            for (Lane &ln : s->lanes) {
+                if (ln.busy || ln.dead) continue;
+                {
+                    std::lock_guard<std::mutex> lk(s->mu);
+                    if (s->stop) {
+                        stopping = true;
+                        break;
+                    }
+                    take_batch(s, ln.batch, taken);
+                }
+                if (ln.batch.empty()) break;
+                issue_round(s, ln);
+                busy = progressed = true;
             }
         }
-        const double t_start = now_s();
-        int rc;
-        {
-            NvtxRange range("am_server round");
-            rc = serve_round(s, batch);
+        if (stopping && !busy) break;
+        if (progressed) continue;
+        bool live = false;
+        for (const Lane &ln : s->lanes) live = live || !ln.dead;
+        if (!live) break;  // every lane ran out of time: what is queued fails below
+        if (busy) {
+            // rounds in flight: poll their events (a request arriving now
+            // waits for a free lane, at most one round)
+            std::this_thread::yield();
+            continue;
         }
-        const double t_done = now_s();
-        std::lock_guard<std::mutex> lk(s->mu);
-        for (size_t k = 0; k < batch.size(); ++k) {
-            Request &q = batch[k];
-            am_result r;
-            std::memset(&r, 0, sizeof(r));
-            r.status = rc;
-            r.t_submit = q.t_submit;
-            r.t_start = t_start;
-            r.t_done = t_done;
-            r.round = s->rounds;
-            r.batch = int(batch.size());
-            if (!rc) {
-                const float *o = s->h_bests + 36 * k;
-                r.index = int(o[0]);
-                r.cost = o[1];
-                r.residual = o[2];
-                std::memcpy(r.coeffs, o + 3, sizeof(r.coeffs));
-                Scene &sc = s->scenes[q.r.scene];
-                std::memcpy(sc.best, r.coeffs, sizeof(sc.best));
-                sc.has_best = true;
-            }
-            s->done[q.ticket] = r;
-            ++s->completed;
-        }
-        ++s->rounds;
-        s->cv_done.notify_all();
+        std::unique_lock<std::mutex> lk(s->mu);
+        s->cv_work.wait(lk, [&] { return s->stop || admissible(s); });
+        if (s->stop) stopping = true;
     }
     // Stopped: what is still queued completes with AM_ERR_STATE.
     std::lock_guard<std::mutex> lk(s->mu);
@@ -195,6 +287,17 @@ void worker_main(am_server *s)
     }
     s->pending.clear();
     s->cv_done.notify_all();
+}
+
+void free_lanes(am_server *s)
+{
+    for (Lane &ln : s->lanes) {
+        if (ln.g) am_group_destroy(ln.g);
+        if (ln.h_bests) cudaFreeHost(ln.h_bests);
+        if (ln.ev) cudaEventDestroy(ln.ev);
+        if (ln.st) cudaStreamDestroy(ln.st);
+    }
+    s->lanes.clear();
 }
 
 }  // namespace
@@ -213,11 +316,14 @@ int am_server_create(const am_server_desc *d, am_server **out)
     *out = nullptr;
     if (d->iters < 1 || d->iters > 100000) return report_error(AM_ERR_ARG, "iters must be in [1, 100000]");
     if (d->mode != AM_SRV_BATCHED && d->mode != AM_SRV_SEQUENTIAL) return report_error(AM_ERR_ARG, "bad mode");
-    if (d->max_batch < 0 || d->max_pending < 0) return report_error(AM_ERR_ARG, "negative limit");
+    if (d->max_batch < 0 || d->max_pending < 0 || d->lanes < 0) return report_error(AM_ERR_ARG, "negative limit");
+    if (d->lanes > kMaxLanes) return report_error(AM_ERR_ARG, "at most 8 lanes");
     am_server *s = new (std::nothrow) am_server;
     if (!s) return report_error(AM_ERR_ARG, "out of host memory");
     s->d = *d;
     if (s->d.max_pending == 0) s->d.max_pending = 65536;
+    if (s->d.mode == AM_SRV_SEQUENTIAL) s->d.lanes = 1;
+    else if (s->d.lanes == 0) s->d.lanes = 2;
     cudaGetDevice(&s->device);
     if (cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking) != cudaSuccess) {
         delete s;
@@ -259,18 +365,30 @@ int am_server_start(am_server *s)
     if (!s) return report_error(AM_ERR_ARG, "null server");
     if (s->started) return report_error(AM_ERR_STATE, "already started");
     if (s->scenes.empty()) return report_error(AM_ERR_STATE, "no scenes");
-    if (cudaMallocHost(&s->h_bests, sizeof(float) * 36 * s->scenes.size()) != cudaSuccess)
-        return report_error(AM_ERR_CUDA, "pinned allocation failed");
-    if (s->d.mode == AM_SRV_BATCHED) {
-        std::vector<am_problem *> hs;
-        for (auto &sc : s->scenes) hs.push_back(sc.h);
-        int rc = am_group_create(hs.data(), int(hs.size()), &s->g);
-        if (rc) return rc;
-        int threads = 0;
-        float ms = 0;
-        rc = am_group_autotune(s->g, s->d.iters, s->st, &threads, &ms);
-        if (rc) return rc;
+    std::vector<am_problem *> hs;
+    for (auto &sc : s->scenes) hs.push_back(sc.h);
+    int threads = 0;
+    s->lanes.resize(size_t(s->d.lanes));
+    for (size_t k = 0; k < s->lanes.size(); ++k) {
+        Lane &ln = s->lanes[k];
+        int rc = AM_OK;
+        if (cudaStreamCreateWithFlags(&ln.st, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ln.ev, cudaEventDisableTiming) != cudaSuccess ||
+            cudaMallocHost(&ln.h_bests, sizeof(float) * 36 * s->scenes.size()) != cudaSuccess)
+            rc = report_error(AM_ERR_CUDA, "lane set-up failed");
+        if (!rc && s->d.mode == AM_SRV_BATCHED) {
+            rc = am_group_create(hs.data(), int(hs.size()), &ln.g);
+            // the block size is tuned once (on the admission stream) and shared
+            float ms = 0;
+            if (!rc && k == 0) rc = am_group_autotune(ln.g, s->d.iters, s->st, &threads, &ms);
+            else if (!rc) rc = am_group_set_option(ln.g, AM_GOPT_THREADS, threads);
+        }
+        if (rc) {
+            free_lanes(s);
+            return rc;
+        }
     }
+    s->in_flight.assign(s->scenes.size(), 0);
     s->started = true;
     s->worker = std::thread(worker_main, s);
     return AM_OK;
@@ -357,8 +475,7 @@ void am_server_destroy(am_server *s)
             std::this_thread::yield();
     }
     for (Scene &sc : s->scenes) am_set_stream(sc.h, nullptr);
-    if (s->g) am_group_destroy(s->g);
-    if (s->h_bests) cudaFreeHost(s->h_bests);
+    free_lanes(s);
     if (s->st) cudaStreamDestroy(s->st);
     delete s;
 }

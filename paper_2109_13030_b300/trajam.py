@@ -49,7 +49,7 @@ class AmProblemDesc(C.Structure):
 
 class AmServerDesc(C.Structure):
     _fields_ = [("budget_bytes", C.c_size_t), ("iters", C.c_int), ("mode", C.c_int),
-                ("max_batch", C.c_int), ("max_pending", C.c_int)]
+                ("max_batch", C.c_int), ("max_pending", C.c_int), ("lanes", C.c_int)]
 
 
 class AmRequest(C.Structure):
@@ -393,8 +393,8 @@ def am_group_destroy(g):
     _lib.am_group_destroy(g)
 
 
-def am_server_create(budget_bytes, iters, mode=AM_SRV_BATCHED, max_batch=0, max_pending=0) -> int:
-    d = AmServerDesc(int(budget_bytes), int(iters), int(mode), int(max_batch), int(max_pending))
+def am_server_create(budget_bytes, iters, mode=AM_SRV_BATCHED, max_batch=0, max_pending=0, lanes=0) -> int:
+    d = AmServerDesc(int(budget_bytes), int(iters), int(mode), int(max_batch), int(max_pending), int(lanes))
     s = C.c_void_p()
     _check(_lib.am_server_create(C.byref(d), C.byref(s)))
     return s.value
@@ -602,8 +602,8 @@ class Group:
 class Server:
     """Re-planning server over resident scenes (Problems), see am_server_*."""
 
-    def __init__(self, budget_bytes, iters, mode=AM_SRV_BATCHED, max_batch=0, max_pending=0):
-        self.s = am_server_create(budget_bytes, iters, mode, max_batch, max_pending)
+    def __init__(self, budget_bytes, iters, mode=AM_SRV_BATCHED, max_batch=0, max_pending=0, lanes=0):
+        self.s = am_server_create(budget_bytes, iters, mode, max_batch, max_pending, lanes)
         self.scenes = []   # keeps the Problems alive while the server uses them
 
     def add_scene(self, problem, init):

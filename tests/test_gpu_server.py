@@ -76,6 +76,32 @@ def test_result_alone_equals_result_in_mix():
     np.testing.assert_array_equal(np.asarray(mixed[0]["coeffs"]), np.asarray(alone["coeffs"]))
 
 
+def test_request_arriving_during_a_round_overlaps_it():
+    """Continuous batching with rounds in flight: with one request per round
+    and two lanes, a request for another scene submitted while a long round is
+    on the GPU is issued on the second lane and starts before the first round
+    completes; both results equal their scenes served alone, bit for bit."""
+    big = W.make_shape(31, B=6000, q=100, n=10, m=3)
+    small = W.make_shape(32, B=64, q=50, n=4, m=2)
+    pbs = [big, small]
+    alone = []
+    for k in range(2):
+        S, probs = make_server(pbs, 200, max_batch=1)
+        alone.append(S.wait(S.submit(k)))
+        close(S, probs)
+    S, probs = make_server(pbs, 200, max_batch=1, lanes=2)
+    ta = S.submit(0)
+    tb = S.submit(1)
+    ra, rb = S.wait(ta), S.wait(tb)
+    close(S, probs)
+    assert ra["status"] == 0 and rb["status"] == 0
+    assert ra["round"] != rb["round"] and ra["batch"] == rb["batch"] == 1
+    assert rb["t_start"] < ra["t_done"], (rb["t_start"], ra["t_done"])
+    for r, a in zip((ra, rb), alone):
+        np.testing.assert_array_equal(np.asarray(r["coeffs"]), np.asarray(a["coeffs"]))
+        assert r["cost"] == a["cost"]
+
+
 def test_batched_round_holds_many_scenes_and_matches_oracle():
     """One round advances six scenes of different shapes; a second request for
     a scene already in the round waits for the next round."""
