@@ -269,8 +269,13 @@ AM_API int am_last_solve_stats(am_problem *h, int *launches);
  * re-planning step whose budget cudaMalloc's unbounded, device-synchronising
  * latency would break, or code running under an allocator or a stream
  * capture that forbids raw allocations.
- *  h        a handle set up beforehand (am_init_problem, am_set_obstacles);
- *           only its device constants are read, its buffers are untouched.
+ *  h        a handle set up beforehand (am_init_problem, am_set_obstacles)
+ *           on the device that is current now (else AM_ERR_ARG); only its
+ *           device constants are read, its buffers are untouched.  The call
+ *           orders itself after the handle's own stream, where the constants
+ *           were uploaded (an event of the handle, recorded there and waited
+ *           on; nothing is allocated).  While `stream` is being captured the
+ *           caller must have ordered it after the handle's stream itself.
  *  state    device, B x AM_STATE_FLOATS, in/out (the cold-start state has
  *           xi1 = (c_x, cos c_psi, c_y, sin c_psi), lambda = 0).
  *  res, res_psi, cost, mind   device, B floats each (as am_get_results).
@@ -278,7 +283,8 @@ AM_API int am_last_solve_stats(am_problem *h, int *launches);
  * needs more than the fixed area holds (about 650 trajectories at q = 100,
  * m = 3, n = 10).  The first call on a device looks up the area's device
  * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  All calls in the process share the one
+ * call before any stream capture.  Later calls check the cached address
+ * against the current context and look it up again after a device reset.  All calls in the process share the one
  * area: calls that overlap on the GPU (other streams, other host threads)
  * race and must be serialised by the caller.  Nothing in the area needs to
  * start at zero: every word a call reads it has written earlier in the same

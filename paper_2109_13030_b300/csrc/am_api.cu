@@ -86,6 +86,7 @@ struct am_problem {
     int tile = 0;
     cudaStream_t stream = nullptr;
     cudaEvent_t ev = nullptr;
+    cudaEvent_t order_ev = nullptr;  // orders other streams after this handle's stream
     int launches = 0;
     bool solved = false;
     int diag_stall = 0;
@@ -240,6 +241,8 @@ int am_init_problem(const am_problem_desc *d, am_problem **out)
     int rc = AM_OK;
     cudaError_t e = cudaFree(nullptr);
     if (e != cudaSuccess) rc = cuda_fail(e, "CUDA initialisation");
+    if (!rc && cudaEventCreateWithFlags(&h->order_ev, cudaEventDisableTiming) != cudaSuccess)
+        rc = fail(AM_ERR_CUDA, "event creation failed");
     if (!rc && cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming) != cudaSuccess)
         rc = fail(AM_ERR_CUDA, "event creation failed");
     if (!rc && cudaMallocHost(&h->h_best, 64 * sizeof(float)) != cudaSuccess)
@@ -274,6 +277,7 @@ void am_destroy(am_problem *h)
     cudaFree(h->d_score);
     if (h->h_best) cudaFreeHost(h->h_best);
     if (h->ev) cudaEventDestroy(h->ev);
+    if (h->order_ev) cudaEventDestroy(h->order_ev);
     delete h;
 }
 
@@ -540,6 +544,19 @@ int handle_constants(const am_problem *h, const float **cblob, ConstLayout *L)
     if (!h) return fail(AM_ERR_ARG, "null handle");
     *cblob = h->d_blob;
     *L = h->L;
+    return AM_OK;
+}
+
+int handle_order_before(const am_problem *h, void *stream)
+{
+    if (!h) return fail(AM_ERR_ARG, "null handle");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (st == h->stream) return AM_OK;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(st, &cs), "stream capture query");
+    if (cs != cudaStreamCaptureStatusNone) return AM_OK;  // the caller orders a captured stream
+    CK(cudaEventRecord(h->order_ev, h->stream), "order event record");
+    CK(cudaStreamWaitEvent(st, h->order_ev, 0), "order event wait");
     return AM_OK;
 }
 

@@ -254,6 +254,11 @@ int problem_status_async(::am_problem *h, void *st);
 int problem_status(const ::am_problem *h);
 // Handle accessors for entry points outside the C-ABI file.
 int handle_constants(const ::am_problem *h, const float **cblob, ConstLayout *L);
+// Makes work queued next on stream wait for everything queued so far on the
+// handle's own stream (its constant uploads and obstacle preparation): an
+// event the handle owns is recorded there and waited on.  Nothing is
+// allocated.  Skipped when the streams are the same or stream is capturing.
+int handle_order_before(const ::am_problem *h, void *stream);
 int report_error(int code, const char *msg);
 // Scene accessors for the server.  problem_shape returns -1 when the handle
 // has no state yet.

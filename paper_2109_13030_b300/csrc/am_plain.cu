@@ -463,7 +463,11 @@ float *g_noalloc_addr[kMaxDevices] = {};
 
 // Device address of the fixed area on the current device.  Host code cannot
 // use the symbol itself (it names a host-side stand-in), so the address is
-// looked up once per device, with that device current, and cached.
+// looked up once per device, with that device current, and cached.  Every
+// call checks that the cached address is still a device allocation of the
+// current context (a cudaDeviceReset destroys the context and reloads the
+// module, possibly elsewhere) and looks it up again when it is not; neither
+// query allocates.
 int noalloc_scratch(float **out)
 {
     int dev = 0;
@@ -471,6 +475,14 @@ int noalloc_scratch(float **out)
     if (e != cudaSuccess) return trajam::report_error(AM_ERR_CUDA, cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return trajam::report_error(AM_ERR_ARG, "device index out of range");
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (g_noalloc_addr[dev]) {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, g_noalloc_addr[dev]) != cudaSuccess || at.type != cudaMemoryTypeDevice ||
+            at.device != dev) {
+            cudaGetLastError();  // a failed query leaves no error behind
+            g_noalloc_addr[dev] = nullptr;
+        }
+    }
     if (!g_noalloc_addr[dev]) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
@@ -506,6 +518,16 @@ extern "C" AM_API int am_solve_batch_noalloc(const am_problem *h, int B, float *
     }
     float *scratch = nullptr;
     rc = noalloc_scratch(&scratch);
+    if (rc) return rc;
+    // the handle's constants must live on the device whose area is used
+    int dev = 0;
+    cudaPointerAttributes at;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaPointerGetAttributes(&at, cblob) != cudaSuccess ||
+        at.type != cudaMemoryTypeDevice || at.device != dev) {
+        cudaGetLastError();
+        return report_error(AM_ERR_ARG, "the handle's constants are not on the current device");
+    }
+    rc = handle_order_before(h, stream);
     if (rc) return rc;
     SolveArgs a;
     a.cblob = cblob;

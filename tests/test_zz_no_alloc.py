@@ -73,3 +73,42 @@ def test_noalloc_rejects_batches_beyond_the_fixed_area():
     assert e.value.code == T.AM_ERR_BUDGET
     assert "32 MiB" in str(e.value)
     P.close()
+
+
+def test_noalloc_orders_itself_after_the_handles_stream():
+    """The handle works on its own non-blocking stream and the caller solves on
+    another: the call waits for what the handle's stream has queued (an event
+    the handle owns, recorded there), so obstacles replaced just before the
+    call are the ones the solve sees.  Checked against the allocating entry
+    point solving the same scene after a full synchronisation."""
+    import torch
+    from paper_2109_13030_b300 import trajam as T
+    pb = W.make_problem("paper", 8, B=128)
+    other = W.make_problem("paper", 9, B=128)  # different obstacles
+    B, iters = pb["B"], 20
+    s0 = cold_state(pb["init"].astype(np.float32))
+    obs = [np.ascontiguousarray(other[k], dtype=np.float32) for k in ("xo", "yo", "ao", "bo")]
+
+    R = T.Problem(dict(pb, xo=other["xo"], yo=other["yo"], ao=other["ao"], bo=other["bo"]),
+                  kernel=T.AM_KERNEL_PLAIN)
+    T.am_set_state(R.h, B, s0)
+    R.B = B
+    R.solve(None, iters)
+    ref_state, ref = R.state(), R.results()
+    R.close()
+
+    s_handle, s_call = torch.cuda.Stream(), torch.cuda.Stream()
+    P = T.Problem(pb)
+    state = torch.tensor(s0, device="cuda")
+    outs = [torch.full((B,), float("nan"), device="cuda") for _ in range(4)]
+    torch.cuda.synchronize()
+    T.am_set_stream(P.h, s_handle)
+    T.am_set_obstacles(P.h, other["n"], *obs)  # queued on the handle's stream
+    T.am_solve_batch_noalloc(P.h, B, state, *outs, iters, s_call)
+    s_call.synchronize()
+    st = state.cpu().numpy().astype(np.float64)
+    err = np.max(np.abs(st - ref_state), axis=1) / np.maximum(np.max(np.abs(ref_state), axis=1), 1.0)
+    assert err.max() <= COEF_TOL, err.max()
+    np.testing.assert_allclose(outs[2].cpu().numpy(), ref["cost"], rtol=1e-3)
+    T.am_set_stream(P.h, None)
+    P.close()
