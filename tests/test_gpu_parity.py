@@ -79,18 +79,30 @@ def noisy_oracle_spread(pb, iters, segments=10, eps=1e-6, reps=2, seed=11):
     return clean, spread
 
 
-def assert_final(g, o, idx=None, spread=None):
-    """Final cost, residual and distance within the stated tolerances; with
-    spread (from noisy_oracle_spread) each bound also admits three times the
-    oracle's own movement under FP32-sized noise on that trajectory."""
+def assert_final(g, o, idx=None, spread=None, label="final"):
+    """Final cost, residual and smallest distance within the stated tolerances.
+
+    Every trajectory is held to the plain bound, except where FP32-sized noise
+    moves the FP64 oracle itself by a third of the tolerance or more (spread,
+    from noisy_oracle_spread: the run crosses a transition of the projections
+    late, where the fixed-rho iteration amplifies rounding); such a trajectory
+    may exceed the plain bound by at most three times that movement.  The
+    counts are printed and returned."""
     sel = slice(None) if idx is None else idx
-    sp = spread or {k: 0.0 for k in ("cost", "res", "mind")}
-    dc = np.abs(g["cost"][sel] - o["cost"])
-    assert np.all(dc <= COST_TOL * np.abs(o["cost"]) + 3 * sp["cost"]), (dc / np.abs(o["cost"])).max()
-    dr = np.abs(g["res"][sel] - o["res"])
-    assert np.all(dr <= RES_RTOL * o["res"] + RES_ATOL + 3 * sp["res"]), (dr - RES_RTOL * o["res"]).max()
-    dm = np.abs(g["mind"][sel] - o["mind"])
-    assert np.all(dm <= 1e-3 * np.maximum(1.0, o["mind"]) + 3 * sp["mind"]), dm.max()
+    sp = spread or {k: np.zeros_like(o[k]) for k in ("cost", "res", "mind")}
+    checks = (("cost", np.abs(g["cost"][sel] - o["cost"]), COST_TOL * np.abs(o["cost"])),
+              ("res", np.abs(g["res"][sel] - o["res"]), RES_RTOL * o["res"] + RES_ATOL),
+              ("mind", np.abs(g["mind"][sel] - o["mind"]), 1e-3 * np.maximum(1.0, o["mind"])))
+    counts = {}
+    for name, d, tol in checks:
+        plain = d <= tol
+        allowed = (sp[name] >= tol / 3) & (d <= tol + 3 * sp[name])
+        counts[name] = (int(plain.sum()), int((~plain & allowed).sum()), len(d))
+        print(f"{label} {name}: {counts[name][0]}/{len(d)} within the plain bound, "
+              f"{counts[name][1]} within the sensitivity allowance")
+        bad = ~(plain | allowed)
+        assert not bad.any(), (name, np.nonzero(bad)[0], (d / tol)[bad])
+    return counts
 
 
 def sub_problem(pb, idx):
@@ -130,23 +142,21 @@ def test_paper_shape_full_batch_sampled(seed):
     assert_coefs(g10, o10, idx)
     g100 = gpu_solve(pb, 100)
     o100, spread = noisy_oracle_spread(sub_problem(pb, idx), 100)
-    assert_final(g100, o100, idx, spread=spread)
+    counts = assert_final(g100, o100, idx, spread=spread, label=f"paper seed {seed}")
+    for name, (plain, allowed, n) in counts.items():
+        assert plain == n, (name, plain, allowed)
 
 
 def test_paper_shape_all_trajectories_after_100():
-    """Every one of 64 paper-shaped trajectories after 100 iterations.  Past the
-    5-10 iterations the paper reports, the fixed-rho iteration on moving
-    ellipses is sensitive: FP32-sized noise moves the FP64 oracle itself by up
-    to ~2e-3 in cost on single trajectories (one of these 64 crosses a
-    transition near iteration 80).  The bound is 1e-3 relative plus three times
-    that measured movement, per trajectory; at least 90% of the trajectories
-    are held to the plain 1e-3."""
+    """Every one of 64 paper-shaped trajectories after 100 iterations within
+    the plain bound (1e-3 on cost and residual), with no allowance: the noise
+    spread is measured and printed, but none of these trajectories may use it."""
     pb = W.make_problem("paper", 0, B=64)
     g = gpu_solve(pb, 100)
     o, spread = noisy_oracle_spread(pb, 100)
-    assert_final(g, o, spread=spread)
-    plain = np.abs(g["cost"] - o["cost"]) <= COST_TOL * np.abs(o["cost"])
-    assert plain.mean() >= 0.9
+    counts = assert_final(g, o, spread=spread, label="paper B=64")
+    for name, (plain, allowed, n) in counts.items():
+        assert plain == n, (name, plain, allowed)
 
 
 def test_paper_shape_plain_sampled():
