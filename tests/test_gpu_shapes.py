@@ -3,8 +3,8 @@ fused kernel holds in shared memory, the maximum shape (q = 256, m = 4,
 n = 64) on the plain kernel, and the shapes that are rejected.
 
 The fused kernel stages a problem's constants in shared memory; the largest
-shapes (q = 200 with 64 obstacles, q = 256 with 32 or more) do not fit and
-are refused with AM_ERR_ARG, naming the plain kernel, which runs any shape.
+shapes (q = 256 with more than 45 obstacles) do not fit and are refused with
+AM_ERR_ARG, naming the plain kernel, which runs any shape.
 Tolerances against the oracle follow the mixed-problem rule (the larger of
 1e-4 and three times the oracle's own movement under FP32-sized noise).
 """
@@ -50,7 +50,7 @@ def test_singular_horizon_rejected():
     assert e.value.code == T.AM_ERR_ARG and "singular" in str(e.value)
 
 
-@pytest.mark.parametrize("q,n,m", [(150, 64, 4), (200, 32, 4), (256, 10, 4), (50, 64, 1)])
+@pytest.mark.parametrize("q,n,m", [(150, 64, 4), (200, 64, 4), (256, 32, 4), (256, 45, 2), (50, 64, 1)])
 def test_largest_fused_shapes(q, n, m):
     pb = W.make_shape(5, B=6, q=q, n=n, m=m)
     o, tol = coef_tolerance(pb, 5)
