@@ -292,9 +292,9 @@ def bench_uneven(TJ, W, torch, dev, flush, steps: int, iters: int = 100) -> dict
 
 
 def bench_precision(TJ, W, torch, dev, flush, steps: int, iters: int = 100) -> dict:
-    """The paper-shaped scene at B = 4096 in the three precision forms: FP32
-    (three TF32 products per contraction), and one TF32 or BF16 product for
-    the contractions over the time grid.  Reports the fused kernel's time and
+    """The paper-shaped scene at B = 4096 in the four precision forms of the
+    contraction R: FP32 (three TF32 products), one TF32 or BF16 product, and
+    split BF16 (three BF16 products of K = 16).  Reports the fused kernel's time and
     each reduced form's coefficient deviation from the FP32 form after 10
     iterations (the error against the FP64 oracle is measured by the tests)."""
     pb = W.make_problem("precision", 0)
@@ -302,7 +302,8 @@ def bench_precision(TJ, W, torch, dev, flush, steps: int, iters: int = 100) -> d
     init = torch.tensor(pb["init"], dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
     out, ref = {}, None
-    for prec, name in ((TJ.AM_FP32, "fp32"), (TJ.AM_TF32, "tf32"), (TJ.AM_BF16, "bf16")):
+    for prec, name in ((TJ.AM_FP32, "fp32"), (TJ.AM_TF32, "tf32"), (TJ.AM_BF16, "bf16"),
+                       (TJ.AM_SPLIT_BF16, "split_bf16")):
         P = TJ.Problem(pb, precision=prec)
         P.solve(init, 10, stream=stream)
         xi = P.state()[:, :55].astype(np.float64)

@@ -58,13 +58,16 @@ extern "C" {
 /* Precision of the fused kernel's tensor-core contraction over the time grid
  * (R = F^T (g - F xi1)): AM_FP32 takes three TF32 products per product
  * (hi*hi + hi*lo + lo*hi, FP32 accuracy); AM_TF32 and AM_BF16 take one
- * product of operands rounded to TF32 or BF16 (the reduced-precision form).
- * The position and heading steps are FP32 in every form.  Groups run each
- * problem in its own precision; the plain kernel and the allocation-free
- * entry run FP32 only. */
+ * product of operands rounded to TF32 or BF16 (the reduced-precision form);
+ * AM_SPLIT_BF16 splits each operand into BF16 hi + lo (16 significant bits)
+ * and takes three BF16 products of K = 16 (half the tensor-core
+ * instructions of AM_FP32).  The position and heading steps are FP32 in
+ * every form.  Groups run each problem in its own precision; the plain
+ * kernel and the allocation-free entry run FP32 only. */
 #define AM_FP32 0
 #define AM_TF32 1
 #define AM_BF16 2
+#define AM_SPLIT_BF16 3
 
 #define AM_KERNEL_FUSED 0   /* one launch runs every iteration (default)     */
 #define AM_KERNEL_PLAIN 1   /* one launch per step, intermediates in memory  */

@@ -214,7 +214,8 @@ int am_init_problem(const am_problem_desc *d, am_problem **out)
         return fail(AM_ERR_ARG, "r_c >= 0 and v_max, a_max, rho, rho_psi > 0 required");
     if (!finite_all(d->x_bc, 6) || !finite_all(d->y_bc, 6) || !finite_all(d->psi_bc, 6))
         return fail(AM_ERR_ARG, "non-finite boundary condition");
-    if (d->precision != AM_FP32 && d->precision != AM_TF32 && d->precision != AM_BF16)
+    if (d->precision != AM_FP32 && d->precision != AM_TF32 && d->precision != AM_BF16 &&
+        d->precision != AM_SPLIT_BF16)
         return fail(AM_ERR_ARG, "precision %d not available", d->precision);
     if (d->alpha_mode < 0 || d->alpha_mode > 1 || d->psi_dual_sign < 0 || d->psi_dual_sign > 1 ||
         d->cs_boundary < 0 || d->cs_boundary > 1)

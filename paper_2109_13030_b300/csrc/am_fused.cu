@@ -230,6 +230,38 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const float (&a)[4], flo
         : "r"(a01), "r"(a23), "r"(b));
 }
 
+// Split BF16 (AM_SPLIT_BF16): x = hi + lo with hi = bf16(x), lo = bf16(x - hi)
+// (16 significant bits), two values packed per register as the mma operands
+// want them (the first value in the low half).
+__device__ __forceinline__ void split_bf16x2(float x0, float x1, uint32_t &hi, uint32_t &lo)
+{
+    hi = pack_bf16(x0, x1);
+    const float h0 = __uint_as_float(hi << 16), h1 = __uint_as_float(hi & 0xFFFF0000u);
+    lo = pack_bf16(x0 - h0, x1 - h1);
+}
+
+// D += A B, m16n8k16 with BF16 operands (a: rows g, g + 8 at k 2t, 2t + 1,
+// then at k 2t + 8, 2t + 9; b: k 2t, 2t + 1, then 2t + 8, 2t + 9 at column g).
+__device__ __forceinline__ void mma_bf16_k16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                             uint32_t b0, uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// The same with K = 8 (a: rows g, g + 8 at k 2t, 2t + 1; b: k 2t, 2t + 1).
+__device__ __forceinline__ void mma_bf16_k8(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t b0)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(b0));
+}
+
 // One 16x8x8 step of D += A B on operands split into TF32 (hi, lo) pairs
 // (the constants on the host, the residual rows and heading increments by
 // the phases that produce them, so the tensor-core phases only load).
@@ -465,6 +497,62 @@ __device__ void phase_dot(const KParams &p, float *sm, const Smem &S, const Tile
         float d0[4] = {0.f, 0.f, 0.f, 0.f}, d2[4] = {0.f, 0.f, 0.f, 0.f};
         float e0[4] = {0.f, 0.f, 0.f, 0.f}, e2[4] = {0.f, 0.f, 0.f, 0.f};
         const int k0 = part * per, k1 = min(nks, k0 + per);
+        if constexpr (PR == 3) {
+            // split BF16: pairs of k-steps as one K = 16 product; lane tq takes
+            // the four consecutive steps 4 tq .. 4 tq + 3 of the pair (k 2tq,
+            // 2tq + 1 and 2tq + 8, 2tq + 9 of the product), in A and B alike
+            int ks = k0;
+#pragma unroll 1
+            for (; ks + 2 <= k1; ks += 2) {
+                const int c = ks * 8 + 4 * tq;
+                const float4 x0 = *reinterpret_cast<const float4 *>(a_lo + c);  // row g (side x)
+                const float4 x1 = *reinterpret_cast<const float4 *>(a_hi + c);  // row g + 8 (side y)
+                uint32_t ah[4], al[4];
+                split_bf16x2(x0.x, x0.y, ah[0], al[0]);
+                split_bf16x2(x1.x, x1.y, ah[1], al[1]);
+                split_bf16x2(x0.z, x0.w, ah[2], al[2]);
+                split_bf16x2(x1.z, x1.w, ah[3], al[3]);
+#pragma unroll
+                for (int nt = 0; nt < 2; ++nt) {
+                    // the basis column as stored: TF32 (hi, lo) pairs; their sum is exact in FP32
+                    const uint4 p0 = *reinterpret_cast<const uint4 *>((nt ? bc1 : bc0) + c);
+                    const uint4 p1 = *reinterpret_cast<const uint4 *>((nt ? bc1 : bc0) + c + 2);
+                    const float b0 = __uint_as_float(p0.x) + __uint_as_float(p0.y);
+                    const float b1 = __uint_as_float(p0.z) + __uint_as_float(p0.w);
+                    const float b2 = __uint_as_float(p1.x) + __uint_as_float(p1.y);
+                    const float b3 = __uint_as_float(p1.z) + __uint_as_float(p1.w);
+                    uint32_t bh0, bl0, bh1, bl1;
+                    split_bf16x2(b0, b1, bh0, bl0);
+                    split_bf16x2(b2, b3, bh1, bl1);
+                    float (&dc)[4] = nt ? e0 : d0;
+                    float (&dh)[4] = nt ? e2 : d2;
+                    mma_bf16_k16(dc, al[0], al[1], al[2], al[3], bh0, bh1);
+                    mma_bf16_k16(dc, ah[0], ah[1], ah[2], ah[3], bl0, bl1);
+                    mma_bf16_k16(dh, ah[0], ah[1], ah[2], ah[3], bh0, bh1);
+                }
+            }
+            if (ks < k1) {
+                // an odd last k-step: one K = 8 product per split term
+                const int c0 = ks * 8 + 2 * tq;
+                const float2 lo = *reinterpret_cast<const float2 *>(a_lo + c0);
+                const float2 hi = *reinterpret_cast<const float2 *>(a_hi + c0);
+                uint32_t ah0, al0, ah1, al1;
+                split_bf16x2(lo.x, lo.y, ah0, al0);
+                split_bf16x2(hi.x, hi.y, ah1, al1);
+#pragma unroll
+                for (int nt = 0; nt < 2; ++nt) {
+                    const uint4 p0 = *reinterpret_cast<const uint4 *>((nt ? bc1 : bc0) + c0);
+                    uint32_t bh, bl;
+                    split_bf16x2(__uint_as_float(p0.x) + __uint_as_float(p0.y),
+                                 __uint_as_float(p0.z) + __uint_as_float(p0.w), bh, bl);
+                    float (&dc)[4] = nt ? e0 : d0;
+                    float (&dh)[4] = nt ? e2 : d2;
+                    mma_bf16_k8(dc, al0, al1, bh);
+                    mma_bf16_k8(dc, ah0, ah1, bl);
+                    mma_bf16_k8(dh, ah0, ah1, bh);
+                }
+            }
+        } else {
 #pragma unroll 1
         for (int ks = k0; ks < k1; ++ks) {
             const int c0 = ks * 8 + 2 * tq;
@@ -477,6 +565,7 @@ __device__ void phase_dot(const KParams &p, float *sm, const Smem &S, const Tile
             ld_pair2(bc1 + c0, b2, b3);
             mma_pairs<PR>(d0, d0, d2, ap, b0, b1);
             mma_pairs<PR>(e0, e0, e2, ap, b2, b3);
+        }
         }
         if (g < tl.count) {
             float *R = sm + S.rb + (seg < 3 ? kDotParts * seg + part : part) * S.T * 48 + g * 48;
@@ -1120,6 +1209,7 @@ int launch_group(const GroupLaunch &g, void *stream, int *launches, const char *
         AM_GCASES(0)
         AM_GCASES(1)
         AM_GCASES(2)
+        AM_GCASES(3)
 #undef AM_GCASES
 #undef AM_GCASE
     default:
@@ -1249,6 +1339,7 @@ int launch_fused(const SolveArgs &a, void *stream, int *launches)
         AM_CASES(0)
         AM_CASES(1)
         AM_CASES(2)
+        AM_CASES(3)
 #undef AM_CASES
 #undef AM_CASE
     default:

@@ -115,8 +115,9 @@ struct ConstLayout {
     float psi_sign;           // +1 default reading, -1 printed sign
     int alpha_mode;
     int cs_boundary;          // slack blocks carry boundary rows
-    int precision;            // contractions over the time grid: 0 FP32 (three TF32
-                              // products), 1 one TF32 product, 2 one BF16 product
+    int precision;            // the contraction R: 0 FP32 (three TF32 products), 1 one
+                              // TF32 product, 2 one BF16 product, 3 split BF16 (three
+                              // BF16 products of K = 16)
     int diag_stall;           // diagnostic: stage without the copy, so the bounded
                               // wait on it runs out (failure-detection tests)
     int select;               // best selection among colliding trajectories:
@@ -162,7 +163,7 @@ constexpr float kNearMargin = 0.6f;
 // Grouped launch: many problems' tiles in persistent kernels, one kernel per
 // variant (circle count, alpha form) present; the variant kernels of one
 // solve run concurrently.
-constexpr int kGroupVariants = 24;  // precision (3) x circle count (4) x alpha form (2)
+constexpr int kGroupVariants = 32;  // precision (4) x circle count (4) x alpha form (2)
 struct GroupLaunch {
     const FusedProblem *d_probs;  // device array, one per problem
     const int *d_items;           // device array of (problem, tile) pairs, all variants

@@ -1,14 +1,17 @@
-"""Reduced-precision forms (AM_TF32, AM_BF16) on the 4096-trajectory
-paper-shaped workload, against the FP64 oracle on sampled trajectories.
+"""Reduced-precision forms (AM_TF32, AM_BF16, AM_SPLIT_BF16) on the
+4096-trajectory paper-shaped workload, against the FP64 oracle on sampled
+trajectories.
 
 In these forms the tensor-core contraction over the time grid, R = F^T (g -
 F xi1), takes one product of operands rounded to TF32 (unit roundoff u =
-2^-11) or BF16 (u = 2^-8); the position and heading steps stay FP32.  The error is a reported
-property of the form, not an FP32 parity bar: after 10 iterations the
-coefficients are measured within ~7 u (TF32) and ~17 u (BF16) of the oracle
-and the cost within ~1 u and ~2.5 u.  The bounds below are 30 u on
-coefficients and 10 u on the cost; an implementation mistake (a wrong
-fragment layout, a dropped term) gives errors of order one.
+2^-11) or BF16 (u = 2^-8), or three BF16 products of operands split into
+hi + lo (split BF16, u = 2^-16); the position and heading steps stay FP32.
+The error is a reported property of the form, not an FP32 parity bar: after
+10 iterations the coefficients are measured within ~6 u (TF32), ~17 u (BF16)
+and ~7 u (split BF16) of the oracle, and the cost within ~1 u, ~2 u and
+~0.5 u.  The bounds below are 30 u on coefficients and 10 u on the cost; an
+implementation mistake (a wrong fragment layout, a dropped term) gives
+errors of order one.
 """
 import numpy as np
 import pytest
@@ -20,7 +23,7 @@ from test_gpu_parity import COEF_TOL, coef_err, sub_problem
 
 pytestmark = pytest.mark.gpu
 
-U = {1: 2.0 ** -11, 2: 2.0 ** -8}
+U = {1: 2.0 ** -11, 2: 2.0 ** -8, 3: 2.0 ** -16}
 
 
 def tj():
@@ -45,7 +48,7 @@ def solve(pb, precision, iters=10):
     return out
 
 
-@pytest.mark.parametrize("precision", [1, 2])
+@pytest.mark.parametrize("precision", [1, 2, 3])
 def test_reduced_precision_error_bound(workload, precision):
     pb, idx, o = workload
     g = solve(pb, precision)
