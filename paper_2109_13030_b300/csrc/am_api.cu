@@ -115,6 +115,15 @@ int wait_event(cudaEvent_t ev, cudaStream_t st)
     }
 }
 
+// A kernel's status word: bit 0 a bounded wait that gave up, bit 1 an index
+// outside its array caught by the debug build's checks.
+int status_error(int err)
+{
+    if (err & 2) return fail(AM_ERR_STATE, "a kernel index was out of bounds (debug build; status %d)", err);
+    if (err) return fail(AM_ERR_TIMEOUT, "a kernel gave up a bounded wait (status %d)", err);
+    return AM_OK;
+}
+
 int wait_stream(am_problem *h)
 {
     // the status word rides on the same stream into pinned memory, so one
@@ -123,9 +132,7 @@ int wait_stream(am_problem *h)
     CK(cudaMemcpyAsync(h_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "status read");
     int rc = wait_event(h->ev, h->stream);
     if (rc) return rc;
-    const int err = *h_err;
-    if (err) return fail(AM_ERR_TIMEOUT, "a kernel gave up a bounded wait (status %d)", err);
-    return AM_OK;
+    return status_error(*h_err);
 }
 
 cudaMemcpyKind kind_in(int mem) { return mem == AM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; }
@@ -1268,8 +1275,7 @@ int problem_status_async(::am_problem *h, void *stream)
 
 int problem_status(const ::am_problem *h)
 {
-    const int err = reinterpret_cast<const int *>(h->h_best + 40)[0];
-    return err ? fail(AM_ERR_TIMEOUT, "a kernel gave up a bounded wait (status %d)", err) : AM_OK;
+    return status_error(reinterpret_cast<const int *>(h->h_best + 40)[0]);
 }
 
 }  // namespace trajam

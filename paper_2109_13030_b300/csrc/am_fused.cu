@@ -82,6 +82,18 @@ struct Smem {
     int cst, cob, xi1, lam, rb, xi2, dx2, lps, ptp, G2, RS, GX, U, PTD, XD, X2D, bar, total, T;
 };
 
+// Debug build (-DAM_DEBUG_BOUNDS, libtrajam_debug.so): every checked index
+// outside its array sets the block's flag and the access is skipped; at the
+// end of a tile the flag becomes bit 2 of the problem's status word, which
+// the host reports as AM_ERR_STATE.  There is no trap.  In the release build
+// the checks compile to nothing.
+#ifdef AM_DEBUG_BOUNDS
+__shared__ int g_oob;
+#define AM_BOUND(cond) ((cond) ? true : (g_oob = 1, false))
+#else
+#define AM_BOUND(cond) true
+#endif
+
 // Shared-memory layout (float offsets).
 //   cst region [off_fused, off_obs) of the constant block (shape sections);
 //   cob region [off_obt, total) (near thresholds, paired obstacle sections)
@@ -370,6 +382,7 @@ __device__ __forceinline__ int dpos(int blk) { return blk == 0 ? 0 : blk == 2 ? 
 // buffer buf, and its duplicate.
 __device__ __forceinline__ void put_xi1(float *sm, const Smem &S, int buf, int tt, int o, float v)
 {
+    if (!AM_BOUND(buf >= 0 && buf < 2 && tt >= 0 && tt < S.T && o >= 0 && o < 48)) return;
     sm[S.xi1 + (buf * S.T + tt) * 48 + o] = v;
     const int blk = o / 12, k = o - 12 * blk;
     reinterpret_cast<float2 *>(sm + S.XD)[((buf * S.T + tt) * 12 + k) * 4 + dpos(blk)] = make_float2(v, v);
@@ -378,6 +391,7 @@ __device__ __forceinline__ void put_xi1(float *sm, const Smem &S, int buf, int t
 // The same for coefficient k of trajectory tt's xi2.
 __device__ __forceinline__ void put_xi2(float *sm, const Smem &S, int buf, int tt, int k, float v)
 {
+    if (!AM_BOUND(buf >= 0 && buf < 2 && tt >= 0 && tt < S.T && k >= 0 && k < 12)) return;
     sm[S.xi2 + (buf * S.T + tt) * 12 + k] = v;
     reinterpret_cast<float2 *>(sm + S.X2D)[(buf * S.T + tt) * 12 + k] = make_float2(v, v);
 }
@@ -485,6 +499,7 @@ __device__ void phase_dot(const KParams &p, float *sm, const Smem &S, const Tile
     const int row = frag_row4(g, tl.count);
     for (int task = warp; task < 4 * kDotParts; task += blockDim.x >> 5) {
         const int seg = task / kDotParts, part = task - kDotParts * seg;
+        if (!AM_BOUND(8 * nks <= L.qp && row < S.T)) continue;  // operand columns within a segment
         const int bsel = seg == 0 ? 1 : seg == 1 ? 2 : 0;  // Pd, Pdd, P, P
         const uint2 *B = reinterpret_cast<const uint2 *>(sm + S.cst + L.off_pcol2) + bsel * NV * L.qp;
         // n-tile 1 holds columns 8..10; its other lanes give discarded
@@ -889,6 +904,7 @@ __device__ __forceinline__ void sweep_pair(float *sm, const Smem &S, const Const
         }
     }
     const int qs = L.qs, qp = L.qp;
+    if (!AM_BOUND(tt >= 0 && tt < S.T && t0 >= 0 && t0 + 1 < qp && t0 + 1 < qs)) return;
     float *Gx = sm + S.G2 + tt * S.RS + t0;   // side x: row tt
     float *Gy = Gx + S.T * S.RS;              // side y: row T + tt
     const float2 svm = f2(sv.x - 1.f, sv.y - 1.f), sam = f2(sa.x - 1.f, sa.y - 1.f);
@@ -973,8 +989,13 @@ __device__ void run_tile(const KParams &p, float *sm, const Smem &S, const Tile 
     const ConstLayout &L = p.L;
     const int Tn = tl.count;
     // The tile's state: xi1, xi2 as given into buffer 1, multipliers into buffer 0.
+#ifdef AM_DEBUG_BOUNDS
+    if (threadIdx.x == 0) g_oob = 0;
+    __syncthreads();
+#endif
     for (int i = threadIdx.x; i < Tn * STATE; i += blockDim.x) {
         const int tt = i / STATE, e = i - STATE * tt;
+        if (!AM_BOUND(tl.first >= 0 && tl.first + Tn <= p.B && Tn <= p.T)) break;
         const float v = p.state[(size_t)tl.first * STATE + i];
         if (e < 44) put_xi1(sm, S, 1, tt, (e / NV) * 12 + e % NV, v);
         else if (e < 55) put_xi2(sm, S, 1, tt, e - 44, v);
@@ -1046,10 +1067,12 @@ __device__ void run_tile(const KParams &p, float *sm, const Smem &S, const Tile 
                 pk[k] = m.x + m.y;
             }
             pk[11] = 0.f;
-            float4 *dst = reinterpret_cast<float4 *>(sm + S.PTD + (tt * np + jp) * 12);
-            dst[0] = make_float4(pk[0], pk[1], pk[2], pk[3]);
-            dst[1] = make_float4(pk[4], pk[5], pk[6], pk[7]);
-            dst[2] = make_float4(pk[8], pk[9], pk[10], pk[11]);
+            if (AM_BOUND(tt < S.T && jp < np)) {
+                float4 *dst = reinterpret_cast<float4 *>(sm + S.PTD + (tt * np + jp) * 12);
+                dst[0] = make_float4(pk[0], pk[1], pk[2], pk[3]);
+                dst[1] = make_float4(pk[4], pk[5], pk[6], pk[7]);
+                dst[2] = make_float4(pk[8], pk[9], pk[10], pk[11]);
+            }
         }
         __syncthreads();
         phase_psi(p, sm, S, tl, cur2);
@@ -1066,6 +1089,7 @@ __device__ void run_tile(const KParams &p, float *sm, const Smem &S, const Tile 
     __syncthreads();
     for (int i = threadIdx.x; i < Tn * STATE; i += blockDim.x) {
         const int tq = i / STATE, e = i - STATE * tq;
+        if (!AM_BOUND(tl.first >= 0 && tl.first + Tn <= p.B && Tn <= p.T)) break;
         float v;
         if (e < 44) v = sm[S.xi1 + (cur * p.T + tq) * 48 + (e / NV) * 12 + e % NV];
         else if (e < 55) v = sm[S.xi2 + (cur2 * p.T + tq) * 12 + (e - 44)];
@@ -1074,6 +1098,9 @@ __device__ void run_tile(const KParams &p, float *sm, const Smem &S, const Tile 
         p.state[(size_t)tl.first * STATE + i] = v;
     }
     __syncthreads();
+#ifdef AM_DEBUG_BOUNDS
+    if (threadIdx.x == 0 && g_oob) atomicOr(p.err, 2);
+#endif
 }
 
 template <int M, bool LIT, int PR>
@@ -1148,6 +1175,13 @@ am_group_kernel(const KParams *probs, const int *items, const int *head, int *ct
 // The group kernel's static shared memory (its problem descriptor) comes out
 // of the same 227 KB as the dynamic area.
 constexpr size_t kGroupSmemMax = 227 * 1024 - 512;
+// The single-problem kernel's dynamic area; the debug build's static flag
+// needs a little of the 227 KB.
+#ifdef AM_DEBUG_BOUNDS
+constexpr size_t kFusedSmemMax = 227 * 1024 - 512;
+#else
+constexpr size_t kFusedSmemMax = 227 * 1024;
+#endif
 
 size_t fused_smem_bytes(const ConstLayout &L, int tile)
 {
@@ -1158,7 +1192,7 @@ int fused_max_tile(const ConstLayout &L)
 {
     int tmax = kMaxThreads / pair_threads(L.q);
     if (tmax > kMaxTile) tmax = kMaxTile;
-    while (tmax > 1 && fused_smem_bytes(L, tmax) > 227 * 1024) --tmax;
+    while (tmax > 1 && fused_smem_bytes(L, tmax) > kFusedSmemMax) --tmax;
     return tmax < 1 ? 1 : tmax;
 }
 
@@ -1264,7 +1298,7 @@ int launch_variant(const KParams &p, int threads, size_t smem, int dev, int sms,
         std::lock_guard<std::mutex> lk(g_launch_mu);
         if (attr_dev != dev) {
             if (cudaFuncSetAttribute(am_fused_kernel<M, LIT, PR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     227 * 1024) != cudaSuccess)
+                                     int(kFusedSmemMax)) != cudaSuccess)
                 return -2;
             resident.clear();
             attr_dev = dev;
@@ -1301,7 +1335,7 @@ int launch_fused(const SolveArgs &a, void *stream, int *launches)
     const int tq = T * pair_threads(L.q);
     if (tq > kMaxThreads || T < 1 || T > kMaxTile) return -1;
     const size_t smem = fused_smem_bytes(L, T);
-    if (smem > 227 * 1024) return -1;
+    if (smem > kFusedSmemMax) return -1;
     // twelve warps whatever the tile: the tensor-core phases run all their tasks at once
     const int threads = kMaxThreads;
     const int ntiles = (a.B + T - 1) / T;

@@ -13,7 +13,8 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libtrajam.so")
+# TRAJAM_LIBRARY=libtrajam_debug.so selects the bounds-checking debug build
+LIB_PATH = os.path.join(HERE, os.environ.get("TRAJAM_LIBRARY", "libtrajam.so"))
 
 AM_OK, AM_ERR_ARG, AM_ERR_CUDA, AM_ERR_BUDGET, AM_ERR_TIMEOUT, AM_ERR_NAN, AM_ERR_STATE = 0, -1, -2, -3, -4, -5, -6
 AM_HOST, AM_DEVICE = 0, 1
