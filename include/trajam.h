@@ -71,6 +71,7 @@ extern "C" {
 
 #define AM_KERNEL_FUSED 0   /* one launch runs every iteration (default)     */
 #define AM_KERNEL_PLAIN 1   /* one launch per step, intermediates in memory  */
+#define AM_KERNEL_LARGE 2   /* fused, 128 trajectories per CTA on tcgen05    */
 
 #define AM_NV 11
 #define AM_STATE_FLOATS 110
@@ -234,7 +235,16 @@ AM_API int am_set_state(am_problem *h, int B, const float *in, int mem);
 AM_API int am_set_history(am_problem *h, int enable);
 AM_API int am_get_history(am_problem *h, float *out, int mem);
 
-/* Options.  AM_OPT_KERNEL: AM_KERNEL_FUSED or AM_KERNEL_PLAIN.
+/* Options.  AM_OPT_KERNEL: AM_KERNEL_FUSED, AM_KERNEL_PLAIN or
+ * AM_KERNEL_LARGE.  AM_KERNEL_LARGE is the batch matrix form of Sec. III-E
+ * (Eq. over_3) for large batches: one persistent CTA per SM runs every
+ * iteration for tiles of 128 trajectories, with the position step, the
+ * trajectory values, P^T delta and R as tcgen05 tensor-core products (three
+ * TF32 products each, FP32 accuracy) accumulated in tensor memory.  It takes
+ * the FP32 precision form, the default alpha form, q <= 128 and no history;
+ * am_solve_batch returns AM_ERR_ARG (nothing launched) for anything else or
+ * when the shape's operands exceed the shared memory of an SM.  Results
+ * agree with AM_KERNEL_FUSED to FP32 rounding, not bit for bit.
  * AM_OPT_TILE: trajectories per CTA of the fused kernel (0 = automatic).
  * AM_OPT_SELECT: the best-trajectory rule of am_get_best and of grouped
  * and served solves when no trajectory is collision-free.  AM_SELECT_COST

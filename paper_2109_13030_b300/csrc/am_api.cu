@@ -347,7 +347,8 @@ int am_set_option(am_problem *h, int option, int value)
 {
     if (!h) return fail(AM_ERR_ARG, "null handle");
     if (option == AM_OPT_KERNEL) {
-        if (value != AM_KERNEL_FUSED && value != AM_KERNEL_PLAIN) return fail(AM_ERR_ARG, "bad kernel");
+        if (value != AM_KERNEL_FUSED && value != AM_KERNEL_PLAIN && value != AM_KERNEL_LARGE)
+            return fail(AM_ERR_ARG, "bad kernel");
         h->kernel = value;
         return AM_OK;
     }
@@ -390,6 +391,11 @@ int am_solve_batch(am_problem *h, int B, const float *init, const float *warm_la
     if (!init && warm_lambda) return fail(AM_ERR_ARG, "warm_lambda needs init");
     if (h->kernel == AM_KERNEL_PLAIN && h->pp.precision != AM_FP32)
         return fail(AM_ERR_ARG, "reduced precision runs on the fused kernel only");
+    if (h->kernel == AM_KERNEL_LARGE && !large_supported(h->L, h->hist_on))
+        return fail(AM_ERR_ARG,
+                    "the large-batch kernel takes the FP32 form, the default alpha form, q <= 128, no history "
+                    "and operands within an SM's shared memory (q=%d, m=%d, n=%d: %zu bytes)",
+                    h->pp.q, h->pp.m, h->n, large_smem_bytes(h->L));
     if (mem == AM_HOST) {
         if (init && !finite_floats(init, size_t(B) * 33)) return fail(AM_ERR_ARG, "non-finite initial coefficients");
         if (warm_lambda && !finite_floats(warm_lambda, size_t(B) * 55)) return fail(AM_ERR_ARG, "non-finite warm multipliers");
@@ -434,6 +440,8 @@ int am_solve_batch(am_problem *h, int B, const float *init, const float *warm_la
     a.err = h->d_err;
     if (h->kernel == AM_KERNEL_FUSED) {
         rc = launch_fused(a, h->stream, &h->launches);
+    } else if (h->kernel == AM_KERNEL_LARGE) {
+        rc = launch_large(a, h->stream, &h->launches);
     } else {
         const size_t need = plain_scratch_floats(h->L, B);
         rc = ensure(h->d_scratch, h->scratch_cap, need, "plain scratch");

@@ -57,6 +57,8 @@
 #include <mutex>
 #include <utility>
 
+#include "am_async.cuh"
+#include "am_heading.cuh"
 #include "am_internal.h"
 
 namespace trajam {
@@ -68,8 +70,6 @@ constexpr int kDotParts = 2;      // parts of the steps per segment of R in the 
 constexpr int kRParts = 3 * kDotParts;  // partials of R: (rv | ra | r0 segment) x part of the steps
 constexpr int kMinPairThreads = 44;  // threads per trajectory at least (short horizons)
 
-constexpr float kTwoPi = 6.28318530717958647692f;
-constexpr float kPi = 3.14159265358979323846f;
 
 // Threads per trajectory: one per pair of consecutive steps.
 __host__ __device__ inline int pair_threads(int q)
@@ -154,43 +154,6 @@ __device__ __forceinline__ float rsum(const float *sm, const Smem &S, int i)
 }
 
 
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p)
-{
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-// Bulk async copy global -> shared, completion counted on an mbarrier.
-__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
-        :: "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ uint64_t global_ns()
-{
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Limit of the device-side wait for the constant copy: about a second of
-// the global timer (and an iteration cap behind it).
-constexpr uint64_t kWaitLimitNs = 1000000000ull;
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
 
 // ------------------------------------------------------------ tensor cores
 
@@ -326,38 +289,8 @@ __device__ __forceinline__ void split4(const float (&a)[4], uint2 (&ap)[4])
 
 // ------------------------------------------------------------------ small
 
-// atan2 for the heading target psi_t = atan2(s, c).  Octant reduction to
-// a = min(|x|, |y|) / max(|x|, |y|) in [0, 1], atan(a) = a P(a^2) with P of
-// degree 8 fitted for this kernel (iteratively reweighted least squares,
-// Lawson's method, on [0, 1]: relative error 1.5e-8 in exact arithmetic,
-// within 2 ulp when evaluated in FP32), then the octant is restored.
-// atan2(0, 0) = 0, the reading the method takes.
-__device__ __constant__ const float kAtanPoly[9] = {1.0f, -0.33333072f, 0.1999262f, -0.14203647f, 0.106409416f,
-                                                    -0.07504311f, 0.042691723f, -0.016068758f, 0.002849923f};
-
-__device__ __forceinline__ float atan2_heading(float y, float x)
-{
-    const float ax = fabsf(x), ay = fabsf(y);
-    const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
-    const float a = mx > 0.f ? __fdividef(mn, mx) : 0.f;
-    const float s = a * a;
-    float p = kAtanPoly[8];
-#pragma unroll
-    for (int k = 7; k >= 0; --k) p = fmaf(p, s, kAtanPoly[k]);
-    float r = a * p;
-    if (ay > ax) r = 1.57079637f - r;
-    if (x < 0.f) r = 3.14159274f - r;
-    return copysignf(r, y);  // the sign of y, -0 included (atan2(-0, -1) = -pi)
-}
-
 // Side-row r (0..21) of (c_pos, c_slack) -> padded index within a 24-float side block.
 __device__ __forceinline__ int rowpad(int r) { return r < NV ? r : r + 1; }
-
-// Wrap into (-pi, pi].
-__device__ __forceinline__ float wrap_pi(float a)
-{
-    return a - kTwoPi * ceilf((a - kPi) * (1.0f / kTwoPi));
-}
 
 struct Tile {
     int first, count;  // trajectories [first, first + count)
@@ -1175,13 +1108,6 @@ am_group_kernel(const KParams *probs, const int *items, const int *head, int *ct
 // The group kernel's static shared memory (its problem descriptor) comes out
 // of the same 227 KB as the dynamic area.
 constexpr size_t kGroupSmemMax = 227 * 1024 - 512;
-// The single-problem kernel's dynamic area; the debug build's static flag
-// needs a little of the 227 KB.
-#ifdef AM_DEBUG_BOUNDS
-constexpr size_t kFusedSmemMax = 227 * 1024 - 512;
-#else
-constexpr size_t kFusedSmemMax = 227 * 1024;
-#endif
 
 size_t fused_smem_bytes(const ConstLayout &L, int tile)
 {

@@ -145,6 +145,22 @@ struct SolveArgs {
 // Fused persistent kernel: every iteration of the loop in one launch.
 int launch_fused(const SolveArgs &a, void *stream, int *launches);
 
+// Large-batch fused kernel on the fifth-generation tensor cores (tiles of
+// 128 trajectories).  large_supported: 1 when the problem's form and shape
+// fit it (FP32 precision form, default alpha form, q <= 128, no history,
+// shared memory within the limit), else 0; launch_large returns -1 then.
+int large_supported(const ConstLayout &L, bool hist);
+size_t large_smem_bytes(const ConstLayout &L);
+int launch_large(const SolveArgs &a, void *stream, int *launches);
+
+// Dynamic shared memory of the single-problem kernels; the debug build's
+// static flag needs a little of the 227 KB.
+#ifdef AM_DEBUG_BOUNDS
+constexpr size_t kFusedSmemMax = 227 * 1024 - 512;
+#else
+constexpr size_t kFusedSmemMax = 227 * 1024;
+#endif
+
 // One problem as the fused kernels see it (also the element of the work
 // descriptor array of a grouped launch).
 struct FusedProblem {

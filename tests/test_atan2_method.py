@@ -1,8 +1,8 @@
-"""The fused kernel's atan2 for the heading target (octant reduction and a
+"""The fused kernels' atan2 for the heading target (octant reduction and a
 degree-8 polynomial in a^2), replayed step by step in float32 on the CPU and
 checked against FP64 arctan2: every octant, both axes, signed zeros, tiny and
 huge magnitudes, and atan2(0, 0) = 0.  The coefficients are read from the
-kernel source so the two cannot drift apart."""
+kernels' shared header so the two cannot drift apart."""
 import os
 import re
 
@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def coefficients():
-    src = open(os.path.join(ROOT, "paper_2109_13030_b300", "csrc", "am_fused.cu")).read()
+    src = open(os.path.join(ROOT, "paper_2109_13030_b300", "csrc", "am_heading.cuh")).read()
     body = re.search(r"kAtanPoly\[9\] = \{([^}]*)\}", src).group(1)
     return np.array([float(v.strip().rstrip("f")) for v in body.split(",")], dtype=np.float32)
 
