@@ -70,6 +70,31 @@ def measured_traffic():
     return int(t.group(1).replace(",", "")) + int(t.group(2).replace(",", ""))
 
 
+def large_profile():
+    """Tensor-pipe share and DRAM bytes per launch of the large-batch kernel
+    from its committed ncu summary, if taken on the current kernel source."""
+    import hashlib
+    import re
+    prof = os.path.join(ROOT, "profiles", "am_large_kernel_paper_b18944.md")
+    src = os.path.join(ROOT, "paper_2109_13030_b300", "csrc", "am_large.cu")
+    try:
+        text = open(prof).read()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    m = re.search(r"am_large.cu: `([0-9a-f]{16})`", text)
+    t = re.search(r"sm__pipe_tensor_cycles_active \| ([\d.]+) %", text)
+    d = re.search(r"dram__bytes_read.sum / write.sum \| ([\d,]+) B / ([\d,]+) B", text)
+    if not m or m.group(1) != sha:
+        return None
+    out = {}
+    if t:
+        out["tensor_pipe_pct"] = float(t.group(1))
+    if d:
+        out["traffic"] = int(d.group(1).replace(",", "")) + int(d.group(2).replace(",", ""))
+    return out or None
+
+
 def sig(x, n: int = 4):
     """x rounded to n significant digits (None and non-numbers unchanged)."""
     if isinstance(x, bool) or not isinstance(x, (int, float)) or x == 0 or not np.isfinite(x):
@@ -104,6 +129,13 @@ def summary_sections(extra: dict) -> dict:
         out["precision_b4096"] = {k: {"value": v["value"], **({"dev10": v["coef_dev_vs_fp32_after_10"]["max"]}
                                                               if "coef_dev_vs_fp32_after_10" in v else {})}
                                   for k, v in pr.items() if isinstance(v, dict)}
+    if "large" in extra:
+        lg = extra["large"]
+        out["large_batch"] = {k: {"large": v["large"]["value"], "small_tile": v["small_tile"]["value"],
+                                  "large_ms": v["large"]["kernel_ms"], "frac": v["large"]["frac_of_fp32_peak"]}
+                              for k, v in lg.items() if k.startswith("B=")}
+        if lg.get("profile"):
+            out["large_batch"]["profile"] = lg["profile"]
     if "serving" in extra:
         sv = extra["serving"]
         pq = lambda r: [r["p50_ms"], r["p99_ms"]]
@@ -330,6 +362,46 @@ def bench_precision(TJ, W, torch, dev, flush, steps: int, iters: int = 100) -> d
     return out
 
 
+def bench_large(TJ, W, torch, dev, flush, steps: int, iters: int = 100) -> dict:
+    """The large-batch kernel (AM_KERNEL_LARGE: 128 trajectories per CTA, the
+    contractions on tcgen05 tensor cores) on the paper-shaped scene at B =
+    16384 and at one full wave (128 trajectories per SM), beside the
+    small-tile fused kernel on the same batch.  Times are CUDA events around
+    the solve on its stream, the initial state re-made and L2 flushed before
+    each."""
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = peak_fp32_tflops(sms)
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    for Bl in (16384, 128 * sms):
+        pb = W.make_problem("paper", 0, B=Bl)
+        init = torch.tensor(pb["init"], dtype=torch.float32, device=dev)
+        row = {}
+        for kern, name in ((TJ.AM_KERNEL_LARGE, "large"), (TJ.AM_KERNEL_FUSED, "small_tile")):
+            P = TJ.Problem(pb, kernel=kern)
+            ms = []
+            for i in range(steps + 2):
+                flush.fill_(float(i))
+                P.init_state(init, stream=stream)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                TJ.am_solve_batch(P.h, Bl, None, None, iters, stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            res_med = float(np.median(P.results()["res"]))
+            P.close()
+            k_ms = statistics.mean(ms[2:])
+            row[name] = {"value": Bl * iters / (k_ms / 1e3), "kernel_ms": k_ms, "res_median": res_med}
+        achieved = algorithmic_flops(pb["q"], pb["m"], pb["n"]) * Bl * iters / (row["large"]["kernel_ms"] / 1e3) / 1e12
+        row["large"]["achieved_tflops"] = achieved
+        row["large"]["frac_of_fp32_peak"] = achieved / peak
+        out[f"B={Bl}"] = row
+    out["profile"] = large_profile()
+    out["workload"] = "paper-shaped scene, 100 iterations per timed solve"
+    return out
+
+
 def serve_run(TJ, W, pbs, mode, kernel, seconds, warmup_s=1.0, rate=400.0, iters=30, seed=7):
     """One serving run: 64 resident scenes, Poisson arrivals at `rate`/s for
     warmup_s + seconds; each request picks a scene uniformly, moves its
@@ -500,6 +572,8 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=3)
     ap.add_argument("--uneven-steps", type=int, default=3)
     ap.add_argument("--precision-steps", type=int, default=3)
+    ap.add_argument("--large-steps", type=int, default=3,
+                    help="timed solves per kernel of the large-batch section (0 skips it)")
     ap.add_argument("--jsonl", default=None, help="also append the JSON line to this file")
     ap.add_argument("--mpc-episodes", type=int, default=0,
                     help="closed-loop episodes per crowd benchmark (0: skip; the study takes minutes)")
@@ -626,6 +700,8 @@ def main():
             extra["uneven"] = bench_uneven(TJ, W, torch, dev, flush, args.uneven_steps)
         if args.precision_steps > 0:
             extra["precision"] = bench_precision(TJ, W, torch, dev, flush, args.precision_steps)
+        if args.large_steps > 0:
+            extra["large"] = bench_large(TJ, W, torch, dev, flush, args.large_steps)
         if args.serve_seconds > 0:
             extra["serving"] = bench_serving(TJ, W, args.serve_seconds, args.serve_plain_seconds)
         if args.mpc_episodes > 0:
