@@ -72,6 +72,8 @@ extern "C" {
 #define AM_KERNEL_FUSED 0   /* one launch runs every iteration (default)     */
 #define AM_KERNEL_PLAIN 1   /* one launch per step, intermediates in memory  */
 #define AM_KERNEL_LARGE 2   /* fused, 128 trajectories per CTA on tcgen05    */
+#define AM_KERNEL_WARP 3    /* fused, two warps per trajectory, no block     */
+                            /* barriers in the loop                          */
 
 #define AM_NV 11
 #define AM_STATE_FLOATS 110
@@ -235,8 +237,8 @@ AM_API int am_set_state(am_problem *h, int B, const float *in, int mem);
 AM_API int am_set_history(am_problem *h, int enable);
 AM_API int am_get_history(am_problem *h, float *out, int mem);
 
-/* Options.  AM_OPT_KERNEL: AM_KERNEL_FUSED, AM_KERNEL_PLAIN or
- * AM_KERNEL_LARGE.  AM_KERNEL_LARGE is the batch matrix form of Sec. III-E
+/* Options.  AM_OPT_KERNEL: AM_KERNEL_FUSED, AM_KERNEL_PLAIN,
+ * AM_KERNEL_LARGE or AM_KERNEL_WARP.  AM_KERNEL_LARGE is the batch matrix form of Sec. III-E
  * (Eq. over_3) for large batches: one persistent CTA per SM runs every
  * iteration for tiles of 128 trajectories, with the position step, the
  * trajectory values, P^T delta and R as tcgen05 tensor-core products (three
@@ -245,7 +247,17 @@ AM_API int am_get_history(am_problem *h, float *out, int mem);
  * am_solve_batch returns AM_ERR_ARG (nothing launched) for anything else or
  * when the shape's operands exceed the shared memory of an SM.  Results
  * agree with AM_KERNEL_FUSED to FP32 rounding, not bit for bit.
- * AM_OPT_TILE: trajectories per CTA of the fused kernel (0 = automatic).
+ * AM_KERNEL_WARP runs the same iteration (Sec. III-D, steps 1-5) with two
+ * warps per trajectory for all iterations: after the constants are staged
+ * the two warps of a trajectory synchronise only with each other, never
+ * with the other trajectories of their CTA, which suits batches of a few
+ * trajectories per SM (the paper's B = 1000).  Its contraction R is FP32
+ * SIMT; it takes the FP32 precision form, the default alpha form and
+ * q <= 128 (history included), and am_solve_batch returns AM_ERR_ARG
+ * (nothing launched) for anything else.  Results agree with
+ * AM_KERNEL_FUSED to FP32 rounding, not bit for bit.
+ * AM_OPT_TILE: trajectories per CTA of the fused kernel (0 = automatic);
+ * for AM_KERNEL_WARP, trajectories in flight per CTA, 1..7.
  * AM_OPT_SELECT: the best-trajectory rule of am_get_best and of grouped
  * and served solves when no trajectory is collision-free.  AM_SELECT_COST
  * (default): the lowest cost (Fig. 1's rule applied to every trajectory);

@@ -347,7 +347,8 @@ int am_set_option(am_problem *h, int option, int value)
 {
     if (!h) return fail(AM_ERR_ARG, "null handle");
     if (option == AM_OPT_KERNEL) {
-        if (value != AM_KERNEL_FUSED && value != AM_KERNEL_PLAIN && value != AM_KERNEL_LARGE)
+        if (value != AM_KERNEL_FUSED && value != AM_KERNEL_PLAIN && value != AM_KERNEL_LARGE &&
+            value != AM_KERNEL_WARP)
             return fail(AM_ERR_ARG, "bad kernel");
         h->kernel = value;
         return AM_OK;
@@ -396,6 +397,14 @@ int am_solve_batch(am_problem *h, int B, const float *init, const float *warm_la
                     "the large-batch kernel takes the FP32 form, the default alpha form, q <= 128, no history "
                     "and operands within an SM's shared memory (q=%d, m=%d, n=%d: %zu bytes)",
                     h->pp.q, h->pp.m, h->n, large_smem_bytes(h->L));
+    if (h->kernel == AM_KERNEL_WARP && !warp_supported(h->L))
+        return fail(AM_ERR_ARG,
+                    "the warp-pair kernel takes the FP32 form, the default alpha form, q <= 128 "
+                    "and constants within an SM's shared memory (q=%d, m=%d, n=%d: %zu bytes)",
+                    h->pp.q, h->pp.m, h->n, warp_smem_bytes(h->L, 1));
+    if (h->kernel == AM_KERNEL_WARP && (h->tile < 0 || h->tile > warp_max_traj()))
+        return fail(AM_ERR_ARG, "the warp-pair kernel runs 1..%d trajectories per CTA (tile %d)", warp_max_traj(),
+                    h->tile);
     if (mem == AM_HOST) {
         if (init && !finite_floats(init, size_t(B) * 33)) return fail(AM_ERR_ARG, "non-finite initial coefficients");
         if (warm_lambda && !finite_floats(warm_lambda, size_t(B) * 55)) return fail(AM_ERR_ARG, "non-finite warm multipliers");
@@ -442,6 +451,8 @@ int am_solve_batch(am_problem *h, int B, const float *init, const float *warm_la
         rc = launch_fused(a, h->stream, &h->launches);
     } else if (h->kernel == AM_KERNEL_LARGE) {
         rc = launch_large(a, h->stream, &h->launches);
+    } else if (h->kernel == AM_KERNEL_WARP) {
+        rc = launch_warp(a, h->stream, &h->launches);
     } else {
         const size_t need = plain_scratch_floats(h->L, B);
         rc = ensure(h->d_scratch, h->scratch_cap, need, "plain scratch");

@@ -153,6 +153,16 @@ int large_supported(const ConstLayout &L, bool hist);
 size_t large_smem_bytes(const ConstLayout &L);
 int launch_large(const SolveArgs &a, void *stream, int *launches);
 
+// Warp-pair fused kernel (two warps run every iteration of one trajectory;
+// no block barrier inside the loop).  warp_supported: 1 when the form and
+// shape fit it (FP32 precision form, default alpha form, q <= 128, shared
+// memory within the limit), else 0; launch_warp returns -1 then.
+int warp_supported(const ConstLayout &L);
+size_t warp_smem_bytes(const ConstLayout &L, int traj_per_cta);
+int warp_max_traj();
+int warp_auto_traj(const ConstLayout &L, int B, int sms);
+int launch_warp(const SolveArgs &a, void *stream, int *launches);
+
 // Dynamic shared memory of the single-problem kernels; the debug build's
 // static flag needs a little of the 227 KB.
 #ifdef AM_DEBUG_BOUNDS
