@@ -73,6 +73,9 @@ constexpr int kRS = 68;           // row stride of the transpose rows: 64 partia
 // is all zero: lanes without a pair read it.
 constexpr int kPB = 28;
 constexpr int kPairs = 65;
+// Row stride of the Minv and MQ rows (24 padded columns): 28, for the same
+// reason, so the owner lanes' 128-bit row loads do not share banks.
+constexpr int kMR = 28;
 
 // Per-trajectory shared-memory area (float offsets from the trajectory's base).
 constexpr int kWxd = 0;       // [2][12][8] xi1 duplicated per coefficient k:
@@ -102,8 +105,8 @@ __shared__ int g_woob;
 //          boundary control points, Mpsi^T, (Mpsi H)^T, P^T P), placed so
 //          that sm + cst + off_x addresses section x
 //   cob    region [off_obt, total) (near thresholds, paired obstacle sections)
-//   mir    [22][24] Minv by rows, columns in blocks of 12 per polynomial
-//   mqr    [22][24] MQ by rows, the same columns
+//   mir    [22][kMR] Minv by rows, columns in blocks of 12 per polynomial
+//   mqr    [22][kMR] MQ by rows, the same columns
 //   mpr    [11][12] Mpsi by rows;  mhr [11][12] Mpsi H by rows;  ptr [11][12] P^T P by rows
 //   pb     [2][65][kPB] Pd, Pdd per pair of steps j: (B(2j, k), B(2j + 1, k))
 //          for k = 0..10, zero past the horizon
@@ -120,8 +123,8 @@ __host__ __device__ inline WSmem wsmem_layout(const ConstLayout &L, int T)
     s.cst = o - L.off_mt; o += L.off_obs - L.off_mt;
     s.cob = o; o += L.total - L.off_obt;
     o = (o + 3) & ~3;
-    s.mir = o; o += NS * 24;
-    s.mqr = o; o += NS * 24;
+    s.mir = o; o += NS * kMR;
+    s.mqr = o; o += NS * kMR;
     s.mpr = o; o += NV * 12;
     s.mhr = o; o += NV * 12;
     s.ptr = o; o += NV * 12;
@@ -574,8 +577,8 @@ __device__ void traj_solve(const FusedProblem &p, const float *sm, const WSmem &
             // xi1' = xi1 + Minv u - MQ xi1 on the side's 22 unknowns (rows of
             // Minv and MQ with columns in blocks of 12; the padding is zero)
             if (owner) {
-                const float4 *mr = reinterpret_cast<const float4 *>(sm + S.mir + lane * 24);
-                const float4 *qr = reinterpret_cast<const float4 *>(sm + S.mqr + lane * 24);
+                const float4 *mr = reinterpret_cast<const float4 *>(sm + S.mir + lane * kMR);
+                const float4 *qr = reinterpret_cast<const float4 *>(sm + S.mqr + lane * kMR);
                 const float4 *uu = reinterpret_cast<const float4 *>(ta + kWu + 24 * half);
                 const float4 *xx = reinterpret_cast<const float4 *>(ta + kWxi + cur * 48 + 24 * half);
                 float a0 = 0.f, a1 = 0.f;
@@ -755,8 +758,8 @@ __global__ void __launch_bounds__(kWMaxTraj * kWThreads, 1) am_warp_kernel(Fused
     const float *cst = sm + S.cst;
     for (int i = threadIdx.x; i < NS * NS; i += blockDim.x) {
         const int row = i / NS, c = i - NS * row, cp = c < NV ? c : c + 1;
-        sm[S.mir + row * 24 + cp] = cst[L.off_mt + c * 24 + row];
-        sm[S.mqr + row * 24 + cp] = cst[L.off_mq + c * 24 + row];
+        sm[S.mir + row * kMR + cp] = cst[L.off_mt + c * 24 + row];
+        sm[S.mqr + row * kMR + cp] = cst[L.off_mq + c * 24 + row];
     }
     for (int i = threadIdx.x; i < NV * NV; i += blockDim.x) {
         const int k = i / NV, c = i - NV * k;
