@@ -51,19 +51,19 @@ def algorithmic_flops(q: int, m: int, n: int) -> float:
     return 17.0 * m * n * q + 16.0 * m * q + (16 + 176 + 66 + 176) * q + 2 * 121 * 2 + 3960.0
 
 
-def measured_traffic():
-    """DRAM bytes per launch of the fused kernel from the committed ncu summary,
-    if that summary was taken on the current kernel source (else None)."""
+def measured_traffic(profile: str = "am_warp_kernel_paper_b1000.md", source: str = "am_warp.cu"):
+    """DRAM bytes per launch of a kernel from its committed ncu summary, if
+    that summary was taken on the current kernel source (else None)."""
     import hashlib
     import re
-    prof = os.path.join(ROOT, "profiles", "am_fused_kernel_paper_b1000.md")
-    src = os.path.join(ROOT, "paper_2109_13030_b300", "csrc", "am_fused.cu")
+    prof = os.path.join(ROOT, "profiles", profile)
+    src = os.path.join(ROOT, "paper_2109_13030_b300", "csrc", source)
     try:
         text = open(prof).read()
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     except OSError:
         return None
-    m = re.search(r"am_fused.cu: `([0-9a-f]{16})`", text)
+    m = re.search(re.escape(source) + r": `([0-9a-f]{16})`", text)
     t = re.search(r"dram__bytes_read.sum / write.sum \| ([\d,]+) B / ([\d,]+) B", text)
     if not m or not t or m.group(1) != sha:
         return None
@@ -132,6 +132,7 @@ def summary_sections(extra: dict) -> dict:
     if "large" in extra:
         lg = extra["large"]
         out["large_batch"] = {k: {"large": v["large"]["value"], "small_tile": v["small_tile"]["value"],
+                                  "warp_pair": v["warp_pair"]["value"],
                                   "large_ms": v["large"]["kernel_ms"], "frac": v["large"]["frac_of_fp32_peak"]}
                               for k, v in lg.items() if k.startswith("B=")}
         if lg.get("profile"):
@@ -366,7 +367,7 @@ def bench_large(TJ, W, torch, dev, flush, steps: int, iters: int = 100) -> dict:
     """The large-batch kernel (AM_KERNEL_LARGE: 128 trajectories per CTA, the
     contractions on tcgen05 tensor cores) on the paper-shaped scene at B =
     16384 and at one full wave (128 trajectories per SM), beside the
-    small-tile fused kernel on the same batch.  Times are CUDA events around
+    small-tile and warp-pair fused kernels on the same batch.  Times are CUDA events around
     the solve on its stream, the initial state re-made and L2 flushed before
     each."""
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -377,7 +378,8 @@ def bench_large(TJ, W, torch, dev, flush, steps: int, iters: int = 100) -> dict:
         pb = W.make_problem("paper", 0, B=Bl)
         init = torch.tensor(pb["init"], dtype=torch.float32, device=dev)
         row = {}
-        for kern, name in ((TJ.AM_KERNEL_LARGE, "large"), (TJ.AM_KERNEL_FUSED, "small_tile")):
+        for kern, name in ((TJ.AM_KERNEL_LARGE, "large"), (TJ.AM_KERNEL_FUSED, "small_tile"),
+                           (TJ.AM_KERNEL_WARP, "warp_pair")):
             P = TJ.Problem(pb, kernel=kern)
             ms = []
             for i in range(steps + 2):
@@ -619,7 +621,8 @@ def main():
     pb_all = W.make_problem(WORKLOAD, seed=0, B=B * world)
     lo, hi = D.shard_range(B * world, rank, world)
     pb = dict(pb_all, init=pb_all["init"][lo:hi], B=hi - lo)
-    P = TJ.Problem(pb)
+    # the warp-pair kernel: two warps per trajectory, no block barrier in the loop
+    P = TJ.Problem(pb, kernel=TJ.AM_KERNEL_WARP)
     init_d = torch.tensor(pb["init"], dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -690,6 +693,20 @@ def main():
     plain_launches = TJ.am_last_solve_stats(Pp.h)
     plain_res = float(np.median(Pp.results()["res"]))
     Pp.close()
+    # the small-tile fused kernel (block-synchronous phases, R on mma.sync), same workload
+    Ps = TJ.Problem(pb, kernel=TJ.AM_KERNEL_FUSED)
+    Ps.solve(init_d, ITERS, stream=stream)
+    torch.cuda.synchronize()
+    small_ms = []
+    for i in range(args.plain_steps):
+        flush.fill_(float(i))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        Ps.solve(init_d, ITERS, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        small_ms.append(e0.elapsed_time(e1))
+    Ps.close()
     fused_res = float(np.median(outs[0].numpy()))
 
     extra = {}
@@ -755,11 +772,11 @@ def main():
                        "parallelism": (f"batch of {B * world} sharded x{world}; best-key all-gather per step"
                                        if world > 1 else "single GPU"),
                        "l2": "512 MiB buffer rewritten between timed steps",
-                       "kernel": "fused persistent, 1 launch per solve"},
+                       "kernel": "warp-pair fused persistent (two warps per trajectory), 1 launch per solve"},
             "gpu_launches": launches_per_step * args.steps,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": measured_traffic(),
-                         "kernel": "am_fused_kernel", "kernel_ms": kern_avg, "flops_per_launch": flops,
+                         "kernel": "am_warp_kernel", "kernel_ms": kern_avg, "flops_per_launch": flops,
                          "peak_basis": "derived FP32 peak: SMs x 128 lanes x 2 x 2032 MHz"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": B * 33 * 4,
                     "d2h_bytes_per_step": B * 4 * 4 + 36 * 4},
@@ -771,6 +788,8 @@ def main():
                                    "ms": statistics.mean(plain_ms), "launches": plain_launches,
                                    "res_median": plain_res}
         line["fused_res_median"] = fused_res
+        line["small_tile_kernel"] = {"value": B * ITERS / (statistics.mean(small_ms) / 1e3),
+                                     "ms": statistics.mean(small_ms)}
         line.update(summary_sections(extra))
         if "closed_loop" in extra:
             line["closed_loop"] = extra.pop("closed_loop")
