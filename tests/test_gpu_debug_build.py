@@ -1,11 +1,12 @@
 """The bounds-checking debug build (libtrajam_debug.so, selected with
 TRAJAM_LIBRARY=libtrajam_debug.so).
 
-Its fused and grouped kernels check their state and shared-memory indices
+Its fused, grouped and warp-pair kernels check their state and shared-memory indices
 and report an index outside its array in the problem's status word (bit 2,
 AM_ERR_STATE on the host) instead of trapping; the access is skipped.  On
 valid shapes -- the tiny and paper-shaped workloads, an odd horizon whose
-last pair of steps has one step, and a grouped launch -- no check may fire,
+last pair of steps has one step, a grouped launch and the warp-pair
+kernel on the paper shape and the odd horizon -- no check may fire,
 and the checks must not change a single result: each build runs in its own
 process and the states are compared bit for bit.
 """
@@ -34,6 +35,12 @@ for name, pb in cases.items():
     P = T.Problem(pb)
     P.solve(pb["init"].astype(np.float32), 20)   # raises TrajamError on a nonzero status word
     out[name] = P.state().tolist()
+    P.close()
+for name in ("paper", "odd_q"):                 # the warp-pair kernel
+    pb = cases[name]
+    P = T.Problem(pb, kernel=T.AM_KERNEL_WARP)
+    P.solve(pb["init"].astype(np.float32), 20)
+    out["warp_" + name] = P.state().tolist()
     P.close()
 pbs = W.make_uneven(4, count=3, scale=1 / 128)
 probs = [T.Problem(pb).init_state(pb["init"].astype(np.float32)) for pb in pbs]
