@@ -87,8 +87,25 @@ constexpr int kWu = 360;      // [48]       lam + coef R, the position step's in
 constexpr int kWv = 408;      // [12]       lam_psi + rho P^T delta, the heading step's input
 constexpr int kWdx2 = 420;    // [12]       the last increment of xi2
 constexpr int kWsum = 432;    // [2][4] double: per half, the sums of the last sweep (res, res_psi, cost, dmin)
-constexpr int kWred = 448;    // [44][kRS]  transpose rows of the reductions over the steps
+constexpr int kWsdx2 = 448;   // [12]       the sum of the heading increments over the iterations
+constexpr int kWacc = 464;    // [4][64] float4: per lane, its residual rows summed over the iterations
+constexpr int kWred = 1488;   // [44][kRS]  transpose rows of the reductions over the steps
 constexpr int kTrajFloats = kWred + 44 * kRS;
+
+// Interior control points.  Every polynomial block has boundary rows (the
+// slack blocks too, with cs_boundary): they fix control points 0, 1, 2 and
+// 8, 9, 10, so the null space of the constraint rows is spanned by points
+// 3..7, and the KKT inverse blocks Minv = N (N^T Qbar N)^-1 N^T and Mpsi
+// vanish on the other rows and columns.  The position and heading steps
+// therefore move only the interior points and read only the interior
+// components of R and P^T delta: 20 of R's 44 components (state order o' =
+// 5 blk + k - 3) and 5 of P^T delta's 11 are formed per iteration.  The
+// multipliers' boundary components change no trajectory; the state keeps
+// them exact through the linearity of their updates (the residual rows and
+// delta are summed over the iterations and contracted once at the end).
+constexpr int kI0 = 3;        // first interior control point
+constexpr int kNI = 5;        // interior control points per block
+__device__ __forceinline__ bool interior(int k) { return k >= kI0 && k < kI0 + kNI; }
 
 // Debug build (-DAM_DEBUG_BOUNDS): a failed index check sets the block's
 // flag and skips the access; the flag becomes bit 2 of the status word.
@@ -483,6 +500,51 @@ __device__ __forceinline__ void dot_partials(float *red, int c, const WBasis &b,
     }
 }
 
+// The interior components of the lane's partial of R (k = 3..7 of each
+// block), to column c of transpose rows 0..19 (o' = 5 blk + k - 3).
+__device__ __forceinline__ void dot_interior(float *red, int c, const WBasis &b, const WRes &g)
+{
+    float4 d, e;
+#pragma unroll
+    for (int k = kI0; k < kI0 + kNI; ++k) {
+        if (k == kI0 || (k & 1) == 0) {
+            d = b.pd[k >> 1];
+            e = b.pdd[k >> 1];
+        }
+        float2 px = fmul2(brow(d, k), g.vx), py = fmul2(brow(d, k), g.vy);
+        px = ffma2(brow(e, k), g.ax, px);
+        py = ffma2(brow(e, k), g.ay, py);
+        px = ffma2(b.P[k], g.r0x, px);
+        py = ffma2(b.P[k], g.r0y, py);
+        const float2 sx = fmul2(b.P[k], g.r1x), sy = fmul2(b.P[k], g.r1y);
+        const int i = k - kI0;
+        red[i * kRS + c] = px.x + px.y;
+        red[(kNI + i) * kRS + c] = sx.x + sx.y;
+        red[(2 * kNI + i) * kRS + c] = py.x + py.y;
+        red[(3 * kNI + i) * kRS + c] = sy.x + sy.y;
+    }
+}
+
+// Adds the lane's residual rows to its running sums (slot-major float4s,
+// consecutive lanes on consecutive words).
+__device__ __forceinline__ void acc_rows(float *ta, int col, const WRes &g)
+{
+    float4 *a = reinterpret_cast<float4 *>(ta + kWacc) + col;
+    const float4 a0 = a[0], a1 = a[64], a2 = a[128], a3 = a[192];
+    a[0] = make_float4(a0.x + g.vx.x, a0.y + g.vx.y, a0.z + g.ax.x, a0.w + g.ax.y);
+    a[64] = make_float4(a1.x + g.r0x.x, a1.y + g.r0x.y, a1.z + g.r1x.x, a1.w + g.r1x.y);
+    a[128] = make_float4(a2.x + g.vy.x, a2.y + g.vy.y, a2.z + g.ay.x, a2.w + g.ay.y);
+    a[192] = make_float4(a3.x + g.r0y.x, a3.y + g.r0y.y, a3.z + g.r1y.x, a3.w + g.r1y.y);
+}
+
+__device__ __forceinline__ WRes acc_load(const float *ta, int col)
+{
+    const float4 *a = reinterpret_cast<const float4 *>(ta + kWacc) + col;
+    const float4 a0 = a[0], a1 = a[64], a2 = a[128], a3 = a[192];
+    return WRes{f2(a0.x, a0.y), f2(a0.z, a0.w), f2(a1.x, a1.y), f2(a1.z, a1.w),
+                f2(a2.x, a2.y), f2(a2.z, a2.w), f2(a3.x, a3.y), f2(a3.z, a3.w)};
+}
+
 // The whole AM loop for one trajectory on its two warps.  half: 0 or 1 (the
 // warp's role); b: the lane's basis rows; bid: the pair's named barrier.
 template <int M>
@@ -494,9 +556,14 @@ __device__ void traj_solve(const FusedProblem &p, const float *sm, const WSmem &
     const float *cob = sm + S.cob;
     float *red = ta + kWred;
     const int col = 32 * half + lane;        // the lane's column of the transpose rows
-    const bool owner = lane < NS;            // owns position-step output o = 22 half + lane
-    const int o = NS * half + lane;
-    const bool psi_lane = half == 0 && lane < NV;  // owns heading coefficient k = lane
+    // lanes 0..9 of half h own the interior position-step outputs of side h:
+    // block 2h + lane / 5, control point 3 + lane % 5
+    const bool owner = lane < 2 * kNI;
+    const int oblk = 2 * half + lane / kNI, ok = kI0 + lane % kNI;
+    const int o = NV * oblk + ok, pp = 12 * oblk + ok, orow = NV * (oblk & 1) + ok;
+    // lanes 0..4 of half 0 own the interior heading coefficients k = 3 + lane
+    const bool psi_lane = half == 0 && lane < kNI;
+    const int pk = kI0 + lane;
     const float rho = L.rho;
 
     // ---- state: xi1, xi2 as given into buffer 1 (half 0), lam and lam_psi
@@ -511,7 +578,13 @@ __device__ void traj_solve(const FusedProblem &p, const float *sm, const WSmem &
         }
     }
     float lam = owner ? gs[55 + o] : 0.f;
-    float lps = psi_lane ? gs[99 + lane] : 0.f;
+    float lps = psi_lane ? gs[99 + pk] : 0.f;
+    {
+        float4 *a = reinterpret_cast<float4 *>(ta + kWacc) + col;
+        a[0] = a[64] = a[128] = a[192] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (half == 0 && lane < 12) ta[kWsdx2 + lane] = 0.f;
+    }
+    float2 dsum = f2(0.f, 0.f);  // the lane's delta summed over the iterations
     pair_sync(bid);
     // boundary control points from the boundary conditions on every block with
     // boundary rows, the rest as given (entries split between the halves)
@@ -547,9 +620,19 @@ __device__ void traj_solve(const FusedProblem &p, const float *sm, const WSmem &
         sweep_pair<M, false, false, true>(cob, L, pg, z2, jp, valid, v1, r, f, st, g, sums);
         st.psi_cur = pr;
     }
-    dot_partials(red, col, b, g);
+    dot_interior(red, col, b, g);
     pair_sync(bid);
-    float R = owner ? row_sum(red, o) : 0.f;
+    const int rrow = 2 * kNI * half + lane;  // the owner's transpose row of R
+    float R = owner ? row_sum(red, rrow) : 0.f;
+    // The boundary points never move from here on: both buffers take the
+    // reference's (buffer 1 held the given samples for the first step).
+    if (half == 0) {
+        for (int e = lane; e < 30; e += 32) {
+            const int blk = e / 6, i = e - 6 * blk, k = i < 3 ? i : i + 5;
+            if (blk < 4) put_xi1(ta, 1, blk * 12 + k, ta[kWxi + blk * 12 + k]);
+            else put_xi2(ta, 1, k, ta[kWx2 + k]);
+        }
+    }
     float ptp = 0.f;  // heading lanes: P^T delta of the last heading step
     int cur = 0, cur2 = 0;
 
@@ -563,8 +646,8 @@ __device__ void traj_solve(const FusedProblem &p, const float *sm, const WSmem &
                 lam = fmaf(rho, R, lam);
                 // lambda_psi (Eq. update_lambda_psi): P^T (P xi2' - psi_t) = P^T P dxi2 - P^T delta
                 if (psi_lane) {
-                    const float *dx2 = ta + kWdx2;
-                    const float *pr = sm + S.ptr + lane * 12;
+                    const float *dx2 = ta + kWdx2;  // zero at the boundary points
+                    const float *pr = sm + S.ptr + pk * 12;
                     float a = 0.f;
 #pragma unroll
                     for (int c = 0; c < NV; ++c) a = fmaf(pr[c], dx2[c], a);
@@ -572,13 +655,14 @@ __device__ void traj_solve(const FusedProblem &p, const float *sm, const WSmem &
                 }
             }
             if (post) break;
-            if (owner) ta[kWu + pidx(o)] = u;
+            if (owner) ta[kWu + pp] = u;  // the boundary entries of u stay zero
             __syncwarp();
-            // xi1' = xi1 + Minv u - MQ xi1 on the side's 22 unknowns (rows of
-            // Minv and MQ with columns in blocks of 12; the padding is zero)
+            // xi1' = xi1 + Minv u - MQ xi1 on the interior rows of the side's
+            // 22 unknowns (rows of Minv and MQ with columns in blocks of 12; the
+            // padding is zero)
             if (owner) {
-                const float4 *mr = reinterpret_cast<const float4 *>(sm + S.mir + lane * kMR);
-                const float4 *qr = reinterpret_cast<const float4 *>(sm + S.mqr + lane * kMR);
+                const float4 *mr = reinterpret_cast<const float4 *>(sm + S.mir + orow * kMR);
+                const float4 *qr = reinterpret_cast<const float4 *>(sm + S.mqr + orow * kMR);
                 const float4 *uu = reinterpret_cast<const float4 *>(ta + kWu + 24 * half);
                 const float4 *xx = reinterpret_cast<const float4 *>(ta + kWxi + cur * 48 + 24 * half);
                 float a0 = 0.f, a1 = 0.f;
@@ -594,7 +678,6 @@ __device__ void traj_solve(const FusedProblem &p, const float *sm, const WSmem &
                     a0 = fmaf(m.w, uv.w, a0);
                     a1 = fmaf(qq.w, x.w, a1);
                 }
-                const int pp = pidx(o);
                 put_xi1(ta, cur ^ 1, pp, ta[kWxi + cur * 48 + pp] + (a0 - a1));
             }
             cur ^= 1;
@@ -612,10 +695,11 @@ __device__ void traj_solve(const FusedProblem &p, const float *sm, const WSmem &
             st.psi_t.y = st.psi_prev.y + wrap_pi(atan2_heading(r.s.y, r.c.y) - st.psi_prev.y);
             const float2 dl = fsub2(st.psi_t, st.psi_cur);
             const float2 dd = f2(valid ? dl.x : 0.f, v1 ? dl.y : 0.f);
+            dsum = fadd2(dsum, dd);
 #pragma unroll
-            for (int k = 0; k < NV; ++k) {
+            for (int k = kI0; k < kI0 + kNI; ++k) {
                 const float2 m = fmul2(b.P[k], dd);
-                red[k * kRS + col] = m.x + m.y;
+                red[(k - kI0) * kRS + col] = m.x + m.y;
             }
             pair_sync(bid);
         }
@@ -623,12 +707,12 @@ __device__ void traj_solve(const FusedProblem &p, const float *sm, const WSmem &
         if (half == 0) {
             if (psi_lane) {
                 ptp = row_sum(red, lane);
-                ta[kWv + lane] = fmaf(rho, ptp, lps);
+                ta[kWv + pk] = fmaf(rho, ptp, lps);  // the boundary entries of v stay zero
             }
             __syncwarp();
             if (psi_lane) {
-                const float4 *mr = reinterpret_cast<const float4 *>(sm + S.mpr + lane * 12);
-                const float4 *hr = reinterpret_cast<const float4 *>(sm + S.mhr + lane * 12);
+                const float4 *mr = reinterpret_cast<const float4 *>(sm + S.mpr + pk * 12);
+                const float4 *hr = reinterpret_cast<const float4 *>(sm + S.mhr + pk * 12);
                 const float4 *vv = reinterpret_cast<const float4 *>(ta + kWv);
                 const float4 *xx = reinterpret_cast<const float4 *>(ta + kWx2 + cur2 * 12);
                 float a0 = 0.f, a1 = 0.f;
@@ -647,8 +731,9 @@ __device__ void traj_solve(const FusedProblem &p, const float *sm, const WSmem &
                     }
                 }
                 const float d = a0 - a1;
-                put_xi2(ta, cur2 ^ 1, lane, ta[kWx2 + cur2 * 12 + lane] + d);
-                ta[kWdx2 + lane] = d;
+                put_xi2(ta, cur2 ^ 1, pk, ta[kWx2 + cur2 * 12 + pk] + d);
+                ta[kWdx2 + pk] = d;
+                ta[kWsdx2 + pk] += d;
             }
         }
         cur2 ^= 1;
@@ -662,7 +747,8 @@ __device__ void traj_solve(const FusedProblem &p, const float *sm, const WSmem &
             if (fin) sweep_pair<M, true, true, false>(cob, L, ps, pdd, jp, valid, v1, r, r, st, g, sums);
             else if (res) sweep_pair<M, true, false, false>(cob, L, ps, pdd, jp, valid, v1, r, r, st, g, sums);
             else sweep_pair<M, false, false, false>(cob, L, ps, pdd, jp, valid, v1, r, r, st, g, sums);
-            dot_partials(red, col, b, g);
+            acc_rows(ta, col, g);
+            dot_interior(red, col, b, g);
             double *hs = reinterpret_cast<double *>(ta + kWsum);
             if (res) {
                 // the sums over the steps of the residuals and the cost in FP64
@@ -699,15 +785,40 @@ __device__ void traj_solve(const FusedProblem &p, const float *sm, const WSmem &
                     p.mind[traj] = sqrtf(float(fmin(hs[3], hs[7])));
                 }
             }
-            R = owner ? row_sum(red, o) : 0.f;
+            R = owner ? row_sum(red, rrow) : 0.f;
         }
     }
-    // ---- the state back: xi1 (cur), xi2 (cur2), lam, lam_psi
+    // ---- the state back: xi1 (cur), xi2 (cur2), lam, lam_psi.  The
+    // multipliers' boundary components: lam_b' = lam_b + rho F_b^T (sum of
+    // the residual rows of the iterations), and lam_psi_b' = lam_psi_b -
+    // sign rho_psi (P^T P sum(dxi2) - P^T sum(delta))_b (Eq. update_lambda_1
+    // and update_lambda_psi summed over the iterations; both are linear).
     float *gd = p.state + (size_t)traj * STATE;
+    pair_sync(bid);  // every R row read before the rows are reused
+    dot_partials(red, col, b, acc_load(ta, col));
+    pair_sync(bid);
+    if (lane < NS) {
+        const int ob = NS * half + lane;
+        if (!interior(ob % NV)) gd[55 + ob] = fmaf(rho, row_sum(red, ob), gs[55 + ob]);
+    }
+    pair_sync(bid);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        const float2 m = fmul2(b.P[k], dsum);
+        red[k * kRS + col] = m.x + m.y;
+    }
+    pair_sync(bid);
     if (half == 0) {
+        if (lane < NV && !interior(lane)) {
+            const float *pr = sm + S.ptr + lane * 12;
+            float a = 0.f;
+#pragma unroll
+            for (int c = 0; c < NV; ++c) a = fmaf(pr[c], ta[kWsdx2 + c], a);
+            gd[99 + lane] = gs[99 + lane] - L.psi_sign * L.rho_psi * (a - row_sum(red, lane));
+        }
         for (int e = lane; e < 55; e += 32)
             gd[e] = e < 44 ? ta[kWxi + cur * 48 + pidx(e)] : ta[kWx2 + cur2 * 12 + (e - 44)];
-        if (psi_lane) gd[99 + lane] = lps;
+        if (psi_lane) gd[99 + pk] = lps;
     }
     if (owner) gd[55 + o] = lam;
     pair_sync(bid);  // the area is free for the next trajectory
@@ -820,7 +931,9 @@ size_t warp_smem_bytes(const ConstLayout &L, int T) { return size_t(wsmem_layout
 
 int warp_supported(const ConstLayout &L)
 {
-    if (L.precision != 0 || L.alpha_mode != 0) return 0;
+    // every block needs its boundary rows (cs_boundary): the kernel moves
+    // only the interior control points
+    if (L.precision != 0 || L.alpha_mode != 0 || !L.cs_boundary) return 0;
     if (L.q < 2 || L.q > kWMaxQ || L.m < 1 || L.m > MAXM || L.n > 64) return 0;
     return warp_smem_bytes(L, 1) <= kFusedSmemMax ? 1 : 0;
 }
