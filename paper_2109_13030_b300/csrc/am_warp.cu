@@ -89,7 +89,9 @@ constexpr int kWdx2 = 420;    // [12]       the last increment of xi2
 constexpr int kWsum = 432;    // [2][4] double: per half, the sums of the last sweep (res, res_psi, cost, dmin)
 constexpr int kWsdx2 = 448;   // [12]       the sum of the heading increments over the iterations
 constexpr int kWacc = 464;    // [4][64] float4: per lane, its residual rows summed over the iterations
-constexpr int kWred = 1488;   // [44][kRS]  transpose rows of the reductions over the steps
+constexpr int kWeb = 1488;    // [5][64] float4: per lane, the boundary control points' share of its
+                              //            values (x, xd | xdd, c | y, yd | ydd, s | psi, psidd)
+constexpr int kWred = 2768;   // [44][kRS]  transpose rows of the reductions over the steps
 constexpr int kTrajFloats = kWred + 44 * kRS;
 
 // Interior control points.  Every polynomial block has boundary rows (the
@@ -277,6 +279,91 @@ __device__ __forceinline__ void heading_pair(const float4 *x2, const WBasis &b, 
             dd = ffma2(f2(w.x, w.y), ca, dd);
             if (2 * k2 + 1 < NV) dd = ffma2(f2(w.z, w.w), cb, dd);
         }
+    }
+}
+
+// The boundary control points' share of the trajectory values and of the
+// heading (and its second derivative) at the pair: constant over the
+// iterations, since those points never move.  Formed once per trajectory
+// from the reference (buffer 0) into the lane's slots of eb.
+__device__ __forceinline__ void eval_boundary(const float4 *xd, const float4 *x2, const WBasis &b, float4 *eb)
+{
+    const float2 z = f2(0.f, 0.f);
+    WVals r{z, z, z, z, z, z, z, z};
+    float2 ps = z, pdd = z;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        if (interior(k)) continue;
+        const float2 pd = brow(b.pd[k >> 1], k), pe = brow(b.pdd[k >> 1], k);
+        const float4 u = xd[2 * k], w = xd[2 * k + 1];
+        const float2 cx = f2(u.x, u.y), cy = f2(u.z, u.w), cc = f2(w.x, w.y), cs = f2(w.z, w.w);
+        r.x = ffma2(b.P[k], cx, r.x);
+        r.xd = ffma2(pd, cx, r.xd);
+        r.xdd = ffma2(pe, cx, r.xdd);
+        r.c = ffma2(b.P[k], cc, r.c);
+        r.y = ffma2(b.P[k], cy, r.y);
+        r.yd = ffma2(pd, cy, r.yd);
+        r.ydd = ffma2(pe, cy, r.ydd);
+        r.s = ffma2(b.P[k], cs, r.s);
+        const float4 v = x2[k >> 1];
+        const float2 c2 = (k & 1) ? f2(v.z, v.w) : f2(v.x, v.y);
+        ps = ffma2(b.P[k], c2, ps);
+        pdd = ffma2(pe, c2, pdd);
+    }
+    eb[0] = make_float4(r.x.x, r.x.y, r.xd.x, r.xd.y);
+    eb[64] = make_float4(r.xdd.x, r.xdd.y, r.c.x, r.c.y);
+    eb[128] = make_float4(r.y.x, r.y.y, r.yd.x, r.yd.y);
+    eb[192] = make_float4(r.ydd.x, r.ydd.y, r.s.x, r.s.y);
+    eb[256] = make_float4(ps.x, ps.y, pdd.x, pdd.y);
+}
+
+// Trajectory values at the pair: the boundary share plus the interior
+// control points 3..7 of the duplicated xi1.
+__device__ __forceinline__ void eval_interior(const float4 *xd, const WBasis &b, const float4 *eb, WVals &r)
+{
+    const float4 e0 = eb[0], e1 = eb[64], e2 = eb[128], e3 = eb[192];
+    r = WVals{f2(e0.x, e0.y), f2(e0.z, e0.w), f2(e1.x, e1.y), f2(e2.x, e2.y),
+              f2(e2.z, e2.w), f2(e3.x, e3.y), f2(e1.z, e1.w), f2(e3.z, e3.w)};
+    float4 d, e;
+#pragma unroll
+    for (int k = kI0; k < kI0 + kNI; ++k) {
+        if (k == kI0 || (k & 1) == 0) {
+            d = b.pd[k >> 1];
+            e = b.pdd[k >> 1];
+        }
+        const float4 u = xd[2 * k], w = xd[2 * k + 1];
+        const float2 cx = f2(u.x, u.y), cy = f2(u.z, u.w), cc = f2(w.x, w.y), cs = f2(w.z, w.w);
+        const float2 pd = brow(d, k), pdd = brow(e, k);
+        r.x = ffma2(b.P[k], cx, r.x);
+        r.xd = ffma2(pd, cx, r.xd);
+        r.xdd = ffma2(pdd, cx, r.xdd);
+        r.c = ffma2(b.P[k], cc, r.c);
+        r.y = ffma2(b.P[k], cy, r.y);
+        r.yd = ffma2(pd, cy, r.yd);
+        r.ydd = ffma2(pdd, cy, r.ydd);
+        r.s = ffma2(b.P[k], cs, r.s);
+    }
+}
+
+// Heading (and with DD its second derivative) at the pair: the boundary
+// share plus the interior control points of the duplicated xi2.
+template <bool DD>
+__device__ __forceinline__ void heading_interior(const float4 *x2, const WBasis &b, const float4 *eb, float2 &p,
+                                                 float2 &dd)
+{
+    const float4 e4 = eb[256];
+    p = f2(e4.x, e4.y);
+    dd = f2(e4.z, e4.w);
+    float4 v, w;
+#pragma unroll
+    for (int k = kI0; k < kI0 + kNI; ++k) {
+        if (k == kI0 || (k & 1) == 0) {
+            v = x2[k >> 1];
+            if (DD) w = b.pdd[k >> 1];
+        }
+        const float2 c2 = brow(v, k);
+        p = ffma2(b.P[k], c2, p);
+        if (DD) dd = ffma2(brow(w, k), c2, dd);
     }
 }
 
@@ -474,6 +561,57 @@ __device__ __forceinline__ float row_sum(const float *red, int o)
     return ((a.x + b.x) + (a.y + b.y)) + ((a.z + b.z) + (a.w + b.w));
 }
 
+// Sum of 32 partials of transpose row o starting at column c0 (a multiple
+// of 4), in a fixed order.
+__device__ __forceinline__ float row_part32(const float *red, int o, int c0)
+{
+    const float4 *r = reinterpret_cast<const float4 *>(red + o * kRS + c0);
+    float4 a = r[0], b = r[1];
+#pragma unroll
+    for (int i = 2; i < 8; i += 2) {
+        const float4 v = r[i], w = r[i + 1];
+        a.x += v.x;
+        a.y += v.y;
+        a.z += v.z;
+        a.w += v.w;
+        b.x += w.x;
+        b.y += w.y;
+        b.z += w.z;
+        b.w += w.w;
+    }
+    return ((a.x + b.x) + (a.y + b.y)) + ((a.z + b.z) + (a.w + b.w));
+}
+
+// The same for 16 partials.
+__device__ __forceinline__ float row_part16(const float *red, int o, int c0)
+{
+    const float4 *r = reinterpret_cast<const float4 *>(red + o * kRS + c0);
+    const float4 a = r[0], b = r[1], c = r[2], d = r[3];
+    return (((a.x + b.x) + (c.x + d.x)) + ((a.y + b.y) + (c.y + d.y))) +
+           (((a.z + b.z) + (c.z + d.z)) + ((a.w + b.w) + (c.w + d.w)));
+}
+
+// R for the owner lanes 0..9 of a half: each row is summed by lanes l and
+// l + 16 (columns 0..31 and 32..63), joined by one shuffle.  Every lane of
+// the warp takes part in the shuffle.
+__device__ __forceinline__ float r_rows(const float *red, int half, int lane)
+{
+    const int l = lane & 15;
+    const float s = l < 2 * kNI ? row_part32(red, 2 * kNI * half + l, 32 * (lane >> 4)) : 0.f;
+    return s + __shfl_xor_sync(0xffffffffu, s, 16);
+}
+
+// P^T delta for lanes 0..4 (rows 0..4, interior k = 3..7): each row is
+// summed by lanes k, k + 8, k + 16, k + 24 (16 columns each), joined by two
+// shuffles.  Every lane of the warp takes part.
+__device__ __forceinline__ float ptd_rows(const float *red, int lane)
+{
+    const int l = lane & 7;
+    float s = l < kNI ? row_part16(red, l, 16 * (lane >> 3)) : 0.f;
+    s += __shfl_xor_sync(0xffffffffu, s, 8);
+    return s + __shfl_xor_sync(0xffffffffu, s, 16);
+}
+
 // The lane's partial of R = F^T (g - F xi1) over its two steps, to column c
 // of the transpose rows: R_pos[side][k] = Pd^T rv + Pdd^T ra + P^T r0 and
 // R_slack[side][k] = P^T r1 (state order o = 11 blk + k: c_x pos, c_c slack,
@@ -622,8 +760,7 @@ __device__ void traj_solve(const FusedProblem &p, const float *sm, const WSmem &
     }
     dot_interior(red, col, b, g);
     pair_sync(bid);
-    const int rrow = 2 * kNI * half + lane;  // the owner's transpose row of R
-    float R = owner ? row_sum(red, rrow) : 0.f;
+    float R = r_rows(red, half, lane);  // owner lanes: their component of R
     // The boundary points never move from here on: both buffers take the
     // reference's (buffer 1 held the given samples for the first step).
     if (half == 0) {
@@ -633,6 +770,9 @@ __device__ void traj_solve(const FusedProblem &p, const float *sm, const WSmem &
             else put_xi2(ta, 1, k, ta[kWx2 + k]);
         }
     }
+    const float4 *eb = reinterpret_cast<const float4 *>(ta + kWeb) + col;
+    eval_boundary(reinterpret_cast<const float4 *>(ta + kWxd), reinterpret_cast<const float4 *>(ta + kWx2d), b,
+                  reinterpret_cast<float4 *>(ta + kWeb) + col);
     float ptp = 0.f;  // heading lanes: P^T delta of the last heading step
     int cur = 0, cur2 = 0;
 
@@ -665,17 +805,23 @@ __device__ void traj_solve(const FusedProblem &p, const float *sm, const WSmem &
                 const float4 *qr = reinterpret_cast<const float4 *>(sm + S.mqr + orow * kMR);
                 const float4 *uu = reinterpret_cast<const float4 *>(ta + kWu + 24 * half);
                 const float4 *xx = reinterpret_cast<const float4 *>(ta + kWxi + cur * 48 + 24 * half);
+                // u is zero outside the interior columns 3..7 and 15..19
                 float a0 = 0.f, a1 = 0.f;
 #pragma unroll
                 for (int c4 = 0; c4 < 6; ++c4) {
-                    const float4 m = mr[c4], qq = qr[c4], uv = uu[c4], x = xx[c4];
-                    a0 = fmaf(m.x, uv.x, a0);
+                    const float4 qq = qr[c4], x = xx[c4];
+                    if (c4 == 0 || c4 == 3) {
+                        a0 = fmaf(mr[c4].w, uu[c4].w, a0);
+                    } else if (c4 == 1 || c4 == 4) {
+                        const float4 m = mr[c4], uv = uu[c4];
+                        a0 = fmaf(m.x, uv.x, a0);
+                        a0 = fmaf(m.y, uv.y, a0);
+                        a0 = fmaf(m.z, uv.z, a0);
+                        a0 = fmaf(m.w, uv.w, a0);
+                    }
                     a1 = fmaf(qq.x, x.x, a1);
-                    a0 = fmaf(m.y, uv.y, a0);
                     a1 = fmaf(qq.y, x.y, a1);
-                    a0 = fmaf(m.z, uv.z, a0);
                     a1 = fmaf(qq.z, x.z, a1);
-                    a0 = fmaf(m.w, uv.w, a0);
                     a1 = fmaf(qq.w, x.w, a1);
                 }
                 put_xi1(ta, cur ^ 1, pp, ta[kWxi + cur * 48 + pp] + (a0 - a1));
@@ -688,7 +834,7 @@ __device__ void traj_solve(const FusedProblem &p, const float *sm, const WSmem &
         // ---- EVAL: trajectory values, heading target, the lane's P^T delta
         WVals r;
         {
-            eval_pair(reinterpret_cast<const float4 *>(ta + kWxd) + cur * 24, b, r);
+            eval_interior(reinterpret_cast<const float4 *>(ta + kWxd) + cur * 24, b, eb, r);
             // psi_t = psi + wrap(atan2(s, c) - psi), psi the previous heading;
             // the heading step works on delta = psi_t - P xi2
             st.psi_t.x = st.psi_prev.x + wrap_pi(atan2_heading(r.s.x, r.c.x) - st.psi_prev.x);
@@ -705,10 +851,8 @@ __device__ void traj_solve(const FusedProblem &p, const float *sm, const WSmem &
         }
         // ---- PSI: the heading step of Eq. compute_convex_surrogate in increment form
         if (half == 0) {
-            if (psi_lane) {
-                ptp = row_sum(red, lane);
-                ta[kWv + pk] = fmaf(rho, ptp, lps);  // the boundary entries of v stay zero
-            }
+            ptp = ptd_rows(red, lane);
+            if (psi_lane) ta[kWv + pk] = fmaf(rho, ptp, lps);  // the boundary entries of v stay zero
             __syncwarp();
             if (psi_lane) {
                 const float4 *mr = reinterpret_cast<const float4 *>(sm + S.mpr + pk * 12);
@@ -742,8 +886,8 @@ __device__ void traj_solve(const FusedProblem &p, const float *sm, const WSmem &
         {
             const float4 *x2d = reinterpret_cast<const float4 *>(ta + kWx2d) + cur2 * 6;
             float2 ps, pdd;
-            if (res) heading_pair<true>(x2d, b, ps, pdd);
-            else heading_pair<false>(x2d, b, ps, pdd);
+            if (res) heading_interior<true>(x2d, b, eb, ps, pdd);
+            else heading_interior<false>(x2d, b, eb, ps, pdd);
             if (fin) sweep_pair<M, true, true, false>(cob, L, ps, pdd, jp, valid, v1, r, r, st, g, sums);
             else if (res) sweep_pair<M, true, false, false>(cob, L, ps, pdd, jp, valid, v1, r, r, st, g, sums);
             else sweep_pair<M, false, false, false>(cob, L, ps, pdd, jp, valid, v1, r, r, st, g, sums);
@@ -785,7 +929,7 @@ __device__ void traj_solve(const FusedProblem &p, const float *sm, const WSmem &
                     p.mind[traj] = sqrtf(float(fmin(hs[3], hs[7])));
                 }
             }
-            R = owner ? row_sum(red, rrow) : 0.f;
+            R = r_rows(red, half, lane);
         }
     }
     // ---- the state back: xi1 (cur), xi2 (cur2), lam, lam_psi.  The
