@@ -773,6 +773,7 @@ __device__ void traj_solve(const FusedProblem &p, const float *sm, const WSmem &
     const float4 *eb = reinterpret_cast<const float4 *>(ta + kWeb) + col;
     eval_boundary(reinterpret_cast<const float4 *>(ta + kWxd), reinterpret_cast<const float4 *>(ta + kWx2d), b,
                   reinterpret_cast<float4 *>(ta + kWeb) + col);
+
     float ptp = 0.f;  // heading lanes: P^T delta of the last heading step
     int cur = 0, cur2 = 0;
 
@@ -790,7 +791,7 @@ __device__ void traj_solve(const FusedProblem &p, const float *sm, const WSmem &
                     const float *pr = sm + S.ptr + pk * 12;
                     float a = 0.f;
 #pragma unroll
-                    for (int c = 0; c < NV; ++c) a = fmaf(pr[c], dx2[c], a);
+                    for (int c = kI0; c < kI0 + kNI; ++c) a = fmaf(pr[c], dx2[c], a);
                     lps -= L.psi_sign * L.rho_psi * (a - ptp);
                 }
             }
@@ -805,7 +806,8 @@ __device__ void traj_solve(const FusedProblem &p, const float *sm, const WSmem &
                 const float4 *qr = reinterpret_cast<const float4 *>(sm + S.mqr + orow * kMR);
                 const float4 *uu = reinterpret_cast<const float4 *>(ta + kWu + 24 * half);
                 const float4 *xx = reinterpret_cast<const float4 *>(ta + kWxi + cur * 48 + 24 * half);
-                // u is zero outside the interior columns 3..7 and 15..19
+                // Minv u over the interior columns 3..7 and 15..19 (u is zero
+                // elsewhere); MQ xi1 over every column, in order
                 float a0 = 0.f, a1 = 0.f;
 #pragma unroll
                 for (int c4 = 0; c4 < 6; ++c4) {
@@ -859,20 +861,24 @@ __device__ void traj_solve(const FusedProblem &p, const float *sm, const WSmem &
                 const float4 *hr = reinterpret_cast<const float4 *>(sm + S.mhr + pk * 12);
                 const float4 *vv = reinterpret_cast<const float4 *>(ta + kWv);
                 const float4 *xx = reinterpret_cast<const float4 *>(ta + kWx2 + cur2 * 12);
+                // Mpsi (.) over the interior columns 3..7 (v is zero elsewhere);
+                // Mpsi H xi2 over every column, in order
                 float a0 = 0.f, a1 = 0.f;
 #pragma unroll
                 for (int c4 = 0; c4 < 3; ++c4) {
-                    const float4 m = mr[c4], hh = hr[c4], v = vv[c4], x = xx[c4];
-                    a0 = fmaf(m.x, v.x, a0);
-                    a1 = fmaf(hh.x, x.x, a1);
-                    a0 = fmaf(m.y, v.y, a0);
-                    a1 = fmaf(hh.y, x.y, a1);
-                    a0 = fmaf(m.z, v.z, a0);
-                    a1 = fmaf(hh.z, x.z, a1);
-                    if (c4 < 2) {
-                        a0 = fmaf(m.w, v.w, a0);
-                        a1 = fmaf(hh.w, x.w, a1);
+                    const float4 hh = hr[c4], x = xx[c4];
+                    if (c4 == 0) a0 = fmaf(mr[0].w, vv[0].w, a0);
+                    if (c4 == 1) {
+                        const float4 m = mr[1], w = vv[1];
+                        a0 = fmaf(m.x, w.x, a0);
+                        a0 = fmaf(m.y, w.y, a0);
+                        a0 = fmaf(m.z, w.z, a0);
+                        a0 = fmaf(m.w, w.w, a0);
                     }
+                    a1 = fmaf(hh.x, x.x, a1);
+                    a1 = fmaf(hh.y, x.y, a1);
+                    a1 = fmaf(hh.z, x.z, a1);
+                    if (c4 < 2) a1 = fmaf(hh.w, x.w, a1);
                 }
                 const float d = a0 - a1;
                 put_xi2(ta, cur2 ^ 1, pk, ta[kWx2 + cur2 * 12 + pk] + d);
