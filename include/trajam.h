@@ -74,6 +74,8 @@ extern "C" {
 #define AM_KERNEL_LARGE 2   /* fused, 128 trajectories per CTA on tcgen05    */
 #define AM_KERNEL_WARP 3    /* fused, two warps per trajectory, no block     */
                             /* barriers in the loop                          */
+#define AM_KERNEL_AUTO 4    /* the fastest of the three fused kernels that   */
+                            /* takes the problem (see AM_OPT_KERNEL)         */
 
 #define AM_NV 11
 #define AM_STATE_FLOATS 110
@@ -238,7 +240,7 @@ AM_API int am_set_history(am_problem *h, int enable);
 AM_API int am_get_history(am_problem *h, float *out, int mem);
 
 /* Options.  AM_OPT_KERNEL: AM_KERNEL_FUSED, AM_KERNEL_PLAIN,
- * AM_KERNEL_LARGE or AM_KERNEL_WARP.  AM_KERNEL_LARGE is the batch matrix form of Sec. III-E
+ * AM_KERNEL_LARGE, AM_KERNEL_WARP or AM_KERNEL_AUTO.  AM_KERNEL_LARGE is the batch matrix form of Sec. III-E
  * (Eq. over_3) for large batches: one persistent CTA per SM runs every
  * iteration for tiles of 128 trajectories, with the position step, the
  * trajectory values, P^T delta and R as tcgen05 tensor-core products (three
@@ -256,6 +258,14 @@ AM_API int am_get_history(am_problem *h, float *out, int mem);
  * q <= 128 (history included), and am_solve_batch returns AM_ERR_ARG
  * (nothing launched) for anything else.  Results agree with
  * AM_KERNEL_FUSED to FP32 rounding, not bit for bit.
+ * AM_KERNEL_AUTO picks, per solve, AM_KERNEL_LARGE from B = 16384 on
+ * (where it takes the problem), else AM_KERNEL_WARP where it takes the
+ * problem, else AM_KERNEL_FUSED, with automatic tiles (AM_OPT_TILE is
+ * ignored).  Groups and servers run a problem whose handle selects
+ * AM_KERNEL_WARP or AM_KERNEL_AUTO on the warp-pair group kernels when its
+ * form and shape fit them, every other problem on the small-tile ones; a
+ * problem gives the same bits alone (with the kernel its handle selects
+ * for that batch) and in a group.
  * AM_OPT_TILE: trajectories per CTA of the fused kernel (0 = automatic);
  * for AM_KERNEL_WARP, trajectories in flight per CTA, 1..7.
  * AM_OPT_SELECT: the best-trajectory rule of am_get_best and of grouped

@@ -348,7 +348,7 @@ int am_set_option(am_problem *h, int option, int value)
     if (!h) return fail(AM_ERR_ARG, "null handle");
     if (option == AM_OPT_KERNEL) {
         if (value != AM_KERNEL_FUSED && value != AM_KERNEL_PLAIN && value != AM_KERNEL_LARGE &&
-            value != AM_KERNEL_WARP)
+            value != AM_KERNEL_WARP && value != AM_KERNEL_AUTO)
             return fail(AM_ERR_ARG, "bad kernel");
         h->kernel = value;
         return AM_OK;
@@ -379,6 +379,18 @@ int am_set_history(am_problem *h, int enable)
     return AM_OK;
 }
 
+// The kernel a solve of B trajectories runs: the handle's choice, or for
+// AM_KERNEL_AUTO the large-batch kernel from B = 16384 on, else the
+// warp-pair kernel, else the small-tile kernel, each where it takes the
+// problem's form and shape.
+int solve_kernel(const am_problem *h, int B)
+{
+    if (h->kernel != AM_KERNEL_AUTO) return h->kernel;
+    if (B >= 16384 && large_supported(h->L, h->hist_on)) return AM_KERNEL_LARGE;
+    if (warp_supported(h->L)) return AM_KERNEL_WARP;
+    return AM_KERNEL_FUSED;
+}
+
 int am_solve_batch(am_problem *h, int B, const float *init, const float *warm_lambda, int iters,
                    void *stream, int mem)
 {
@@ -387,19 +399,20 @@ int am_solve_batch(am_problem *h, int B, const float *init, const float *warm_la
     if (B < 1 || B > (1 << 24)) return fail(AM_ERR_ARG, "B must be in [1, 2^24]");
     if (iters < 1 || iters > 100000) return fail(AM_ERR_ARG, "iters must be in [1, 100000]");
     if (mem != AM_HOST && mem != AM_DEVICE) return fail(AM_ERR_ARG, "bad mem flag");
+    const int kern = solve_kernel(h, B);
     if (!init && (!h->solved || B != h->B))
         return fail(AM_ERR_STATE, "warm start needs a previous solve with the same B");
     if (!init && warm_lambda) return fail(AM_ERR_ARG, "warm_lambda needs init");
-    if (h->kernel == AM_KERNEL_PLAIN && h->pp.precision != AM_FP32)
+    if (kern == AM_KERNEL_PLAIN && h->pp.precision != AM_FP32)
         return fail(AM_ERR_ARG, "reduced precision runs on the fused kernel only");
-    if (h->kernel == AM_KERNEL_LARGE && !large_supported(h->L, h->hist_on))
+    if (kern == AM_KERNEL_LARGE && !large_supported(h->L, h->hist_on))
         return fail(AM_ERR_ARG,
                     "the large-batch kernel takes the FP32 form, the default alpha form, q <= 128, no history "
                     "and operands within an SM's shared memory (q=%d, m=%d, n=%d: %zu bytes)",
                     h->pp.q, h->pp.m, h->n, large_smem_bytes(h->L));
-    if (h->kernel == AM_KERNEL_WARP && !warp_supported(h->L))
+    if (kern == AM_KERNEL_WARP && !warp_supported(h->L))
         return fail(AM_ERR_ARG,
-                    "the warp-pair kernel takes the FP32 form, the default alpha form, q <= 128 "
+                    "the warp-pair kernel takes the FP32 form, the default alpha form, cs_boundary, q <= 128 "
                     "and constants within an SM's shared memory (q=%d, m=%d, n=%d: %zu bytes)",
                     h->pp.q, h->pp.m, h->n, warp_smem_bytes(h->L, 1));
     if (h->kernel == AM_KERNEL_WARP && (h->tile < 0 || h->tile > warp_max_traj()))
@@ -445,13 +458,13 @@ int am_solve_batch(am_problem *h, int B, const float *init, const float *warm_la
     a.cost = h->d_out + 2 * size_t(B);
     a.mind = h->d_out + 3 * size_t(B);
     a.hist = hist;
-    a.tile = h->tile;
+    a.tile = h->kernel == AM_KERNEL_AUTO ? 0 : h->tile;
     a.err = h->d_err;
-    if (h->kernel == AM_KERNEL_FUSED) {
+    if (kern == AM_KERNEL_FUSED) {
         rc = launch_fused(a, h->stream, &h->launches);
-    } else if (h->kernel == AM_KERNEL_LARGE) {
+    } else if (kern == AM_KERNEL_LARGE) {
         rc = launch_large(a, h->stream, &h->launches);
-    } else if (h->kernel == AM_KERNEL_WARP) {
+    } else if (kern == AM_KERNEL_WARP) {
         rc = launch_warp(a, h->stream, &h->launches);
     } else {
         const size_t need = plain_scratch_floats(h->L, B);
@@ -622,7 +635,8 @@ struct am_group {
     cudaStream_t vst[kGroupVariants] = {};
     cudaEvent_t fork_ev = nullptr, join_ev[kGroupVariants] = {};
     struct Captured {
-        int mask, threads;
+        uint64_t mask;
+        int threads;
         cudaStream_t stream;
         const char *up;
         size_t smem[kGroupVariants];
@@ -656,6 +670,17 @@ std::vector<int> active_list(const am_group *g)
 // variant: the problems with the costliest tiles first (longest-processing-
 // time order), the tiles of one problem together so a CTA rarely re-stages
 // constants.
+// The group variant of a problem: the warp-pair kernels (32 + m - 1) when
+// its handle selects them and they take its shape, else the small-tile
+// variant of its precision form, circle count and alpha form.
+int problem_variant(const am_problem *h)
+{
+    if ((h->kernel == AM_KERNEL_WARP || h->kernel == AM_KERNEL_AUTO) && warp_supported(h->L) &&
+        warp_group_smem(h->L) <= kGroupSmemLimit)
+        return kGroupWarpVariant0 + h->L.m - 1;
+    return group_variant(h->L);
+}
+
 int build_work(am_group *g, int threads, int iters, int sms)
 {
     const int np = int(g->probs.size());
@@ -664,7 +689,9 @@ int build_work(am_group *g, int threads, int iters, int sms)
     for (int v = 0; v < kGroupVariants; ++v) g->vsmem[v] = 0;
     for (int i = 0; i < np; ++i) {
         am_problem *h = g->probs[i];
-        const int T = group_tile(h->L, threads);
+        const int v = problem_variant(h);
+        const bool warp = v >= kGroupWarpVariant0;
+        const int T = warp ? warp_group_traj() : group_tile(h->L, threads);
         if (T < 1) return fail(AM_ERR_ARG, "problem %d (q=%d, n=%d) does not fit a block of %d", i, h->pp.q, h->n, threads);
         FusedProblem &f = g->h_probs[i];
         f.cblob = h->d_blob;
@@ -680,8 +707,7 @@ int build_work(am_group *g, int threads, int iters, int sms)
         f.mind = h->d_out + 3 * size_t(h->B);
         f.hist = nullptr;
         f.err = h->d_err;  // a failed wait shows in the problem's own getters
-        const int v = group_variant(h->L);
-        const size_t sm = fused_smem_bytes(h->L, T);
+        const size_t sm = warp ? warp_group_smem(h->L) : fused_smem_bytes(h->L, T);
         if (sm > g->vsmem[v]) g->vsmem[v] = sm;
     }
     // Tiles of the active problems: each problem gets a share of the SMs in
@@ -709,7 +735,7 @@ int build_work(am_group *g, int threads, int iters, int sms)
     for (int i : act) {
         const am_problem *h = g->probs[i];
         const double tile_cost = double(g->h_probs[i].T) * h->pp.q * (12.0 * h->pp.m * h->n + 250.0);
-        order[group_variant(h->L)].push_back({-tile_cost, i});
+        order[problem_variant(h)].push_back({-tile_cost, i});
     }
     g->h_items.clear();
     for (int v = 0; v < kGroupVariants; ++v) {
@@ -780,10 +806,10 @@ int upload_work(am_group *g, cudaStream_t st)
 
 // Issues the variant kernels of the mask: on the given stream when there is
 // one variant, else forked onto the group's streams and joined back.
-int issue_variants(am_group *g, int mask, int threads, int sms, bool fixed_grid, cudaStream_t st,
+int issue_variants(am_group *g, uint64_t mask, int threads, int sms, bool fixed_grid, cudaStream_t st,
                    int *launches)
 {
-    const int nv = __builtin_popcount(unsigned(mask));
+    const int nv = __builtin_popcountll(mask);
     GroupLaunch gl;
     gl.d_probs = g->d_probs;
     gl.d_items = g->d_items;
@@ -792,7 +818,7 @@ int issue_variants(am_group *g, int mask, int threads, int sms, bool fixed_grid,
     gl.threads = threads;
     if (nv > 1) CK(cudaEventRecord(g->fork_ev, st), "fork");
     for (int v = 0; v < kGroupVariants; ++v) {
-        if (!(mask >> v & 1)) continue;
+        if (!(mask >> v & 1ull)) continue;
         gl.variant = v;
         gl.smem = g->vsmem[v];
         gl.grid = fixed_grid || g->count[v] > sms ? sms : g->count[v];
@@ -824,11 +850,11 @@ int group_launch(am_group *g, int iters, cudaStream_t st)
     if (rc) return rc;
     rc = upload_work(g, st);
     if (rc) return rc;
-    int mask = 0;
+    uint64_t mask = 0;
     for (int v = 0; v < kGroupVariants; ++v)
-        if (g->count[v] > 0) mask |= 1 << v;
+        if (g->count[v] > 0) mask |= 1ull << v;
     if (!mask) return AM_OK;
-    if (__builtin_popcount(unsigned(mask)) > 1 && !g->vst[0]) {
+    if (__builtin_popcountll(mask) > 1 && !g->vst[0]) {
         for (int v = 0; v < kGroupVariants; ++v) {
             CK(cudaStreamCreateWithFlags(&g->vst[v], cudaStreamNonBlocking), "stream creation");
             CK(cudaEventCreateWithFlags(&g->join_ev[v], cudaEventDisableTiming), "event creation");
@@ -867,7 +893,7 @@ int group_launch(am_group *g, int iters, cudaStream_t st)
         hit = &g->graphs.back();
     }
     CK(cudaGraphLaunch(hit->exec, st), "graph launch");
-    g->launches += __builtin_popcount(unsigned(mask));
+    g->launches += __builtin_popcountll(mask);
     return AM_OK;
 }
 

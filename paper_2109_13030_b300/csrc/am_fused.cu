@@ -1134,6 +1134,7 @@ int group_tile(const ConstLayout &L, int threads)
 
 int launch_group(const GroupLaunch &g, void *stream, int *launches, const char **why)
 {
+    if (g.variant >= kGroupWarpVariant0) return launch_group_warp(g, stream, launches, why);
     *why = nullptr;
     if (g.threads < 32 || g.threads > kMaxThreads || g.smem > kGroupSmemMax || g.grid < 1 ||
         g.variant < 0 || g.variant >= kGroupVariants)

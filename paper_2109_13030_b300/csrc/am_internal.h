@@ -162,6 +162,10 @@ size_t warp_smem_bytes(const ConstLayout &L, int traj_per_cta);
 int warp_max_traj();
 int warp_auto_traj(const ConstLayout &L, int B, int sms);
 int launch_warp(const SolveArgs &a, void *stream, int *launches);
+// The warp-pair group kernels (variants 32..35): seven trajectory slots per
+// CTA; the shared memory a problem needs in them.
+int warp_group_traj();
+size_t warp_group_smem(const ConstLayout &L);
 
 // Dynamic shared memory of the single-problem kernels; the debug build's
 // static flag needs a little of the 227 KB.
@@ -189,7 +193,15 @@ constexpr float kNearMargin = 0.6f;
 // Grouped launch: many problems' tiles in persistent kernels, one kernel per
 // variant (circle count, alpha form) present; the variant kernels of one
 // solve run concurrently.
-constexpr int kGroupVariants = 32;  // precision (4) x circle count (4) x alpha form (2)
+// Variants 0..31: the small-tile group kernels, precision (4) x circle count
+// (4) x alpha form (2); 32..35: the warp-pair group kernels (FP32, default
+// alpha form) for 1..4 circles, for problems whose handle selects the
+// warp-pair kernel (AM_KERNEL_WARP or AM_KERNEL_AUTO) and whose shape it takes.
+constexpr int kGroupWarpVariant0 = 32;
+constexpr int kGroupVariants = 36;
+// Dynamic shared memory a warp-pair group kernel may take (its problem
+// descriptor and work-item slot are static shared memory).
+constexpr size_t kGroupSmemLimit = 227 * 1024 - 1024;
 struct GroupLaunch {
     const FusedProblem *d_probs;  // device array, one per problem
     const int *d_items;           // device array of (problem, tile) pairs, all variants
@@ -209,6 +221,7 @@ int group_tile(const ConstLayout &L, int threads);
 int fused_max_threads();
 // Returns 0, -1 (configuration out of range) or -2 (CUDA error, *why says which).
 int launch_group(const GroupLaunch &g, void *stream, int *launches, const char **why);
+int launch_group_warp(const GroupLaunch &g, void *stream, int *launches, const char **why);
 // Best-trajectory selection for several problems in one launch: one block per
 // listed problem; writes 36 floats per entry ({index, cost, res, 33 coefficients}).
 int launch_group_argmin(const FusedProblem *d_probs, const int *d_list, int count, float *d_out,

@@ -974,26 +974,19 @@ __device__ void traj_solve(const FusedProblem &p, const float *sm, const WSmem &
     pair_sync(bid);  // the area is free for the next trajectory
 }
 
-template <int M>
-__global__ void __launch_bounds__(kWMaxTraj * kWThreads, 1) am_warp_kernel(FusedProblem p)
+// Stages a problem's small matrices and obstacle sections into shared memory
+// (two bulk copies on one mbarrier, waited on with a bound) while zeroing the
+// rest of the area, then forms the row-major copies of Minv, MQ, Mpsi, Mpsi H
+// and P^T P and the pair-interleaved Pd, Pdd.  Every thread of the block
+// calls it; false (for every thread) when the wait ran out.
+__device__ bool stage_problem(const FusedProblem &p, float *sm, const WSmem &S, uint64_t *bar, uint32_t parity)
 {
-    extern __shared__ __align__(128) float sm[];
     const ConstLayout &L = p.L;
-    const int T = blockDim.x / kWThreads;
-    const WSmem S = wsmem_layout(L, T);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + S.bar);
-#ifdef AM_DEBUG_BOUNDS
-    if (threadIdx.x == 0) g_woob = 0;
-#endif
-    if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" :: "r"(smem_u32(bar)));
-        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-    }
-    __syncthreads();
-    // Stage the small matrices and the obstacle sections (two bulk copies on
-    // one mbarrier, bounded wait) and zero the rest of the area.
     if (threadIdx.x == 0) {
         const uint32_t b0 = uint32_t(L.off_obs - L.off_mt) * 4u, b1 = uint32_t(L.total - L.off_obt) * 4u;
+        // order the block's earlier generic-proxy accesses of this area
+        // before the asynchronous copies overwrite it
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n"
                      :: "r"(smem_u32(bar)), "r"(b0 + b1) : "memory");
         if (!L.diag_stall) {
@@ -1006,16 +999,11 @@ __global__ void __launch_bounds__(kWMaxTraj * kWThreads, 1) am_warp_kernel(Fused
     {
         const uint64_t t0 = global_ns();
         for (int spin = 0; spin < (1 << 26) && !ok; ++spin) {
-            ok = mbar_try_wait(bar, 0) ? 1 : 0;
+            ok = mbar_try_wait(bar, parity) ? 1 : 0;
             if (!ok && global_ns() - t0 > kWaitLimitNs) break;
         }
     }
-    if (__syncthreads_and(ok) == 0) {
-        if (threadIdx.x == 0) atomicExch(p.err, 1);
-        return;
-    }
-    // Rows of Minv, MQ (columns in blocks of 12), Mpsi, Mpsi H and P^T P,
-    // from the constant block's column-major copies.
+    if (__syncthreads_and(ok) == 0) return false;
     const float *cst = sm + S.cst;
     for (int i = threadIdx.x; i < NS * NS; i += blockDim.x) {
         const int row = i / NS, c = i - NS * row, cp = c < NV ? c : c + 1;
@@ -1036,21 +1024,122 @@ __global__ void __launch_bounds__(kWMaxTraj * kWThreads, 1) am_warp_kernel(Fused
         sm[S.pb + (ty * kPairs + (t >> 1)) * kPB + 2 * k + (t & 1)] = __ldg(rows + ((1 + ty) * L.q + t) * 12 + k);
     }
     __syncthreads();
+    return true;
+}
 
+// The lane's pair of steps and its basis rows for a problem of horizon q.
+struct WLane {
+    WBasis b;
+    int jp;
+    bool valid, v1;
+};
+
+__device__ __forceinline__ void lane_setup(const FusedProblem &p, const float *sm, const WSmem &S, int half,
+                                           int lane, WLane &w)
+{
+    const int q = p.L.q, np = (q + 1) >> 1, nh = (np + 1) >> 1;
+    const int j = half * nh + lane;
+    w.valid = lane < nh && j < np;
+    w.v1 = w.valid && 2 * j + 1 < q;
+    load_basis(p.cblob + p.L.off_prow, sm + S.pb, w.valid ? j : kPairs - 1, w.valid, w.v1, w.b);
+    w.jp = w.valid ? j : 0;  // obstacle-track pair (in range for every lane)
+}
+
+__device__ __forceinline__ void init_stage_barrier(uint64_t *bar)
+{
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" :: "r"(smem_u32(bar)));
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+}
+
+template <int M>
+__global__ void __launch_bounds__(kWMaxTraj * kWThreads, 1) am_warp_kernel(FusedProblem p)
+{
+    extern __shared__ __align__(128) float sm[];
+    const int T = blockDim.x / kWThreads;
+    const WSmem S = wsmem_layout(p.L, T);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + S.bar);
+#ifdef AM_DEBUG_BOUNDS
+    if (threadIdx.x == 0) g_woob = 0;
+#endif
+    init_stage_barrier(bar);
+    if (!stage_problem(p, sm, S, bar, 0)) {
+        if (threadIdx.x == 0) atomicExch(p.err, 1);
+        return;
+    }
     const int slot = threadIdx.x / kWThreads, half = (threadIdx.x >> 5) & 1, lane = threadIdx.x & 31;
     float *ta = sm + S.traj + slot * kTrajFloats;
-    const int np = (L.q + 1) >> 1, nh = (np + 1) >> 1;
-    const int j = half * nh + lane;
-    const bool valid = lane < nh && j < np;
-    const bool v1 = valid && 2 * j + 1 < L.q;
-    WBasis b;
-    load_basis(rows, sm + S.pb, valid ? j : kPairs - 1, valid, v1, b);
-    const int jp = valid ? j : 0;  // obstacle-track pair (in range for every lane)
+    WLane w;
+    lane_setup(p, sm, S, half, lane, w);
     for (int traj = blockIdx.x * T + slot; traj < p.B; traj += gridDim.x * T)
-        traj_solve<M>(p, sm, S, ta, traj, half, lane, 1 + slot, b, jp, valid, v1);
+        traj_solve<M>(p, sm, S, ta, traj, half, lane, 1 + slot, w.b, w.jp, w.valid, w.v1);
 #ifdef AM_DEBUG_BOUNDS
     __syncthreads();
     if (threadIdx.x == 0 && g_woob) atomicOr(p.err, 2);
+#endif
+}
+
+// Uneven batching with the warp-pair kernel: persistent CTAs of seven
+// trajectory slots take work items (problem, tile of at most seven
+// trajectories) of variant v from a list in order, through one atomic
+// counter, and re-stage constants whenever they move to another problem.
+// Each slot's pair of warps runs one trajectory of the tile.  The lists
+// live in device memory, as for the small-tile group kernels.
+//   head[v]: number of items of variant v; head[kGroupVariants + v]: offset of its list
+//   ctl[2 v]: its work counter (zeroed before the launch); ctl[2 v + 1]: status
+template <int M>
+__global__ void __launch_bounds__(kWMaxTraj * kWThreads, 1)
+am_group_warp_kernel(const FusedProblem *probs, const int *items, const int *head, int *ctl, int v)
+{
+    int *counter = ctl + 2 * v;
+    const int nitems = head[v];
+    const int *list = items + 2 * head[kGroupVariants + v];
+    extern __shared__ __align__(128) float sm[];
+    __shared__ FusedProblem kp;
+    __shared__ int s_item;
+    // the barrier sits at the start of the area, as in every layout below
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm);
+#ifdef AM_DEBUG_BOUNDS
+    if (threadIdx.x == 0) g_woob = 0;
+#endif
+    init_stage_barrier(bar);
+    const int slot = threadIdx.x / kWThreads, half = (threadIdx.x >> 5) & 1, lane = threadIdx.x & 31;
+    int cur = -1;
+    uint32_t parity = 0;
+    WLane w;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= nitems) break;
+        const int pi = list[2 * it], tile = list[2 * it + 1];
+        if (pi != cur) {
+            if (threadIdx.x == 0) kp = probs[pi];
+            __syncthreads();
+            if (!stage_problem(kp, sm, wsmem_layout(kp.L, kWMaxTraj), bar, parity)) {
+                if (threadIdx.x == 0) {
+                    atomicExch(kp.err, 1);
+                    atomicExch(ctl + 2 * v + 1, 1);
+                }
+                return;
+            }
+            parity ^= 1u;
+            cur = pi;
+            lane_setup(kp, sm, wsmem_layout(kp.L, kWMaxTraj), half, lane, w);
+        }
+        const WSmem S = wsmem_layout(kp.L, kWMaxTraj);
+        const long long lo = (long long)tile * kp.B / kp.ntiles, hi = (long long)(tile + 1) * kp.B / kp.ntiles;
+        const int traj = int(lo) + slot;
+        if (traj < hi)
+            traj_solve<M>(kp, sm, S, sm + S.traj + slot * kTrajFloats, traj, half, lane, 1 + slot, w.b, w.jp,
+                          w.valid, w.v1);
+        __syncthreads();
+    }
+#ifdef AM_DEBUG_BOUNDS
+    __syncthreads();
+    if (threadIdx.x == 0 && g_woob) atomicOr(kp.err, 2);
 #endif
 }
 
@@ -1101,6 +1190,41 @@ int warp_auto_traj(const ConstLayout &L, int B, int sms)
     if (T > kWMaxTraj) T = kWMaxTraj;
     while (T > 1 && warp_smem_bytes(L, int(T)) > kFusedSmemMax) --T;
     return int(T);
+}
+
+int warp_group_traj() { return kWMaxTraj; }
+
+size_t warp_group_smem(const ConstLayout &L) { return warp_smem_bytes(L, kWMaxTraj); }
+
+int launch_group_warp(const GroupLaunch &g, void *stream, int *launches, const char **why)
+{
+    *why = nullptr;
+    const int M = g.variant - kGroupWarpVariant0 + 1;
+    if (M < 1 || M > MAXM || g.grid < 1 || g.smem > kGroupSmemLimit) return -1;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(g.d_ctl + 2 * g.variant, 0, 2 * sizeof(int), st);
+    if (e != cudaSuccess) {
+        *why = cudaGetErrorString(e);
+        return -2;
+    }
+    auto go = [&](auto kernel) {
+        cudaError_t r = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(g.smem));
+        if (r != cudaSuccess) return r;
+        kernel<<<g.grid, kWMaxTraj * kWThreads, g.smem, st>>>(g.d_probs, g.d_items, g.d_head, g.d_ctl, g.variant);
+        return cudaPeekAtLastError();
+    };
+    switch (M) {
+    case 1: e = go(am_group_warp_kernel<1>); break;
+    case 2: e = go(am_group_warp_kernel<2>); break;
+    case 3: e = go(am_group_warp_kernel<3>); break;
+    default: e = go(am_group_warp_kernel<4>); break;
+    }
+    if (e != cudaSuccess) {
+        *why = cudaGetErrorString(e);
+        return -2;
+    }
+    if (launches) ++*launches;
+    return 0;
 }
 
 int launch_warp(const SolveArgs &a, void *stream, int *launches)

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, os.environ.get("TRAJAM_LIBRARY", "libtrajam.so"))
 AM_OK, AM_ERR_ARG, AM_ERR_CUDA, AM_ERR_BUDGET, AM_ERR_TIMEOUT, AM_ERR_NAN, AM_ERR_STATE = 0, -1, -2, -3, -4, -5, -6
 AM_HOST, AM_DEVICE = 0, 1
 AM_FP32, AM_TF32, AM_BF16, AM_SPLIT_BF16 = 0, 1, 2, 3
-AM_KERNEL_FUSED, AM_KERNEL_PLAIN, AM_KERNEL_LARGE, AM_KERNEL_WARP = 0, 1, 2, 3
+AM_KERNEL_FUSED, AM_KERNEL_PLAIN, AM_KERNEL_LARGE, AM_KERNEL_WARP, AM_KERNEL_AUTO = 0, 1, 2, 3, 4
 AM_OPT_KERNEL, AM_OPT_TILE, AM_OPT_DIAG_STALL, AM_OPT_SELECT = 1, 2, 3, 4
 AM_SELECT_COST, AM_SELECT_CLEARANCE = 0, 1
 AM_GOPT_THREADS, AM_GOPT_GRAPH = 1, 2

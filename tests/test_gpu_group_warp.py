@@ -1,0 +1,119 @@
+"""Grouped and served solves on the warp-pair kernels.
+
+A problem whose handle selects AM_KERNEL_AUTO (or AM_KERNEL_WARP) runs in a
+group on the warp-pair group kernels when its form and shape fit them (FP32,
+default alpha form, q <= 128), every other problem on the small-tile group
+kernels, all in one launch.  A trajectory's arithmetic on the warp-pair
+kernels does not depend on which CTA slot runs it, so each problem gives
+the same bits in the group as alone with the kernel AM_KERNEL_AUTO picks
+for it; the results also match the FP64 oracle (with the mix's widened
+coefficient tolerance, see test_gpu_group).  A server whose scenes select
+AM_KERNEL_AUTO serves a request alone and in a mixed round with the same
+bits.
+"""
+import numpy as np
+import pytest
+
+from paper_2109_13030_b300 import workload as W
+
+from test_gpu_group import check_oracle, mix, split_all
+
+pytestmark = pytest.mark.gpu
+
+
+def tj():
+    from paper_2109_13030_b300 import trajam
+    return trajam
+
+
+def alone(pb, iters, kernel):
+    T = tj()
+    P = T.Problem(pb, kernel=kernel)
+    P.solve(pb["init"].astype(np.float32), iters)
+    out = split_all(P)
+    out["state"] = P.state()
+    P.close()
+    return out
+
+
+def group(pbs, iters, kernel, reps=1, stream=None):
+    T = tj()
+    probs = [T.Problem(pb, kernel=kernel).init_state(pb["init"].astype(np.float32), stream=stream) for pb in pbs]
+    G = T.Group(probs)
+    for _ in range(reps):
+        G.solve(iters, stream=stream)
+    outs = []
+    for P in probs:
+        o = split_all(P)
+        o["state"] = P.state()
+        outs.append(o)
+    stats = G.stats()
+    G.close()
+    for P in probs:
+        P.close()
+    return outs, stats
+
+
+def test_auto_group_equals_alone_bit_for_bit_and_oracle():
+    """Ten mixed problems, q in {50, 100, 150}: the q <= 128 ones on the
+    warp-pair group kernels, the q = 150 ones on the small-tile kernels."""
+    T = tj()
+    pbs = mix(count=10, seed=8)
+    assert {pb["q"] for pb in pbs} & {50, 100} and 150 in {pb["q"] for pb in pbs}
+    outs, (launches, items) = group(pbs, 10, T.AM_KERNEL_AUTO)
+    variants = {("warp" if pb["q"] <= 128 else "tile", pb["m"]) for pb in pbs}
+    assert launches == len(variants)
+    for pb, g in zip(pbs, outs):
+        a = alone(pb, 10, T.AM_KERNEL_AUTO)
+        np.testing.assert_array_equal(g["state"], a["state"])
+        for k in ("res", "res_psi", "cost", "mind"):
+            np.testing.assert_array_equal(g[k], a[k], err_msg=k)
+        check_oracle(pb, g)
+
+
+def test_warp_group_equals_warp_alone():
+    """Every problem selects AM_KERNEL_WARP: the same bits as lone warp-pair
+    solves, also when the captured launch is replayed on a stream."""
+    import torch
+    T = tj()
+    pbs = [pb for pb in mix(count=12, seed=9) if pb["q"] <= 128][:6]
+    st = torch.cuda.Stream()
+    outs, _ = group(pbs, 10, T.AM_KERNEL_WARP, reps=2, stream=st)
+    for pb, g in zip(pbs, outs):
+        # two group solves of 10 iterations from the cold start: the second
+        # continues from the first, like one 10-iteration solve then a warm one
+        P = T.Problem(pb, kernel=T.AM_KERNEL_WARP)
+        P.solve(pb["init"].astype(np.float32), 10)
+        P.solve(None, 10)
+        ref = P.state()
+        P.close()
+        np.testing.assert_array_equal(g["state"], ref)
+
+
+def test_server_auto_scene_alone_equals_in_mix():
+    T = tj()
+    pbs = W.make_uneven(21, count=4, scale=1.0 / 64)
+
+    def serve(ks, start_after_submit):
+        S = T.Server(8 << 30, 10)
+        probs = []
+        for pb in pbs:
+            P = T.Problem(pb, kernel=T.AM_KERNEL_AUTO)
+            S.add_scene(P, pb["init"].astype(np.float32))
+            probs.append(P)
+        if not start_after_submit:
+            S.start()
+        tickets = [S.submit(k) for k in ks]
+        if start_after_submit:
+            S.start()
+        out = [S.wait(t) for t in tickets]
+        S.close()
+        for P in probs:
+            P.close()
+        return out
+
+    first = serve([0], False)[0]
+    mixed = serve(range(len(pbs)), True)
+    assert first["status"] == 0 and all(r["status"] == 0 for r in mixed)
+    assert all(r["batch"] == len(pbs) for r in mixed)
+    np.testing.assert_array_equal(np.asarray(mixed[0]["coeffs"]), np.asarray(first["coeffs"]))
