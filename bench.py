@@ -134,6 +134,9 @@ def summary_sections(extra: dict) -> dict:
         if "bf16" in u:
             out["uneven"]["bf16_value"] = u["bf16"]["value"]
             out["uneven"]["bf16_ms"] = u["bf16"]["ms_per_solve"]
+        if "auto" in u:
+            out["uneven"]["auto_value"] = u["auto"]["value"]
+            out["uneven"]["auto_ms"] = u["auto"]["ms_per_solve"]
     if "precision" in extra:
         pr = extra["precision"]
         out["precision_b4096"] = {k: {"value": v["value"], **({"dev10": v["coef_dev_vs_fp32_after_10"]["max"]}
@@ -152,9 +155,11 @@ def summary_sections(extra: dict) -> dict:
         pq = lambda r: [r["p50_ms"], r["p99_ms"]]
         out["serving_p50_p99_ms"] = {
             "400/s": {"batched": pq(sv["batched"]), "seq_fused": pq(sv["sequential_fused"]),
+                      "batched_auto": pq(sv["batched_auto"]), "seq_auto": pq(sv["sequential_auto"]),
                       "seq_plain": pq(sv["sequential_plain_fp32_loop"])},
             "2500/s": {"batched": pq(sv["high_load"]["batched"]),
-                       "seq_fused": pq(sv["high_load"]["sequential_fused"])}}
+                       "seq_fused": pq(sv["high_load"]["sequential_fused"]),
+                       "batched_auto": pq(sv["high_load"]["batched_auto"])}}
         out["serving_mean_batch"] = {"400/s": sv["batched"]["mean_batch"],
                                      "2500/s": sv["high_load"]["batched"]["mean_batch"]}
     return out
@@ -323,8 +328,38 @@ def bench_uneven(TJ, W, torch, dev, flush, steps: int, iters: int = 100) -> dict
     G.close()
     for P in probs:
         P.close()
+    # the same mix with AM_KERNEL_AUTO handles: the q <= 128 problems on the
+    # warp-pair group kernels, the q = 150 ones on the small-tile kernels,
+    # in one launch (FP32)
+    probs = [TJ.Problem(pb, kernel=TJ.AM_KERNEL_AUTO) for pb in pbs]
+    reset()
+    G = TJ.Group(probs)
+    G.autotune(iters, stream=side)
+    for _ in range(2):
+        reset()
+        G.solve(iters, stream=side)
+    torch.cuda.synchronize()
+    a_launch0, _ = G.stats()
+    ams = []
+    for i in range(steps):
+        flush.fill_(float(i))
+        reset()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(side)
+        G.solve(iters, stream=side)
+        e1.record(side)
+        torch.cuda.synchronize()
+        ams.append(e0.elapsed_time(e1))
+    a_ms = statistics.mean(ams)
+    a_launches = (G.stats()[0] - a_launch0) / steps
+    G.close()
+    for P in probs:
+        P.close()
     return {"metric": "trajectory-AM-iterations/sec over 64 mixed problems", "value": total * iters / (g_ms / 1e3),
             "bf16": {"value": total * iters / (b_ms / 1e3), "unit": UNIT, "ms_per_solve": b_ms},
+            "auto": {"value": total * iters / (a_ms / 1e3), "unit": UNIT, "ms_per_solve": a_ms,
+                     "launches_per_solve": a_launches,
+                     "problems_on_warp_pair": sum(1 for pb in pbs if pb["q"] <= 128)},
             "unit": UNIT, "ms_per_solve": g_ms, "problems": len(pbs), "trajectories": total,
             "iterations": iters, "work_items": items, "threads": threads, "launches_per_solve": launches,
             "achieved_tflops": flops / (g_ms / 1e3) / 1e12,
@@ -475,6 +510,9 @@ def bench_serving(TJ, W, seconds: float, plain_seconds: float) -> dict:
            "iterations_per_request": 30}
     out["batched"] = serve_run(TJ, W, pbs, TJ.AM_SRV_BATCHED, TJ.AM_KERNEL_FUSED, seconds)
     out["sequential_fused"] = serve_run(TJ, W, pbs, TJ.AM_SRV_SEQUENTIAL, TJ.AM_KERNEL_FUSED, seconds)
+    # scenes selecting AM_KERNEL_AUTO (warp-pair kernels where they take the scene)
+    out["batched_auto"] = serve_run(TJ, W, pbs, TJ.AM_SRV_BATCHED, TJ.AM_KERNEL_AUTO, seconds)
+    out["sequential_auto"] = serve_run(TJ, W, pbs, TJ.AM_SRV_SEQUENTIAL, TJ.AM_KERNEL_AUTO, seconds)
     out["sequential_plain_fp32_loop"] = serve_run(TJ, W, pbs, TJ.AM_SRV_SEQUENTIAL, TJ.AM_KERNEL_PLAIN,
                                                   plain_seconds)
     # a heavier load, where requests arrive while others are on the GPU and
@@ -483,9 +521,11 @@ def bench_serving(TJ, W, seconds: float, plain_seconds: float) -> dict:
     out["high_load"] = {
         "offered_per_s": hi_rate,
         "batched": serve_run(TJ, W, pbs, TJ.AM_SRV_BATCHED, TJ.AM_KERNEL_FUSED, plain_seconds * 1.5,
-                             warmup_s=0.5, rate=hi_rate),
+                             warmup_s=1.0, rate=hi_rate),
         "sequential_fused": serve_run(TJ, W, pbs, TJ.AM_SRV_SEQUENTIAL, TJ.AM_KERNEL_FUSED,
-                                      plain_seconds * 1.5, warmup_s=0.5, rate=hi_rate),
+                                      plain_seconds * 1.5, warmup_s=1.0, rate=hi_rate),
+        "batched_auto": serve_run(TJ, W, pbs, TJ.AM_SRV_BATCHED, TJ.AM_KERNEL_AUTO, plain_seconds * 1.5,
+                                  warmup_s=1.0, rate=hi_rate),
     }
     return out
 
