@@ -117,3 +117,33 @@ def test_server_auto_scene_alone_equals_in_mix():
     assert first["status"] == 0 and all(r["status"] == 0 for r in mixed)
     assert all(r["batch"] == len(pbs) for r in mixed)
     np.testing.assert_array_equal(np.asarray(mixed[0]["coeffs"]), np.asarray(first["coeffs"]))
+
+
+@pytest.mark.parametrize("case", ["paper", "q150", "literal", "large"])
+def test_auto_picks_the_kernel(case):
+    """AM_KERNEL_AUTO solves with the large-batch kernel from B = 16384 on,
+    else with the warp-pair kernel where it takes the problem, else with the
+    small-tile kernel: the same bits as the explicit choice."""
+    T = tj()
+    flags, expect = {}, T.AM_KERNEL_WARP
+    if case == "paper":
+        pb = W.make_problem("paper", 0, B=64)
+    elif case == "q150":
+        pb, expect = W.make_shape(11, 16, 150, 6, 3), T.AM_KERNEL_FUSED
+    elif case == "literal":
+        pb, flags, expect = W.make_problem("tiny", 0, B=16), dict(alpha_mode=1), T.AM_KERNEL_FUSED
+    else:
+        pb, expect = W.make_problem("paper", 0, B=16384), T.AM_KERNEL_LARGE
+    a = alone(dict(pb), 10, T.AM_KERNEL_AUTO) if not flags else None
+    if flags:
+        P = T.Problem(pb, kernel=T.AM_KERNEL_AUTO, **flags)
+        P.solve(pb["init"].astype(np.float32), 10)
+        a = {"state": P.state()}
+        P.close()
+        P = T.Problem(pb, kernel=expect, **flags)
+        P.solve(pb["init"].astype(np.float32), 10)
+        b = {"state": P.state()}
+        P.close()
+    else:
+        b = alone(dict(pb), 10, expect)
+    np.testing.assert_array_equal(a["state"], b["state"])
