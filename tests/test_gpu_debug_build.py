@@ -51,6 +51,15 @@ out["group"] = [P.state().tolist() for P in probs]   # each state read checks it
 G.close()
 for P in probs:
     P.close()
+# the warp-pair group kernels (AUTO handles, q <= 128) beside the small-tile ones
+probs = [T.Problem(pb, kernel=T.AM_KERNEL_AUTO).init_state(pb["init"].astype(np.float32)) for pb in pbs]
+G = T.Group(probs)
+G.solve(10)
+T.am_group_get_best(G.g, len(probs))
+out["group_auto"] = [P.state().tolist() for P in probs]
+G.close()
+for P in probs:
+    P.close()
 print(json.dumps(out))
 '''
 
@@ -69,7 +78,7 @@ def test_debug_build_runs_clean_and_matches_release():
     dbg, rel = run("libtrajam_debug.so"), run("libtrajam.so")
     assert dbg.keys() == rel.keys()
     for key in rel:
-        a, b = (dbg[key], rel[key]) if key == "group" else ([dbg[key]], [rel[key]])
+        a, b = (dbg[key], rel[key]) if key.startswith("group") else ([dbg[key]], [rel[key]])
         assert len(a) == len(b), key
         for x, y in zip(a, b):
             np.testing.assert_array_equal(np.asarray(x), np.asarray(y), err_msg=key)
