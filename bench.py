@@ -328,9 +328,9 @@ def bench_uneven(TJ, W, torch, dev, flush, steps: int, iters: int = 100) -> dict
     G.close()
     for P in probs:
         P.close()
-    # the same mix with AM_KERNEL_AUTO handles: the q <= 128 problems on the
-    # warp-pair group kernels, the q = 150 ones on the small-tile kernels,
-    # in one launch (FP32)
+    # the same mix with AM_KERNEL_AUTO handles: every problem on the
+    # warp-pair group kernels (two warps per trajectory for q <= 128, three
+    # for q = 150), in one launch (FP32)
     probs = [TJ.Problem(pb, kernel=TJ.AM_KERNEL_AUTO) for pb in pbs]
     reset()
     G = TJ.Group(probs)
@@ -359,7 +359,8 @@ def bench_uneven(TJ, W, torch, dev, flush, steps: int, iters: int = 100) -> dict
             "bf16": {"value": total * iters / (b_ms / 1e3), "unit": UNIT, "ms_per_solve": b_ms},
             "auto": {"value": total * iters / (a_ms / 1e3), "unit": UNIT, "ms_per_solve": a_ms,
                      "launches_per_solve": a_launches,
-                     "problems_on_warp_pair": sum(1 for pb in pbs if pb["q"] <= 128)},
+                     "problems_two_warps": sum(1 for pb in pbs if pb["q"] <= 128),
+                     "problems_three_warps": sum(1 for pb in pbs if 128 < pb["q"] <= 192)},
             "unit": UNIT, "ms_per_solve": g_ms, "problems": len(pbs), "trajectories": total,
             "iterations": iters, "work_items": items, "threads": threads, "launches_per_solve": launches,
             "achieved_tflops": flops / (g_ms / 1e3) / 1e12,

@@ -249,14 +249,14 @@ AM_API int am_get_history(am_problem *h, float *out, int mem);
  * am_solve_batch returns AM_ERR_ARG (nothing launched) for anything else or
  * when the shape's operands exceed the shared memory of an SM.  Results
  * agree with AM_KERNEL_FUSED to FP32 rounding, not bit for bit.
- * AM_KERNEL_WARP runs the same iteration (Sec. III-D, steps 1-5) with two
- * warps per trajectory for all iterations: after the constants are staged
- * the two warps of a trajectory synchronise only with each other, never
- * with the other trajectories of their CTA, which suits batches of a few
- * trajectories per SM (the paper's B = 1000).  Its contraction R is FP32
- * SIMT; it takes the FP32 precision form, the default alpha form and
- * q <= 128 (history included), and am_solve_batch returns AM_ERR_ARG
- * (nothing launched) for anything else.  Results agree with
+ * AM_KERNEL_WARP runs the same iteration (Sec. III-D, steps 1-5) with two,
+ * three or four warps per trajectory (q <= 128, 192, 256) for all
+ * iterations: after the constants are staged the warps of a trajectory
+ * synchronise only with each other, never with the other trajectories of
+ * their CTA, which suits batches of a few trajectories per SM (the paper's
+ * B = 1000).  Its contraction R is FP32 SIMT; it takes the FP32 precision
+ * form, the default alpha form and cs_boundary (history included), and
+ * am_solve_batch returns AM_ERR_ARG (nothing launched) for anything else.  Results agree with
  * AM_KERNEL_FUSED to FP32 rounding, not bit for bit.
  * AM_KERNEL_AUTO picks, per solve, AM_KERNEL_LARGE from B = 16384 on
  * (where it takes the problem), else AM_KERNEL_WARP where it takes the
@@ -267,7 +267,9 @@ AM_API int am_get_history(am_problem *h, float *out, int mem);
  * problem gives the same bits alone (with the kernel its handle selects
  * for that batch) and in a group.
  * AM_OPT_TILE: trajectories per CTA of the fused kernel (0 = automatic);
- * for AM_KERNEL_WARP, trajectories in flight per CTA, 1..7.
+ * for AM_KERNEL_WARP, trajectories in flight per CTA: 1..8 for q <= 128,
+ * 1..5 for q <= 192, 1..4 for q <= 256 (fewer where shared memory runs
+ * out; am_solve_batch returns AM_ERR_ARG then).
  * AM_OPT_SELECT: the best-trajectory rule of am_get_best and of grouped
  * and served solves when no trajectory is collision-free.  AM_SELECT_COST
  * (default): the lowest cost (Fig. 1's rule applied to every trajectory);

@@ -412,12 +412,12 @@ int am_solve_batch(am_problem *h, int B, const float *init, const float *warm_la
                     h->pp.q, h->pp.m, h->n, large_smem_bytes(h->L));
     if (kern == AM_KERNEL_WARP && !warp_supported(h->L))
         return fail(AM_ERR_ARG,
-                    "the warp-pair kernel takes the FP32 form, the default alpha form, cs_boundary, q <= 128 "
+                    "the warp-pair kernel takes the FP32 form, the default alpha form, cs_boundary, q <= 256 "
                     "and constants within an SM's shared memory (q=%d, m=%d, n=%d: %zu bytes)",
                     h->pp.q, h->pp.m, h->n, warp_smem_bytes(h->L, 1));
-    if (h->kernel == AM_KERNEL_WARP && (h->tile < 0 || h->tile > warp_max_traj()))
-        return fail(AM_ERR_ARG, "the warp-pair kernel runs 1..%d trajectories per CTA (tile %d)", warp_max_traj(),
-                    h->tile);
+    if (h->kernel == AM_KERNEL_WARP && (h->tile < 0 || h->tile > warp_max_traj(h->L)))
+        return fail(AM_ERR_ARG, "the warp-pair kernel runs 1..%d trajectories per CTA at q = %d (tile %d)",
+                    warp_max_traj(h->L), h->pp.q, h->tile);
     if (mem == AM_HOST) {
         if (init && !finite_floats(init, size_t(B) * 33)) return fail(AM_ERR_ARG, "non-finite initial coefficients");
         if (warm_lambda && !finite_floats(warm_lambda, size_t(B) * 55)) return fail(AM_ERR_ARG, "non-finite warm multipliers");
@@ -631,6 +631,7 @@ struct am_group {
     std::vector<int> h_items, solved_list;  // work lists; active list of the last solve
     int count[kGroupVariants] = {}, offset[kGroupVariants] = {};
     size_t vsmem[kGroupVariants] = {};      // shared memory per variant kernel
+    int vslots[kGroupVariants] = {};        // trajectory slots per CTA of a warp-pair variant
     // concurrent variant kernels: a stream each, fork and join events
     cudaStream_t vst[kGroupVariants] = {};
     cudaEvent_t fork_ev = nullptr, join_ev[kGroupVariants] = {};
@@ -640,6 +641,7 @@ struct am_group {
         cudaStream_t stream;
         const char *up;
         size_t smem[kGroupVariants];
+        int slots[kGroupVariants];
         cudaGraphExec_t exec;
     };
     std::vector<Captured> graphs;
@@ -670,14 +672,13 @@ std::vector<int> active_list(const am_group *g)
 // variant: the problems with the costliest tiles first (longest-processing-
 // time order), the tiles of one problem together so a CTA rarely re-stages
 // constants.
-// The group variant of a problem: the warp-pair kernels (32 + m - 1) when
-// its handle selects them and they take its shape, else the small-tile
+// The group variant of a problem: a warp-pair kernel (32 + 4 (NW - 2) + m - 1)
+// when its handle selects them and they take its shape, else the small-tile
 // variant of its precision form, circle count and alpha form.
 int problem_variant(const am_problem *h)
 {
-    if ((h->kernel == AM_KERNEL_WARP || h->kernel == AM_KERNEL_AUTO) && warp_supported(h->L) &&
-        warp_group_smem(h->L) <= kGroupSmemLimit)
-        return kGroupWarpVariant0 + h->L.m - 1;
+    if ((h->kernel == AM_KERNEL_WARP || h->kernel == AM_KERNEL_AUTO) && warp_group_traj(h->L) > 0)
+        return warp_group_variant(h->L);
     return group_variant(h->L);
 }
 
@@ -686,12 +687,20 @@ int build_work(am_group *g, int threads, int iters, int sms)
     const int np = int(g->probs.size());
     g->h_probs.resize(np);
     std::memset(static_cast<void *>(g->h_probs.data()), 0, sizeof(FusedProblem) * np);
-    for (int v = 0; v < kGroupVariants; ++v) g->vsmem[v] = 0;
+    for (int v = 0; v < kGroupVariants; ++v) g->vsmem[v] = 0, g->vslots[v] = 0;
+    // a warp-pair variant runs as many trajectory slots per CTA as all its
+    // problems fit
+    for (int i = 0; i < np; ++i) {
+        const int v = problem_variant(g->probs[i]);
+        if (v < kGroupWarpVariant0) continue;
+        const int t = warp_group_traj(g->probs[i]->L);
+        if (g->vslots[v] == 0 || t < g->vslots[v]) g->vslots[v] = t;
+    }
     for (int i = 0; i < np; ++i) {
         am_problem *h = g->probs[i];
         const int v = problem_variant(h);
         const bool warp = v >= kGroupWarpVariant0;
-        const int T = warp ? warp_group_traj() : group_tile(h->L, threads);
+        const int T = warp ? g->vslots[v] : group_tile(h->L, threads);
         if (T < 1) return fail(AM_ERR_ARG, "problem %d (q=%d, n=%d) does not fit a block of %d", i, h->pp.q, h->n, threads);
         FusedProblem &f = g->h_probs[i];
         f.cblob = h->d_blob;
@@ -707,7 +716,7 @@ int build_work(am_group *g, int threads, int iters, int sms)
         f.mind = h->d_out + 3 * size_t(h->B);
         f.hist = nullptr;
         f.err = h->d_err;  // a failed wait shows in the problem's own getters
-        const size_t sm = warp ? warp_group_smem(h->L) : fused_smem_bytes(h->L, T);
+        const size_t sm = warp ? warp_smem_bytes(h->L, T) : fused_smem_bytes(h->L, T);
         if (sm > g->vsmem[v]) g->vsmem[v] = sm;
     }
     // Tiles of the active problems: each problem gets a share of the SMs in
@@ -821,6 +830,7 @@ int issue_variants(am_group *g, uint64_t mask, int threads, int sms, bool fixed_
         if (!(mask >> v & 1ull)) continue;
         gl.variant = v;
         gl.smem = g->vsmem[v];
+        gl.slots = g->vslots[v];
         gl.grid = fixed_grid || g->count[v] > sms ? sms : g->count[v];
         cudaStream_t s = st;
         if (nv > 1) {
@@ -868,7 +878,7 @@ int group_launch(am_group *g, int iters, cudaStream_t st)
     am_group::Captured *hit = nullptr;
     for (auto &c : g->graphs)
         if (c.mask == mask && c.threads == threads && c.stream == st && c.up == g->d_up &&
-            !std::memcmp(c.smem, g->vsmem, sizeof(c.smem)))
+            !std::memcmp(c.smem, g->vsmem, sizeof(c.smem)) && !std::memcmp(c.slots, g->vslots, sizeof(c.slots)))
             hit = &c;
     if (!hit) {
         if (g->graphs.size() >= 16) drop_graph(g);
@@ -886,6 +896,7 @@ int group_launch(am_group *g, int iters, cudaStream_t st)
         c.stream = st;
         c.up = g->d_up;
         std::memcpy(c.smem, g->vsmem, sizeof(c.smem));
+        std::memcpy(c.slots, g->vslots, sizeof(c.slots));
         e = cudaGraphInstantiate(&c.exec, graph_obj, 0);
         cudaGraphDestroy(graph_obj);
         if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");

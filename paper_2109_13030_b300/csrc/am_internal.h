@@ -153,19 +153,23 @@ int large_supported(const ConstLayout &L, bool hist);
 size_t large_smem_bytes(const ConstLayout &L);
 int launch_large(const SolveArgs &a, void *stream, int *launches);
 
-// Warp-pair fused kernel (two warps run every iteration of one trajectory;
-// no block barrier inside the loop).  warp_supported: 1 when the form and
-// shape fit it (FP32 precision form, default alpha form, q <= 128, shared
-// memory within the limit), else 0; launch_warp returns -1 then.
+// Warp-pair fused kernel (NW = 2, 3 or 4 warps run every iteration of one
+// trajectory, for q <= 128, 192, 256; no block barrier inside the loop).
+// warp_supported: 1 when the form and shape fit it (FP32 precision form,
+// default alpha form, cs_boundary, q <= 256, shared memory within the
+// limit), else 0; launch_warp returns -1 then.
 int warp_supported(const ConstLayout &L);
 size_t warp_smem_bytes(const ConstLayout &L, int traj_per_cta);
-int warp_max_traj();
+int warp_max_traj(const ConstLayout &L);
 int warp_auto_traj(const ConstLayout &L, int B, int sms);
 int launch_warp(const SolveArgs &a, void *stream, int *launches);
-// The warp-pair group kernels (variants 32..35): seven trajectory slots per
-// CTA; the shared memory a problem needs in them.
-int warp_group_traj();
-size_t warp_group_smem(const ConstLayout &L);
+// The warp-pair group kernels (variants 32..43, one per circle count and
+// NW): up to 16 / NW trajectory slots per CTA, one count per launch.
+// warp_group_traj: the most slots a problem fits in kGroupSmemLimit (0 when
+// not even one fits); warp_smem_bytes(L, slots) is what it needs at a given
+// count; warp_group_variant: its variant.
+int warp_group_traj(const ConstLayout &L);
+int warp_group_variant(const ConstLayout &L);
 
 // Dynamic shared memory of the single-problem kernels; the debug build's
 // static flag needs a little of the 227 KB.
@@ -194,11 +198,12 @@ constexpr float kNearMargin = 0.6f;
 // variant (circle count, alpha form) present; the variant kernels of one
 // solve run concurrently.
 // Variants 0..31: the small-tile group kernels, precision (4) x circle count
-// (4) x alpha form (2); 32..35: the warp-pair group kernels (FP32, default
-// alpha form) for 1..4 circles, for problems whose handle selects the
+// (4) x alpha form (2); 32..43: the warp-pair group kernels (FP32, default
+// alpha form), 32 + 4 (NW - 2) + m - 1 for NW = 2, 3, 4 warps per
+// trajectory and 1..4 circles, for problems whose handle selects the
 // warp-pair kernel (AM_KERNEL_WARP or AM_KERNEL_AUTO) and whose shape it takes.
 constexpr int kGroupWarpVariant0 = 32;
-constexpr int kGroupVariants = 36;
+constexpr int kGroupVariants = 44;
 // Dynamic shared memory a warp-pair group kernel may take (its problem
 // descriptor and work-item slot are static shared memory).
 constexpr size_t kGroupSmemLimit = 227 * 1024 - 1024;
@@ -213,6 +218,7 @@ struct GroupLaunch {
     int threads;
     size_t smem;
     int grid;
+    int slots;                    // warp-pair variants: trajectory slots per CTA
 };
 int group_variant(const ConstLayout &L);
 // Tile size (trajectories per CTA) of a problem in a grouped launch of the

@@ -63,21 +63,19 @@
 namespace trajam {
 namespace {
 
-constexpr int kWMaxTraj = 7;      // trajectories in flight per CTA (two warps each)
-constexpr int kWThreads = 64;     // threads per trajectory
-constexpr int kWMaxQ = 128;       // 64 pairs: one per lane of the two halves
-constexpr int kRS = 68;           // row stride of the transpose rows: 64 partials + 4 (4 mod 32 banks)
+constexpr int kWMaxQ = 256;       // 128 pairs: one per lane of four warps
+constexpr int kWMaxWarps = 16;    // warps per CTA (128 registers each: four per scheduler)
 // Floats per pair of steps in the pair-interleaved copy of Pd, Pdd: 11
 // float2 entries (B(t, k), B(t + 1, k)) and padding; 28 = 4 x 7, so the
-// 128-bit loads of eight neighbouring pairs fall on distinct banks.  Pair 64
-// is all zero: lanes without a pair read it.
+// 128-bit loads of eight neighbouring pairs fall on distinct banks.  Pair
+// 32 NW is all zero: lanes without a pair read it.
 constexpr int kPB = 28;
-constexpr int kPairs = 65;
 // Row stride of the Minv and MQ rows (24 padded columns): 28, for the same
 // reason, so the owner lanes' 128-bit row loads do not share banks.
 constexpr int kMR = 28;
 
-// Per-trajectory shared-memory area (float offsets from the trajectory's base).
+// Per-trajectory shared-memory area (float offsets from the trajectory's
+// base); NW warps per trajectory, C = 32 NW lane columns.
 constexpr int kWxd = 0;       // [2][12][8] xi1 duplicated per coefficient k:
                               //            (cx, cx, cy, cy, cc, cc, cs, cs), both buffers
 constexpr int kWx2d = 192;    // [2][12][2] xi2 duplicated, both buffers
@@ -86,13 +84,27 @@ constexpr int kWx2 = 336;     // [2][12]    xi2, both buffers
 constexpr int kWu = 360;      // [48]       lam + coef R, the position step's input
 constexpr int kWv = 408;      // [12]       lam_psi + rho P^T delta, the heading step's input
 constexpr int kWdx2 = 420;    // [12]       the last increment of xi2
-constexpr int kWsum = 432;    // [2][4] double: per half, the sums of the last sweep (res, res_psi, cost, dmin)
-constexpr int kWsdx2 = 448;   // [12]       the sum of the heading increments over the iterations
-constexpr int kWacc = 464;    // [4][64] float4: per lane, its residual rows summed over the iterations
-constexpr int kWeb = 1488;    // [5][64] float4: per lane, the boundary control points' share of its
-                              //            values (x, xd | xdd, c | y, yd | ydd, s | psi, psidd)
-constexpr int kWred = 2768;   // [44][kRS]  transpose rows of the reductions over the steps
-constexpr int kTrajFloats = kWred + 44 * kRS;
+constexpr int kWsum = 432;    // [NW][4] double: per warp, the sums of the last sweep (res, res_psi, cost, dmin)
+constexpr int kWsdx2 = 464;   // [12]       the sum of the heading increments over the iterations
+constexpr int kWacc = 480;    // [4][C] float4: per lane, its residual rows summed over the iterations
+// then  eb  [5][C] float4: per lane, the boundary control points' share of its
+//                          values (x, xd | xdd, c | y, yd | ydd, s | psi, psidd)
+//       red [44][C + 4]    transpose rows of the reductions over the steps
+//                          (the stride is 4 mod 32 banks)
+template <int NW>
+struct WS {
+    static constexpr int kThreads = 32 * NW;              // threads per trajectory
+    static constexpr int kCols = 32 * NW;                 // lane columns of the transpose rows
+    static constexpr int kRS = kCols + 4;                 // their row stride
+    static constexpr int kMaxTraj = kWMaxWarps / NW;      // trajectories in flight per CTA
+    static constexpr int kPairs = 32 * NW + 1;            // pairs of the Pd, Pdd copy, the last all zero
+    static constexpr int kEb = kWacc + 16 * kCols;
+    static constexpr int kRed = kEb + 20 * kCols;
+    static constexpr int kTrajFloats = kRed + 44 * kRS;
+};
+
+// Warps per trajectory for a horizon of q steps: one pair of steps per lane.
+__host__ __device__ constexpr int warps_for_q(int q) { return q <= 128 ? 2 : q <= 192 ? 3 : 4; }
 
 // Interior control points.  Every polynomial block has boundary rows (the
 // slack blocks too, with cs_boundary): they fix control points 0, 1, 2 and
@@ -127,13 +139,14 @@ __shared__ int g_woob;
 //   mir    [22][kMR] Minv by rows, columns in blocks of 12 per polynomial
 //   mqr    [22][kMR] MQ by rows, the same columns
 //   mpr    [11][12] Mpsi by rows;  mhr [11][12] Mpsi H by rows;  ptr [11][12] P^T P by rows
-//   pb     [2][65][kPB] Pd, Pdd per pair of steps j: (B(2j, k), B(2j + 1, k))
+//   pb     [2][32 NW + 1][kPB] Pd, Pdd per pair of steps j: (B(2j, k), B(2j + 1, k))
 //          for k = 0..10, zero past the horizon
-//   traj   T x kTrajFloats
+//   traj   T x WS<NW>::kTrajFloats
 struct WSmem {
     int bar, cst, cob, mir, mqr, mpr, mhr, ptr, pb, traj, total;
 };
 
+template <int NW>
 __host__ __device__ inline WSmem wsmem_layout(const ConstLayout &L, int T)
 {
     WSmem s;
@@ -147,8 +160,8 @@ __host__ __device__ inline WSmem wsmem_layout(const ConstLayout &L, int T)
     s.mpr = o; o += NV * 12;
     s.mhr = o; o += NV * 12;
     s.ptr = o; o += NV * 12;
-    s.pb = o; o += 2 * kPairs * kPB;
-    s.traj = o; o += T * kTrajFloats;
+    s.pb = o; o += 2 * WS<NW>::kPairs * kPB;
+    s.traj = o; o += T * WS<NW>::kTrajFloats;
     s.total = o;
     return s;
 }
@@ -160,11 +173,12 @@ __device__ __forceinline__ float2 fmul2(float2 a, float2 b) { return __fmul2_rn(
 __device__ __forceinline__ float2 fadd2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 fsub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
 
-// The two warps of a trajectory meet: named barrier id (1..7) of 64 threads.
+// The NW warps of a trajectory meet: named barrier id (1..8) of 32 NW threads.
+template <int NW>
 __device__ __forceinline__ void pair_sync(int id)
 {
     __syncwarp();
-    asm volatile("bar.sync %0, %1;\n" :: "r"(id), "r"(kWThreads) : "memory");
+    asm volatile("bar.sync %0, %1;\n" :: "r"(id), "r"(WS<NW>::kThreads) : "memory");
 }
 
 // Padded index (blocks of 12) of state entry o = blk * 11 + k of xi1 or lam.
@@ -223,6 +237,7 @@ struct WSlot {
 // rows: [3][q][12] P, Pd, Pdd in global memory (P read once per warp); pb:
 // the shared-memory copy of Pd, Pdd per pair (jb: the lane's pair, or the
 // zero pair 64 for a lane without one).
+template <int NW>
 __device__ __forceinline__ void load_basis(const float *rows, const float *pb, int jb, bool valid, bool v1,
                                            WBasis &b)
 {
@@ -231,7 +246,7 @@ __device__ __forceinline__ void load_basis(const float *rows, const float *pb, i
     for (int k = 0; k < NV; ++k)
         b.P[k] = valid ? f2(__ldg(rows + t0 * 12 + k), v1 ? __ldg(rows + t1 * 12 + k) : 0.f) : f2(0.f, 0.f);
     b.pd = reinterpret_cast<const float4 *>(pb + jb * kPB);
-    b.pdd = reinterpret_cast<const float4 *>(pb + (kPairs + jb) * kPB);
+    b.pdd = reinterpret_cast<const float4 *>(pb + (WS<NW>::kPairs + jb) * kPB);
 }
 
 // Pd or Pdd entry k of a pair from its float4 copy (two k per float4).
@@ -286,8 +301,10 @@ __device__ __forceinline__ void heading_pair(const float4 *x2, const WBasis &b, 
 // heading (and its second derivative) at the pair: constant over the
 // iterations, since those points never move.  Formed once per trajectory
 // from the reference (buffer 0) into the lane's slots of eb.
+template <int NW>
 __device__ __forceinline__ void eval_boundary(const float4 *xd, const float4 *x2, const WBasis &b, float4 *eb)
 {
+    constexpr int C = WS<NW>::kCols;
     const float2 z = f2(0.f, 0.f);
     WVals r{z, z, z, z, z, z, z, z};
     float2 ps = z, pdd = z;
@@ -311,17 +328,19 @@ __device__ __forceinline__ void eval_boundary(const float4 *xd, const float4 *x2
         pdd = ffma2(pe, c2, pdd);
     }
     eb[0] = make_float4(r.x.x, r.x.y, r.xd.x, r.xd.y);
-    eb[64] = make_float4(r.xdd.x, r.xdd.y, r.c.x, r.c.y);
-    eb[128] = make_float4(r.y.x, r.y.y, r.yd.x, r.yd.y);
-    eb[192] = make_float4(r.ydd.x, r.ydd.y, r.s.x, r.s.y);
-    eb[256] = make_float4(ps.x, ps.y, pdd.x, pdd.y);
+    eb[C] = make_float4(r.xdd.x, r.xdd.y, r.c.x, r.c.y);
+    eb[2 * C] = make_float4(r.y.x, r.y.y, r.yd.x, r.yd.y);
+    eb[3 * C] = make_float4(r.ydd.x, r.ydd.y, r.s.x, r.s.y);
+    eb[4 * C] = make_float4(ps.x, ps.y, pdd.x, pdd.y);
 }
 
 // Trajectory values at the pair: the boundary share plus the interior
 // control points 3..7 of the duplicated xi1.
+template <int NW>
 __device__ __forceinline__ void eval_interior(const float4 *xd, const WBasis &b, const float4 *eb, WVals &r)
 {
-    const float4 e0 = eb[0], e1 = eb[64], e2 = eb[128], e3 = eb[192];
+    constexpr int C = WS<NW>::kCols;
+    const float4 e0 = eb[0], e1 = eb[C], e2 = eb[2 * C], e3 = eb[3 * C];
     r = WVals{f2(e0.x, e0.y), f2(e0.z, e0.w), f2(e1.x, e1.y), f2(e2.x, e2.y),
               f2(e2.z, e2.w), f2(e3.x, e3.y), f2(e1.z, e1.w), f2(e3.z, e3.w)};
     float4 d, e;
@@ -347,11 +366,11 @@ __device__ __forceinline__ void eval_interior(const float4 *xd, const WBasis &b,
 
 // Heading (and with DD its second derivative) at the pair: the boundary
 // share plus the interior control points of the duplicated xi2.
-template <bool DD>
+template <int NW, bool DD>
 __device__ __forceinline__ void heading_interior(const float4 *x2, const WBasis &b, const float4 *eb, float2 &p,
                                                  float2 &dd)
 {
-    const float4 e4 = eb[256];
+    const float4 e4 = eb[4 * WS<NW>::kCols];
     p = f2(e4.x, e4.y);
     dd = f2(e4.z, e4.w);
     float4 v, w;
@@ -542,72 +561,66 @@ __device__ __forceinline__ double warp_sum(double v)
 }
 
 // Sum of transpose row o (the 64 lane partials) in a fixed order.
+// Sum of F float4s of partials of transpose row o (row stride rs) from
+// column c0 (a multiple of 4), in a fixed order: two running sums over the
+// float4s, or for F = 4 a tree.
+template <int F>
+__device__ __forceinline__ float row_part(const float *red, int o, int c0, int rs)
+{
+    const float4 *r = reinterpret_cast<const float4 *>(red + o * rs + c0);
+    if constexpr (F == 4) {
+        const float4 a = r[0], b = r[1], c = r[2], d = r[3];
+        return (((a.x + b.x) + (c.x + d.x)) + ((a.y + b.y) + (c.y + d.y))) +
+               (((a.z + b.z) + (c.z + d.z)) + ((a.w + b.w) + (c.w + d.w)));
+    } else {
+        float4 a = r[0], b = r[1];
+#pragma unroll
+        for (int i = 2; i < F; i += 2) {
+            const float4 v = r[i];
+            a.x += v.x;
+            a.y += v.y;
+            a.z += v.z;
+            a.w += v.w;
+            if (i + 1 < F) {
+                const float4 w = r[i + 1];
+                b.x += w.x;
+                b.y += w.y;
+                b.z += w.z;
+                b.w += w.w;
+            }
+        }
+        return ((a.x + b.x) + (a.y + b.y)) + ((a.z + b.z) + (a.w + b.w));
+    }
+}
+
+// Sum of the 32 NW partials of transpose row o.
+template <int NW>
 __device__ __forceinline__ float row_sum(const float *red, int o)
 {
-    const float4 *r = reinterpret_cast<const float4 *>(red + o * kRS);
-    float4 a = r[0], b = r[1];
-#pragma unroll
-    for (int i = 2; i < 16; i += 2) {
-        const float4 v = r[i], w = r[i + 1];
-        a.x += v.x;
-        a.y += v.y;
-        a.z += v.z;
-        a.w += v.w;
-        b.x += w.x;
-        b.y += w.y;
-        b.z += w.z;
-        b.w += w.w;
-    }
-    return ((a.x + b.x) + (a.y + b.y)) + ((a.z + b.z) + (a.w + b.w));
+    return row_part<8 * NW>(red, o, 0, WS<NW>::kRS);
 }
 
-// Sum of 32 partials of transpose row o starting at column c0 (a multiple
-// of 4), in a fixed order.
-__device__ __forceinline__ float row_part32(const float *red, int o, int c0)
+// R for the owner lanes 0..9 of warps 0 and 1 (side x, side y): each row
+// is summed by lanes l and l + 16 (the two halves of the columns), joined
+// by one shuffle.  Every lane of the warp takes part in the shuffle; other
+// warps own no component.
+template <int NW>
+__device__ __forceinline__ float r_rows(const float *red, int w, int lane)
 {
-    const float4 *r = reinterpret_cast<const float4 *>(red + o * kRS + c0);
-    float4 a = r[0], b = r[1];
-#pragma unroll
-    for (int i = 2; i < 8; i += 2) {
-        const float4 v = r[i], w = r[i + 1];
-        a.x += v.x;
-        a.y += v.y;
-        a.z += v.z;
-        a.w += v.w;
-        b.x += w.x;
-        b.y += w.y;
-        b.z += w.z;
-        b.w += w.w;
-    }
-    return ((a.x + b.x) + (a.y + b.y)) + ((a.z + b.z) + (a.w + b.w));
-}
-
-// The same for 16 partials.
-__device__ __forceinline__ float row_part16(const float *red, int o, int c0)
-{
-    const float4 *r = reinterpret_cast<const float4 *>(red + o * kRS + c0);
-    const float4 a = r[0], b = r[1], c = r[2], d = r[3];
-    return (((a.x + b.x) + (c.x + d.x)) + ((a.y + b.y) + (c.y + d.y))) +
-           (((a.z + b.z) + (c.z + d.z)) + ((a.w + b.w) + (c.w + d.w)));
-}
-
-// R for the owner lanes 0..9 of a half: each row is summed by lanes l and
-// l + 16 (columns 0..31 and 32..63), joined by one shuffle.  Every lane of
-// the warp takes part in the shuffle.
-__device__ __forceinline__ float r_rows(const float *red, int half, int lane)
-{
+    if (w >= 2) return 0.f;
     const int l = lane & 15;
-    const float s = l < 2 * kNI ? row_part32(red, 2 * kNI * half + l, 32 * (lane >> 4)) : 0.f;
+    const float s = l < 2 * kNI ? row_part<4 * NW>(red, 2 * kNI * w + l, 16 * NW * (lane >> 4), WS<NW>::kRS) : 0.f;
     return s + __shfl_xor_sync(0xffffffffu, s, 16);
 }
 
 // P^T delta for lanes 0..4 (rows 0..4, interior k = 3..7): each row is
-// summed by lanes k, k + 8, k + 16, k + 24 (16 columns each), joined by two
-// shuffles.  Every lane of the warp takes part.
+// summed by lanes k, k + 8, k + 16, k + 24 (a quarter of the columns each),
+// joined by two shuffles.  Every lane of the warp takes part.
+template <int NW>
 __device__ __forceinline__ float ptd_rows(const float *red, int lane)
 {
     const int l = lane & 7;
-    float s = l < kNI ? row_part16(red, l, 16 * (lane >> 3)) : 0.f;
+    float s = l < kNI ? row_part<2 * NW>(red, l, 8 * NW * (lane >> 3), WS<NW>::kRS) : 0.f;
     s += __shfl_xor_sync(0xffffffffu, s, 8);
     return s + __shfl_xor_sync(0xffffffffu, s, 16);
 }
@@ -616,8 +629,10 @@ __device__ __forceinline__ float ptd_rows(const float *red, int lane)
 // of the transpose rows: R_pos[side][k] = Pd^T rv + Pdd^T ra + P^T r0 and
 // R_slack[side][k] = P^T r1 (state order o = 11 blk + k: c_x pos, c_c slack,
 // c_y pos, c_s slack).
+template <int NW>
 __device__ __forceinline__ void dot_partials(float *red, int c, const WBasis &b, const WRes &g)
 {
+    constexpr int kRS = WS<NW>::kRS;
     float4 d, e;
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
@@ -640,8 +655,10 @@ __device__ __forceinline__ void dot_partials(float *red, int c, const WBasis &b,
 
 // The interior components of the lane's partial of R (k = 3..7 of each
 // block), to column c of transpose rows 0..19 (o' = 5 blk + k - 3).
+template <int NW>
 __device__ __forceinline__ void dot_interior(float *red, int c, const WBasis &b, const WRes &g)
 {
+    constexpr int kRS = WS<NW>::kRS;
     float4 d, e;
 #pragma unroll
     for (int k = kI0; k < kI0 + kNI; ++k) {
@@ -665,50 +682,56 @@ __device__ __forceinline__ void dot_interior(float *red, int c, const WBasis &b,
 
 // Adds the lane's residual rows to its running sums (slot-major float4s,
 // consecutive lanes on consecutive words).
+template <int NW>
 __device__ __forceinline__ void acc_rows(float *ta, int col, const WRes &g)
 {
+    constexpr int C = WS<NW>::kCols;
     float4 *a = reinterpret_cast<float4 *>(ta + kWacc) + col;
-    const float4 a0 = a[0], a1 = a[64], a2 = a[128], a3 = a[192];
+    const float4 a0 = a[0], a1 = a[C], a2 = a[2 * C], a3 = a[3 * C];
     a[0] = make_float4(a0.x + g.vx.x, a0.y + g.vx.y, a0.z + g.ax.x, a0.w + g.ax.y);
-    a[64] = make_float4(a1.x + g.r0x.x, a1.y + g.r0x.y, a1.z + g.r1x.x, a1.w + g.r1x.y);
-    a[128] = make_float4(a2.x + g.vy.x, a2.y + g.vy.y, a2.z + g.ay.x, a2.w + g.ay.y);
-    a[192] = make_float4(a3.x + g.r0y.x, a3.y + g.r0y.y, a3.z + g.r1y.x, a3.w + g.r1y.y);
+    a[C] = make_float4(a1.x + g.r0x.x, a1.y + g.r0x.y, a1.z + g.r1x.x, a1.w + g.r1x.y);
+    a[2 * C] = make_float4(a2.x + g.vy.x, a2.y + g.vy.y, a2.z + g.ay.x, a2.w + g.ay.y);
+    a[3 * C] = make_float4(a3.x + g.r0y.x, a3.y + g.r0y.y, a3.z + g.r1y.x, a3.w + g.r1y.y);
 }
 
+template <int NW>
 __device__ __forceinline__ WRes acc_load(const float *ta, int col)
 {
+    constexpr int C = WS<NW>::kCols;
     const float4 *a = reinterpret_cast<const float4 *>(ta + kWacc) + col;
-    const float4 a0 = a[0], a1 = a[64], a2 = a[128], a3 = a[192];
+    const float4 a0 = a[0], a1 = a[C], a2 = a[2 * C], a3 = a[3 * C];
     return WRes{f2(a0.x, a0.y), f2(a0.z, a0.w), f2(a1.x, a1.y), f2(a1.z, a1.w),
                 f2(a2.x, a2.y), f2(a2.z, a2.w), f2(a3.x, a3.y), f2(a3.z, a3.w)};
 }
 
-// The whole AM loop for one trajectory on its two warps.  half: 0 or 1 (the
-// warp's role); b: the lane's basis rows; bid: the pair's named barrier.
-template <int M>
-__device__ void traj_solve(const FusedProblem &p, const float *sm, const WSmem &S, float *ta, int traj, int half,
+// The whole AM loop for one trajectory on its NW warps.  wi: the warp's index
+// within the trajectory (0, 1: the sides of the position step; 0: the
+// heading step); b: the lane's basis rows; bid: the trajectory's named
+// barrier.
+template <int M, int NW>
+__device__ void traj_solve(const FusedProblem &p, const float *sm, const WSmem &S, float *ta, int traj, int wi,
                            int lane, int bid, const WBasis &b, int jp, bool valid, bool v1)
 {
     const ConstLayout &L = p.L;
     const float *cst = sm + S.cst;
     const float *cob = sm + S.cob;
-    float *red = ta + kWred;
-    const int col = 32 * half + lane;        // the lane's column of the transpose rows
-    // lanes 0..9 of half h own the interior position-step outputs of side h:
-    // block 2h + lane / 5, control point 3 + lane % 5
-    const bool owner = lane < 2 * kNI;
-    const int oblk = 2 * half + lane / kNI, ok = kI0 + lane % kNI;
+    float *red = ta + WS<NW>::kRed;
+    const int col = 32 * wi + lane;        // the lane's column of the transpose rows
+    // lanes 0..9 of warp h < 2 own the interior position-step outputs of
+    // side h: block 2h + lane / 5, control point 3 + lane % 5
+    const bool owner = wi < 2 && lane < 2 * kNI;
+    const int oblk = 2 * wi + lane / kNI, ok = kI0 + lane % kNI;
     const int o = NV * oblk + ok, pp = 12 * oblk + ok, orow = NV * (oblk & 1) + ok;
-    // lanes 0..4 of half 0 own the interior heading coefficients k = 3 + lane
-    const bool psi_lane = half == 0 && lane < kNI;
+    // lanes 0..4 of warp 0 own the interior heading coefficients k = 3 + lane
+    const bool psi_lane = wi == 0 && lane < kNI;
     const int pk = kI0 + lane;
     const float rho = L.rho;
 
-    // ---- state: xi1, xi2 as given into buffer 1 (half 0), lam and lam_psi
+    // ---- state: xi1, xi2 as given into buffer 1 (wi 0), lam and lam_psi
     // to the owner lanes' registers, then the reference into buffer 0
     if (!AM_WBOUND(traj >= 0 && traj < p.B)) return;
     const float *gs = p.state + (size_t)traj * STATE;
-    if (half == 0) {
+    if (wi == 0) {
         for (int e = lane; e < 55; e += 32) {
             const float v = gs[e];
             if (e < 44) put_xi1(ta, 1, pidx(e), v);
@@ -718,15 +741,16 @@ __device__ void traj_solve(const FusedProblem &p, const float *sm, const WSmem &
     float lam = owner ? gs[55 + o] : 0.f;
     float lps = psi_lane ? gs[99 + pk] : 0.f;
     {
+        constexpr int C = WS<NW>::kCols;
         float4 *a = reinterpret_cast<float4 *>(ta + kWacc) + col;
-        a[0] = a[64] = a[128] = a[192] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (half == 0 && lane < 12) ta[kWsdx2 + lane] = 0.f;
+        a[0] = a[C] = a[2 * C] = a[3 * C] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (wi == 0 && lane < 12) ta[kWsdx2 + lane] = 0.f;
     }
     float2 dsum = f2(0.f, 0.f);  // the lane's delta summed over the iterations
-    pair_sync(bid);
+    pair_sync<NW>(bid);
     // boundary control points from the boundary conditions on every block with
     // boundary rows, the rest as given (entries split between the halves)
-    for (int e = col; e < 55; e += kWThreads) {
+    for (int e = col; e < 55; e += WS<NW>::kThreads) {
         const int blk = e / NV, k = e - NV * blk;
         const bool has_bc = (blk == 0 || blk == 2 || blk == 4 || L.cs_boundary);
         float v = blk < 4 ? ta[kWxi + 48 + blk * 12 + k] : ta[kWx2 + 12 + k];
@@ -735,7 +759,7 @@ __device__ void traj_solve(const FusedProblem &p, const float *sm, const WSmem &
         if (blk < 4) put_xi1(ta, 0, blk * 12 + k, v);
         else put_xi2(ta, 0, k, v);
     }
-    pair_sync(bid);
+    pair_sync<NW>(bid);
 
     WSlot st;
     st.nrx = st.nry = f2(3.0e18f, 3.0e18f);  // no near list yet
@@ -758,21 +782,21 @@ __device__ void traj_solve(const FusedProblem &p, const float *sm, const WSmem &
         sweep_pair<M, false, false, true>(cob, L, pg, z2, jp, valid, v1, r, f, st, g, sums);
         st.psi_cur = pr;
     }
-    dot_interior(red, col, b, g);
-    pair_sync(bid);
-    float R = r_rows(red, half, lane);  // owner lanes: their component of R
+    dot_interior<NW>(red, col, b, g);
+    pair_sync<NW>(bid);
+    float R = r_rows<NW>(red, wi, lane);  // owner lanes: their component of R
     // The boundary points never move from here on: both buffers take the
     // reference's (buffer 1 held the given samples for the first step).
-    if (half == 0) {
+    if (wi == 0) {
         for (int e = lane; e < 30; e += 32) {
             const int blk = e / 6, i = e - 6 * blk, k = i < 3 ? i : i + 5;
             if (blk < 4) put_xi1(ta, 1, blk * 12 + k, ta[kWxi + blk * 12 + k]);
             else put_xi2(ta, 1, k, ta[kWx2 + k]);
         }
     }
-    const float4 *eb = reinterpret_cast<const float4 *>(ta + kWeb) + col;
-    eval_boundary(reinterpret_cast<const float4 *>(ta + kWxd), reinterpret_cast<const float4 *>(ta + kWx2d), b,
-                  reinterpret_cast<float4 *>(ta + kWeb) + col);
+    const float4 *eb = reinterpret_cast<const float4 *>(ta + WS<NW>::kEb) + col;
+    eval_boundary<NW>(reinterpret_cast<const float4 *>(ta + kWxd), reinterpret_cast<const float4 *>(ta + kWx2d), b,
+                  reinterpret_cast<float4 *>(ta + WS<NW>::kEb) + col);
 
     float ptp = 0.f;  // heading lanes: P^T delta of the last heading step
     int cur = 0, cur2 = 0;
@@ -804,8 +828,8 @@ __device__ void traj_solve(const FusedProblem &p, const float *sm, const WSmem &
             if (owner) {
                 const float4 *mr = reinterpret_cast<const float4 *>(sm + S.mir + orow * kMR);
                 const float4 *qr = reinterpret_cast<const float4 *>(sm + S.mqr + orow * kMR);
-                const float4 *uu = reinterpret_cast<const float4 *>(ta + kWu + 24 * half);
-                const float4 *xx = reinterpret_cast<const float4 *>(ta + kWxi + cur * 48 + 24 * half);
+                const float4 *uu = reinterpret_cast<const float4 *>(ta + kWu + 24 * wi);
+                const float4 *xx = reinterpret_cast<const float4 *>(ta + kWxi + cur * 48 + 24 * wi);
                 // Minv u over the interior columns 3..7 and 15..19 (u is zero
                 // elsewhere); MQ xi1 over every column, in order
                 float a0 = 0.f, a1 = 0.f;
@@ -829,14 +853,14 @@ __device__ void traj_solve(const FusedProblem &p, const float *sm, const WSmem &
                 put_xi1(ta, cur ^ 1, pp, ta[kWxi + cur * 48 + pp] + (a0 - a1));
             }
             cur ^= 1;
-            pair_sync(bid);
+            pair_sync<NW>(bid);
         }
         const bool res = (p.hist != nullptr) || (it == p.iters - 1);
         const bool fin = it == p.iters - 1;
         // ---- EVAL: trajectory values, heading target, the lane's P^T delta
         WVals r;
         {
-            eval_interior(reinterpret_cast<const float4 *>(ta + kWxd) + cur * 24, b, eb, r);
+            eval_interior<NW>(reinterpret_cast<const float4 *>(ta + kWxd) + cur * 24, b, eb, r);
             // psi_t = psi + wrap(atan2(s, c) - psi), psi the previous heading;
             // the heading step works on delta = psi_t - P xi2
             st.psi_t.x = st.psi_prev.x + wrap_pi(atan2_heading(r.s.x, r.c.x) - st.psi_prev.x);
@@ -847,13 +871,13 @@ __device__ void traj_solve(const FusedProblem &p, const float *sm, const WSmem &
 #pragma unroll
             for (int k = kI0; k < kI0 + kNI; ++k) {
                 const float2 m = fmul2(b.P[k], dd);
-                red[(k - kI0) * kRS + col] = m.x + m.y;
+                red[(k - kI0) * WS<NW>::kRS + col] = m.x + m.y;
             }
-            pair_sync(bid);
+            pair_sync<NW>(bid);
         }
         // ---- PSI: the heading step of Eq. compute_convex_surrogate in increment form
-        if (half == 0) {
-            ptp = ptd_rows(red, lane);
+        if (wi == 0) {
+            ptp = ptd_rows<NW>(red, lane);
             if (psi_lane) ta[kWv + pk] = fmaf(rho, ptp, lps);  // the boundary entries of v stay zero
             __syncwarp();
             if (psi_lane) {
@@ -887,18 +911,18 @@ __device__ void traj_solve(const FusedProblem &p, const float *sm, const WSmem &
             }
         }
         cur2 ^= 1;
-        pair_sync(bid);
+        pair_sync<NW>(bid);
         // ---- SWEEP and DOT
         {
             const float4 *x2d = reinterpret_cast<const float4 *>(ta + kWx2d) + cur2 * 6;
             float2 ps, pdd;
-            if (res) heading_interior<true>(x2d, b, eb, ps, pdd);
-            else heading_interior<false>(x2d, b, eb, ps, pdd);
+            if (res) heading_interior<NW, true>(x2d, b, eb, ps, pdd);
+            else heading_interior<NW, false>(x2d, b, eb, ps, pdd);
             if (fin) sweep_pair<M, true, true, false>(cob, L, ps, pdd, jp, valid, v1, r, r, st, g, sums);
             else if (res) sweep_pair<M, true, false, false>(cob, L, ps, pdd, jp, valid, v1, r, r, st, g, sums);
             else sweep_pair<M, false, false, false>(cob, L, ps, pdd, jp, valid, v1, r, r, st, g, sums);
-            acc_rows(ta, col, g);
-            dot_interior(red, col, b, g);
+            acc_rows<NW>(ta, col, g);
+            dot_interior<NW>(red, col, b, g);
             double *hs = reinterpret_cast<double *>(ta + kWsum);
             if (res) {
                 // the sums over the steps of the residuals and the cost in FP64
@@ -912,16 +936,24 @@ __device__ void traj_solve(const FusedProblem &p, const float *sm, const WSmem &
                     for (int off = 16; off >= 1; off >>= 1) dm = fminf(dm, __shfl_xor_sync(0xffffffffu, dm, off));
                 }
                 if (lane == 0) {
-                    hs[4 * half] = a_res;
-                    hs[4 * half + 1] = a_psi;
-                    hs[4 * half + 2] = a_cost;
-                    hs[4 * half + 3] = dm;
+                    hs[4 * wi] = a_res;
+                    hs[4 * wi + 1] = a_psi;
+                    hs[4 * wi + 2] = a_cost;
+                    hs[4 * wi + 3] = dm;
                 }
             }
-            pair_sync(bid);
-            if (res && half == 0 && lane == 0) {
-                const float vr = float(sqrt(hs[0] + hs[4])), vp = float(sqrt(hs[1] + hs[5]));
-                const float vc = float(hs[2] + hs[6]);
+            pair_sync<NW>(bid);
+            if (res && wi == 0 && lane == 0) {
+                double sr = hs[0], sp = hs[1], sc = hs[2], sdm = hs[3];
+#pragma unroll
+                for (int k = 1; k < NW; ++k) {
+                    sr += hs[4 * k];
+                    sp += hs[4 * k + 1];
+                    sc += hs[4 * k + 2];
+                    sdm = fmin(sdm, hs[4 * k + 3]);
+                }
+                const float vr = float(sqrt(sr)), vp = float(sqrt(sp));
+                const float vc = float(sc);
                 if (p.hist) {
                     float *hd = p.hist + ((size_t)traj * p.iters + it) * 3;
                     hd[0] = vr;
@@ -932,10 +964,10 @@ __device__ void traj_solve(const FusedProblem &p, const float *sm, const WSmem &
                     p.res[traj] = vr;
                     p.res_psi[traj] = vp;
                     p.cost[traj] = vc;
-                    p.mind[traj] = sqrtf(float(fmin(hs[3], hs[7])));
+                    p.mind[traj] = sqrtf(float(sdm));
                 }
             }
-            R = r_rows(red, half, lane);
+            R = r_rows<NW>(red, wi, lane);
         }
     }
     // ---- the state back: xi1 (cur), xi2 (cur2), lam, lam_psi.  The
@@ -944,34 +976,34 @@ __device__ void traj_solve(const FusedProblem &p, const float *sm, const WSmem &
     // sign rho_psi (P^T P sum(dxi2) - P^T sum(delta))_b (Eq. update_lambda_1
     // and update_lambda_psi summed over the iterations; both are linear).
     float *gd = p.state + (size_t)traj * STATE;
-    pair_sync(bid);  // every R row read before the rows are reused
-    dot_partials(red, col, b, acc_load(ta, col));
-    pair_sync(bid);
-    if (lane < NS) {
-        const int ob = NS * half + lane;
-        if (!interior(ob % NV)) gd[55 + ob] = fmaf(rho, row_sum(red, ob), gs[55 + ob]);
+    pair_sync<NW>(bid);  // every R row read before the rows are reused
+    dot_partials<NW>(red, col, b, acc_load<NW>(ta, col));
+    pair_sync<NW>(bid);
+    if (wi < 2 && lane < NS) {
+        const int ob = NS * wi + lane;
+        if (!interior(ob % NV)) gd[55 + ob] = fmaf(rho, row_sum<NW>(red, ob), gs[55 + ob]);
     }
-    pair_sync(bid);
+    pair_sync<NW>(bid);
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
         const float2 m = fmul2(b.P[k], dsum);
-        red[k * kRS + col] = m.x + m.y;
+        red[k * WS<NW>::kRS + col] = m.x + m.y;
     }
-    pair_sync(bid);
-    if (half == 0) {
+    pair_sync<NW>(bid);
+    if (wi == 0) {
         if (lane < NV && !interior(lane)) {
             const float *pr = sm + S.ptr + lane * 12;
             float a = 0.f;
 #pragma unroll
             for (int c = 0; c < NV; ++c) a = fmaf(pr[c], ta[kWsdx2 + c], a);
-            gd[99 + lane] = gs[99 + lane] - L.psi_sign * L.rho_psi * (a - row_sum(red, lane));
+            gd[99 + lane] = gs[99 + lane] - L.psi_sign * L.rho_psi * (a - row_sum<NW>(red, lane));
         }
         for (int e = lane; e < 55; e += 32)
             gd[e] = e < 44 ? ta[kWxi + cur * 48 + pidx(e)] : ta[kWx2 + cur2 * 12 + (e - 44)];
         if (psi_lane) gd[99 + pk] = lps;
     }
     if (owner) gd[55 + o] = lam;
-    pair_sync(bid);  // the area is free for the next trajectory
+    pair_sync<NW>(bid);  // the area is free for the next trajectory
 }
 
 // Stages a problem's small matrices and obstacle sections into shared memory
@@ -979,6 +1011,7 @@ __device__ void traj_solve(const FusedProblem &p, const float *sm, const WSmem &
 // rest of the area, then forms the row-major copies of Minv, MQ, Mpsi, Mpsi H
 // and P^T P and the pair-interleaved Pd, Pdd.  Every thread of the block
 // calls it; false (for every thread) when the wait ran out.
+template <int NW>
 __device__ bool stage_problem(const FusedProblem &p, float *sm, const WSmem &S, uint64_t *bar, uint32_t parity)
 {
     const ConstLayout &L = p.L;
@@ -1017,11 +1050,12 @@ __device__ bool stage_problem(const FusedProblem &p, float *sm, const WSmem &S, 
         sm[S.ptr + k * 12 + c] = cst[L.off_ptp + c * 12 + k];
     }
     // Pd, Pdd per pair of steps (global rows [3][q][12]); entries past the
-    // horizon, and pair 64, stay zero
+    // horizon, and the last pair, stay zero
     const float *rows = p.cblob + L.off_prow;
     for (int i = threadIdx.x; i < 2 * L.q * NV; i += blockDim.x) {
         const int ty = i / (L.q * NV), rem = i - ty * L.q * NV, t = rem / NV, k = rem - NV * t;
-        sm[S.pb + (ty * kPairs + (t >> 1)) * kPB + 2 * k + (t & 1)] = __ldg(rows + ((1 + ty) * L.q + t) * 12 + k);
+        sm[S.pb + (ty * WS<NW>::kPairs + (t >> 1)) * kPB + 2 * k + (t & 1)] =
+            __ldg(rows + ((1 + ty) * L.q + t) * 12 + k);
     }
     __syncthreads();
     return true;
@@ -1034,14 +1068,15 @@ struct WLane {
     bool valid, v1;
 };
 
-__device__ __forceinline__ void lane_setup(const FusedProblem &p, const float *sm, const WSmem &S, int half,
+template <int NW>
+__device__ __forceinline__ void lane_setup(const FusedProblem &p, const float *sm, const WSmem &S, int wi,
                                            int lane, WLane &w)
 {
-    const int q = p.L.q, np = (q + 1) >> 1, nh = (np + 1) >> 1;
-    const int j = half * nh + lane;
+    const int q = p.L.q, np = (q + 1) >> 1, nh = (np + NW - 1) / NW;
+    const int j = wi * nh + lane;
     w.valid = lane < nh && j < np;
     w.v1 = w.valid && 2 * j + 1 < q;
-    load_basis(p.cblob + p.L.off_prow, sm + S.pb, w.valid ? j : kPairs - 1, w.valid, w.v1, w.b);
+    load_basis<NW>(p.cblob + p.L.off_prow, sm + S.pb, w.valid ? j : WS<NW>::kPairs - 1, w.valid, w.v1, w.b);
     w.jp = w.valid ? j : 0;  // obstacle-track pair (in range for every lane)
 }
 
@@ -1054,43 +1089,45 @@ __device__ __forceinline__ void init_stage_barrier(uint64_t *bar)
     __syncthreads();
 }
 
-template <int M>
-__global__ void __launch_bounds__(kWMaxTraj * kWThreads, 1) am_warp_kernel(FusedProblem p)
+template <int M, int NW>
+__global__ void __launch_bounds__(kWMaxWarps * 32, 1) am_warp_kernel(FusedProblem p)
 {
     extern __shared__ __align__(128) float sm[];
-    const int T = blockDim.x / kWThreads;
-    const WSmem S = wsmem_layout(p.L, T);
+    const int T = blockDim.x / WS<NW>::kThreads;
+    const WSmem S = wsmem_layout<NW>(p.L, T);
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm + S.bar);
 #ifdef AM_DEBUG_BOUNDS
     if (threadIdx.x == 0) g_woob = 0;
 #endif
     init_stage_barrier(bar);
-    if (!stage_problem(p, sm, S, bar, 0)) {
+    if (!stage_problem<NW>(p, sm, S, bar, 0)) {
         if (threadIdx.x == 0) atomicExch(p.err, 1);
         return;
     }
-    const int slot = threadIdx.x / kWThreads, half = (threadIdx.x >> 5) & 1, lane = threadIdx.x & 31;
-    float *ta = sm + S.traj + slot * kTrajFloats;
+    const int slot = threadIdx.x / WS<NW>::kThreads, wi = (threadIdx.x >> 5) % NW, lane = threadIdx.x & 31;
+    float *ta = sm + S.traj + slot * WS<NW>::kTrajFloats;
     WLane w;
-    lane_setup(p, sm, S, half, lane, w);
+    lane_setup<NW>(p, sm, S, wi, lane, w);
     for (int traj = blockIdx.x * T + slot; traj < p.B; traj += gridDim.x * T)
-        traj_solve<M>(p, sm, S, ta, traj, half, lane, 1 + slot, w.b, w.jp, w.valid, w.v1);
+        traj_solve<M, NW>(p, sm, S, ta, traj, wi, lane, 1 + slot, w.b, w.jp, w.valid, w.v1);
 #ifdef AM_DEBUG_BOUNDS
     __syncthreads();
     if (threadIdx.x == 0 && g_woob) atomicOr(p.err, 2);
 #endif
 }
 
-// Uneven batching with the warp-pair kernel: persistent CTAs of seven
-// trajectory slots take work items (problem, tile of at most seven
+// Uneven batching with the warp-pair kernel: persistent CTAs of up to 16 / NW
+// trajectory slots (one count per launch, the most that every problem of
+// the variant fits in shared memory) take work items (problem, tile of at most that many
 // trajectories) of variant v from a list in order, through one atomic
 // counter, and re-stage constants whenever they move to another problem.
-// Each slot's pair of warps runs one trajectory of the tile.  The lists
+// Each slot's NW warps run one trajectory of the tile.  A variant holds the
+// problems of one circle count and one NW.  The lists
 // live in device memory, as for the small-tile group kernels.
 //   head[v]: number of items of variant v; head[kGroupVariants + v]: offset of its list
 //   ctl[2 v]: its work counter (zeroed before the launch); ctl[2 v + 1]: status
-template <int M>
-__global__ void __launch_bounds__(kWMaxTraj * kWThreads, 1)
+template <int M, int NW>
+__global__ void __launch_bounds__(kWMaxWarps * 32, 1)
 am_group_warp_kernel(const FusedProblem *probs, const int *items, const int *head, int *ctl, int v)
 {
     int *counter = ctl + 2 * v;
@@ -1105,7 +1142,8 @@ am_group_warp_kernel(const FusedProblem *probs, const int *items, const int *hea
     if (threadIdx.x == 0) g_woob = 0;
 #endif
     init_stage_barrier(bar);
-    const int slot = threadIdx.x / kWThreads, half = (threadIdx.x >> 5) & 1, lane = threadIdx.x & 31;
+    const int TM = blockDim.x / WS<NW>::kThreads;  // trajectory slots
+    const int slot = threadIdx.x / WS<NW>::kThreads, wi = (threadIdx.x >> 5) % NW, lane = threadIdx.x & 31;
     int cur = -1;
     uint32_t parity = 0;
     WLane w;
@@ -1118,7 +1156,7 @@ am_group_warp_kernel(const FusedProblem *probs, const int *items, const int *hea
         if (pi != cur) {
             if (threadIdx.x == 0) kp = probs[pi];
             __syncthreads();
-            if (!stage_problem(kp, sm, wsmem_layout(kp.L, kWMaxTraj), bar, parity)) {
+            if (!stage_problem<NW>(kp, sm, wsmem_layout<NW>(kp.L, TM), bar, parity)) {
                 if (threadIdx.x == 0) {
                     atomicExch(kp.err, 1);
                     atomicExch(ctl + 2 * v + 1, 1);
@@ -1127,14 +1165,14 @@ am_group_warp_kernel(const FusedProblem *probs, const int *items, const int *hea
             }
             parity ^= 1u;
             cur = pi;
-            lane_setup(kp, sm, wsmem_layout(kp.L, kWMaxTraj), half, lane, w);
+            lane_setup<NW>(kp, sm, wsmem_layout<NW>(kp.L, TM), wi, lane, w);
         }
-        const WSmem S = wsmem_layout(kp.L, kWMaxTraj);
+        const WSmem S = wsmem_layout<NW>(kp.L, TM);
         const long long lo = (long long)tile * kp.B / kp.ntiles, hi = (long long)(tile + 1) * kp.B / kp.ntiles;
         const int traj = int(lo) + slot;
         if (traj < hi)
-            traj_solve<M>(kp, sm, S, sm + S.traj + slot * kTrajFloats, traj, half, lane, 1 + slot, w.b, w.jp,
-                          w.valid, w.v1);
+            traj_solve<M, NW>(kp, sm, S, sm + S.traj + slot * WS<NW>::kTrajFloats, traj, wi, lane, 1 + slot, w.b,
+                              w.jp, w.valid, w.v1);
         __syncthreads();
     }
 #ifdef AM_DEBUG_BOUNDS
@@ -1145,8 +1183,8 @@ am_group_warp_kernel(const FusedProblem *probs, const int *items, const int *hea
 
 std::mutex g_warp_mu;
 
-template <int M>
-int launch_warp_m(const FusedProblem &p, int T, size_t smem, int grid, cudaStream_t st)
+template <int M, int NW>
+int launch_warp_mn(const FusedProblem &p, int T, size_t smem, int grid, cudaStream_t st)
 {
     static int attr_dev = -1;
     int dev = 0;
@@ -1154,19 +1192,38 @@ int launch_warp_m(const FusedProblem &p, int T, size_t smem, int grid, cudaStrea
     {
         std::lock_guard<std::mutex> lk(g_warp_mu);
         if (attr_dev != dev) {
-            if (cudaFuncSetAttribute(am_warp_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            if (cudaFuncSetAttribute(am_warp_kernel<M, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      int(kFusedSmemMax)) != cudaSuccess)
                 return -2;
             attr_dev = dev;
         }
     }
-    am_warp_kernel<M><<<grid, T * kWThreads, smem, st>>>(p);
+    am_warp_kernel<M, NW><<<grid, T * WS<NW>::kThreads, smem, st>>>(p);
     return 0;
 }
 
+template <int M, int NW>
+cudaError_t launch_group_warp_mn(const GroupLaunch &g, cudaStream_t st)
+{
+    cudaError_t r = cudaFuncSetAttribute(am_group_warp_kernel<M, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(g.smem));
+    if (r != cudaSuccess) return r;
+    am_group_warp_kernel<M, NW><<<g.grid, g.slots * WS<NW>::kThreads, g.smem, st>>>(
+        g.d_probs, g.d_items, g.d_head, g.d_ctl, g.variant);
+    return cudaPeekAtLastError();
+}
+
+int max_traj(int nw) { return nw == 2 ? WS<2>::kMaxTraj : nw == 3 ? WS<3>::kMaxTraj : WS<4>::kMaxTraj; }
+
 }  // namespace
 
-size_t warp_smem_bytes(const ConstLayout &L, int T) { return size_t(wsmem_layout(L, T).total) * sizeof(float); }
+size_t warp_smem_bytes(const ConstLayout &L, int T)
+{
+    const int nw = warps_for_q(L.q);
+    const int total = nw == 2 ? wsmem_layout<2>(L, T).total : nw == 3 ? wsmem_layout<3>(L, T).total
+                                                                      : wsmem_layout<4>(L, T).total;
+    return size_t(total) * sizeof(float);
+}
 
 int warp_supported(const ConstLayout &L)
 {
@@ -1177,47 +1234,55 @@ int warp_supported(const ConstLayout &L)
     return warp_smem_bytes(L, 1) <= kFusedSmemMax ? 1 : 0;
 }
 
-int warp_max_traj() { return kWMaxTraj; }
+int warp_max_traj(const ConstLayout &L) { return max_traj(warps_for_q(L.q)); }
 
 int warp_auto_traj(const ConstLayout &L, int B, int sms)
 {
-    // fewest rounds of trajectories per warp pair, then the fewest
+    // fewest rounds of trajectories per CTA slot, then the fewest
     // trajectories per CTA that keep that number of rounds
-    const long long slots = (long long)sms * kWMaxTraj;
+    const int tmax = warp_max_traj(L);
+    const long long slots = (long long)sms * tmax;
     const long long rounds = (B + slots - 1) / slots;
     long long T = (B + (long long)sms * rounds - 1) / ((long long)sms * rounds);
     if (T < 1) T = 1;
-    if (T > kWMaxTraj) T = kWMaxTraj;
+    if (T > tmax) T = tmax;
     while (T > 1 && warp_smem_bytes(L, int(T)) > kFusedSmemMax) --T;
     return int(T);
 }
 
-int warp_group_traj() { return kWMaxTraj; }
+int warp_group_traj(const ConstLayout &L)
+{
+    if (!warp_supported(L)) return 0;
+    int T = warp_max_traj(L);
+    while (T > 0 && warp_smem_bytes(L, T) > kGroupSmemLimit) --T;
+    return T;
+}
 
-size_t warp_group_smem(const ConstLayout &L) { return warp_smem_bytes(L, kWMaxTraj); }
+int warp_group_variant(const ConstLayout &L) { return kGroupWarpVariant0 + 4 * (warps_for_q(L.q) - 2) + L.m - 1; }
 
 int launch_group_warp(const GroupLaunch &g, void *stream, int *launches, const char **why)
 {
     *why = nullptr;
-    const int M = g.variant - kGroupWarpVariant0 + 1;
-    if (M < 1 || M > MAXM || g.grid < 1 || g.smem > kGroupSmemLimit) return -1;
+    const int k = g.variant - kGroupWarpVariant0, M = k % 4 + 1, NW = k / 4 + 2;
+    if (k < 0 || NW > 4 || g.grid < 1 || g.smem > kGroupSmemLimit || g.slots < 1 || g.slots > max_traj(NW))
+        return -1;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemsetAsync(g.d_ctl + 2 * g.variant, 0, 2 * sizeof(int), st);
     if (e != cudaSuccess) {
         *why = cudaGetErrorString(e);
         return -2;
     }
-    auto go = [&](auto kernel) {
-        cudaError_t r = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(g.smem));
-        if (r != cudaSuccess) return r;
-        kernel<<<g.grid, kWMaxTraj * kWThreads, g.smem, st>>>(g.d_probs, g.d_items, g.d_head, g.d_ctl, g.variant);
-        return cudaPeekAtLastError();
-    };
-    switch (M) {
-    case 1: e = go(am_group_warp_kernel<1>); break;
-    case 2: e = go(am_group_warp_kernel<2>); break;
-    case 3: e = go(am_group_warp_kernel<3>); break;
-    default: e = go(am_group_warp_kernel<4>); break;
+    switch (4 * (NW - 2) + M - 1) {
+#define AM_WG(MM, NN)                                                                                        \
+    case 4 * (NN - 2) + MM - 1:                                                                              \
+        e = launch_group_warp_mn<MM, NN>(g, st);                                                             \
+        break;
+        AM_WG(1, 2) AM_WG(2, 2) AM_WG(3, 2) AM_WG(4, 2)
+        AM_WG(1, 3) AM_WG(2, 3) AM_WG(3, 3) AM_WG(4, 3)
+        AM_WG(1, 4) AM_WG(2, 4) AM_WG(3, 4) AM_WG(4, 4)
+#undef AM_WG
+    default:
+        return -1;
     }
     if (e != cudaSuccess) {
         *why = cudaGetErrorString(e);
@@ -1235,7 +1300,7 @@ int launch_warp(const SolveArgs &a, void *stream, int *launches)
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) return -2;
     const int T = a.tile > 0 ? a.tile : warp_auto_traj(L, a.B, sms);
-    if (T < 1 || T > kWMaxTraj) return -1;
+    if (T < 1 || T > warp_max_traj(L)) return -1;
     const size_t smem = warp_smem_bytes(L, T);
     if (smem > kFusedSmemMax) return -1;
     FusedProblem p;
@@ -1254,13 +1319,19 @@ int launch_warp(const SolveArgs &a, void *stream, int *launches)
     p.err = a.err;
     const int grid = p.ntiles < sms ? p.ntiles : sms;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int nw = warps_for_q(L.q);
     int rc = -1;
-    switch (L.m) {
-    case 1: rc = launch_warp_m<1>(p, T, smem, grid, st); break;
-    case 2: rc = launch_warp_m<2>(p, T, smem, grid, st); break;
-    case 3: rc = launch_warp_m<3>(p, T, smem, grid, st); break;
-    case 4: rc = launch_warp_m<4>(p, T, smem, grid, st); break;
-    default: return -1;
+    switch (4 * (nw - 2) + L.m - 1) {
+#define AM_W(MM, NN)                                                                                         \
+    case 4 * (NN - 2) + MM - 1:                                                                              \
+        rc = launch_warp_mn<MM, NN>(p, T, smem, grid, st);                                                   \
+        break;
+        AM_W(1, 2) AM_W(2, 2) AM_W(3, 2) AM_W(4, 2)
+        AM_W(1, 3) AM_W(2, 3) AM_W(3, 3) AM_W(4, 3)
+        AM_W(1, 4) AM_W(2, 4) AM_W(3, 4) AM_W(4, 4)
+#undef AM_W
+    default:
+        return -1;
     }
     if (rc) return rc;
     if (launches) ++*launches;

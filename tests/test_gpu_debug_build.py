@@ -6,7 +6,8 @@ and report an index outside its array in the problem's status word (bit 2,
 AM_ERR_STATE on the host) instead of trapping; the access is skipped.  On
 valid shapes -- the tiny and paper-shaped workloads, an odd horizon whose
 last pair of steps has one step, a grouped launch and the warp-pair
-kernel on the paper shape and the odd horizon -- no check may fire,
+kernel on the paper shape, the odd horizon and the three- and four-warp
+horizons (q = 151 and q = 256 with 64 obstacles) -- no check may fire,
 and the checks must not change a single result: each build runs in its own
 process and the states are compared bit for bit.
 """
@@ -31,13 +32,14 @@ assert T.LIB_PATH.endswith(sys.argv[2]), T.LIB_PATH
 out = {}
 cases = {"tiny": W.make_problem("tiny", 0), "paper": W.make_problem("paper", 0, B=40),
          "odd_q": W.make_shape(11, B=9, q=51, n=5, m=3)}
+wcases = {"paper": cases["paper"], "odd_q": cases["odd_q"], "q151": W.make_shape(12, B=11, q=151, n=12, m=2),
+          "q256": W.make_shape(13, B=6, q=256, n=64, m=4)}
 for name, pb in cases.items():
     P = T.Problem(pb)
     P.solve(pb["init"].astype(np.float32), 20)   # raises TrajamError on a nonzero status word
     out[name] = P.state().tolist()
     P.close()
-for name in ("paper", "odd_q"):                 # the warp-pair kernel
-    pb = cases[name]
+for name, pb in wcases.items():                 # the warp-pair kernel
     P = T.Problem(pb, kernel=T.AM_KERNEL_WARP)
     P.solve(pb["init"].astype(np.float32), 20)
     out["warp_" + name] = P.state().tolist()
@@ -51,7 +53,7 @@ out["group"] = [P.state().tolist() for P in probs]   # each state read checks it
 G.close()
 for P in probs:
     P.close()
-# the warp-pair group kernels (AUTO handles, q <= 128) beside the small-tile ones
+# the warp-pair group kernels (AUTO handles: two and three warps per trajectory)
 probs = [T.Problem(pb, kernel=T.AM_KERNEL_AUTO).init_state(pb["init"].astype(np.float32)) for pb in pbs]
 G = T.Group(probs)
 G.solve(10)

@@ -2,8 +2,9 @@
 
 A problem whose handle selects AM_KERNEL_AUTO (or AM_KERNEL_WARP) runs in a
 group on the warp-pair group kernels when its form and shape fit them (FP32,
-default alpha form, q <= 128), every other problem on the small-tile group
-kernels, all in one launch.  A trajectory's arithmetic on the warp-pair
+default alpha form; two, three or four warps per trajectory for q <= 128,
+192, 256), every other problem on the small-tile group kernels, all in one
+launch.  A trajectory's arithmetic on the warp-pair
 kernels does not depend on which CTA slot runs it, so each problem gives
 the same bits in the group as alone with the kernel AM_KERNEL_AUTO picks
 for it; the results also match the FP64 oracle (with the mix's widened
@@ -56,12 +57,13 @@ def group(pbs, iters, kernel, reps=1, stream=None):
 
 def test_auto_group_equals_alone_bit_for_bit_and_oracle():
     """Ten mixed problems, q in {50, 100, 150}: the q <= 128 ones on the
-    warp-pair group kernels, the q = 150 ones on the small-tile kernels."""
+    two-warp group kernels, the q = 150 ones on the three-warp kernels, one
+    launch per (warps, circles) pair."""
     T = tj()
     pbs = mix(count=10, seed=8)
     assert {pb["q"] for pb in pbs} & {50, 100} and 150 in {pb["q"] for pb in pbs}
     outs, (launches, items) = group(pbs, 10, T.AM_KERNEL_AUTO)
-    variants = {("warp" if pb["q"] <= 128 else "tile", pb["m"]) for pb in pbs}
+    variants = {(2 if pb["q"] <= 128 else 3, pb["m"]) for pb in pbs}
     assert launches == len(variants)
     for pb, g in zip(pbs, outs):
         a = alone(pb, 10, T.AM_KERNEL_AUTO)
@@ -76,7 +78,7 @@ def test_warp_group_equals_warp_alone():
     solves, also when the captured launch is replayed on a stream."""
     import torch
     T = tj()
-    pbs = [pb for pb in mix(count=12, seed=9) if pb["q"] <= 128][:6]
+    pbs = mix(count=6, seed=9)
     st = torch.cuda.Stream()
     outs, _ = group(pbs, 10, T.AM_KERNEL_WARP, reps=2, stream=st)
     for pb, g in zip(pbs, outs):
@@ -119,7 +121,7 @@ def test_server_auto_scene_alone_equals_in_mix():
     np.testing.assert_array_equal(np.asarray(mixed[0]["coeffs"]), np.asarray(first["coeffs"]))
 
 
-@pytest.mark.parametrize("case", ["paper", "q150", "literal", "large"])
+@pytest.mark.parametrize("case", ["paper", "q150", "q256", "literal", "tf32", "large"])
 def test_auto_picks_the_kernel(case):
     """AM_KERNEL_AUTO solves with the large-batch kernel from B = 16384 on,
     else with the warp-pair kernel where it takes the problem, else with the
@@ -129,7 +131,11 @@ def test_auto_picks_the_kernel(case):
     if case == "paper":
         pb = W.make_problem("paper", 0, B=64)
     elif case == "q150":
-        pb, expect = W.make_shape(11, 16, 150, 6, 3), T.AM_KERNEL_FUSED
+        pb = W.make_shape(11, 16, 150, 6, 3)
+    elif case == "q256":
+        pb = W.make_shape(12, 9, 256, 20, 2)
+    elif case == "tf32":
+        pb, flags, expect = W.make_problem("tiny", 0, B=16), dict(precision=T.AM_TF32), T.AM_KERNEL_FUSED
     elif case == "literal":
         pb, flags, expect = W.make_problem("tiny", 0, B=16), dict(alpha_mode=1), T.AM_KERNEL_FUSED
     else:
