@@ -14,6 +14,7 @@ no data-path collective); rank 0 prints the line.
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import os
 import statistics
@@ -157,11 +158,15 @@ def summary_sections(extra: dict) -> dict:
             "400/s": {"batched": pq(sv["batched"]), "seq_fused": pq(sv["sequential_fused"]),
                       "batched_auto": pq(sv["batched_auto"]), "seq_auto": pq(sv["sequential_auto"]),
                       "seq_plain": pq(sv["sequential_plain_fp32_loop"])},
-            "2500/s": {"batched": pq(sv["high_load"]["batched"]),
-                       "seq_fused": pq(sv["high_load"]["sequential_fused"]),
-                       "batched_auto": pq(sv["high_load"]["batched_auto"])}}
+            # three runs each: [p50 per run], [p99 per run]
+            "2500/s": {k: [[r["p50_ms"] for r in sv["high_load"][name]], [r["p99_ms"] for r in sv["high_load"][name]]]
+                       for k, name in (("batched", "batched"), ("seq_fused", "sequential_fused"),
+                                       ("batched_auto", "batched_auto"), ("seq_auto", "sequential_auto"))}}
         out["serving_mean_batch"] = {"400/s": sv["batched"]["mean_batch"],
-                                     "2500/s": sv["high_load"]["batched"]["mean_batch"]}
+                                     "2500/s": [r["mean_batch"] for r in sv["high_load"]["batched"]]}
+        out["serving_submit_lag_max_ms"] = max(
+            [sv[k]["submit_lag_max_ms"] for k in ("batched", "sequential_fused", "batched_auto", "sequential_auto")]
+            + [r["submit_lag_max_ms"] for k, v in sv["high_load"].items() if isinstance(v, list) for r in v])
     return out
 
 
@@ -474,18 +479,26 @@ def serve_run(TJ, W, pbs, mode, kernel, seconds, warmup_s=1.0, rate=400.0, iters
            for pb in pbs]
     clock = np.zeros(len(pbs))
     tickets = []
-    t0 = time.perf_counter()
-    for a, k in zip(arrivals, picks):
-        while True:
-            dt = t0 + a - time.perf_counter()
-            if dt <= 0:
-                break
-            time.sleep(min(dt, 5e-4))
-        clock[k] += 0.1
-        pb = pbs[k]
-        xo = (pb["xo"] + clock[k] * vel[k][0][:, None]).astype(np.float32)
-        yo = (pb["yo"] + clock[k] * vel[k][1][:, None]).astype(np.float32)
-        tickets.append((a, S.submit(int(k), advance=0.1, xo=xo, yo=yo)))
+    # no collector pause inside the arrival loop: a pause would release the
+    # requests it delayed as one burst
+    gc_on = gc.isenabled()
+    gc.disable()
+    try:
+        t0 = time.perf_counter()
+        for a, k in zip(arrivals, picks):
+            while True:
+                dt = t0 + a - time.perf_counter()
+                if dt <= 0:
+                    break
+                time.sleep(min(dt, 5e-4))
+            clock[k] += 0.1
+            pb = pbs[k]
+            xo = (pb["xo"] + clock[k] * vel[k][0][:, None]).astype(np.float32)
+            yo = (pb["yo"] + clock[k] * vel[k][1][:, None]).astype(np.float32)
+            tickets.append((a, S.submit(int(k), advance=0.1, xo=xo, yo=yo)))
+    finally:
+        if gc_on:
+            gc.enable()
     res = [(a, S.wait(t, timeout_s=300.0)) for a, t in tickets]
     stats = S.stats()
     S.close()
@@ -494,8 +507,12 @@ def serve_run(TJ, W, pbs, mode, kernel, seconds, warmup_s=1.0, rate=400.0, iters
     bad = sum(1 for _, r in res if r["status"] != 0)
     lat = np.array([r["t_done"] - r["t_submit"] for a, r in res if a >= warmup_s]) * 1e3
     span = max(r["t_done"] for _, r in res) - min(r["t_submit"] for _, r in res)
+    # how late the generator submitted each request against its schedule
+    # (the server's clock and perf_counter are both the monotonic clock)
+    lag = max(r["t_submit"] - (t0 + a) for a, r in res) * 1e3
     return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "mean_ms": float(lat.mean()), "requests_measured": int(len(lat)), "requests": len(res),
+            "submit_lag_max_ms": float(lag),
             "failed": bad, "offered_per_s": rate, "served_per_s": len(res) / span,
             "rounds": stats["rounds"], "mean_batch": float(np.mean([r["batch"] for _, r in res])),
             "seconds": seconds, "warmup_s": warmup_s}
@@ -518,16 +535,16 @@ def bench_serving(TJ, W, seconds: float, plain_seconds: float) -> dict:
                                                   plain_seconds)
     # a heavier load, where requests arrive while others are on the GPU and
     # rounds of continuous batching hold several of them
+    # (three runs of each mode, different arrival seeds, so that the spread
+    # of the tail shows)
     hi_rate = 2500.0
-    out["high_load"] = {
-        "offered_per_s": hi_rate,
-        "batched": serve_run(TJ, W, pbs, TJ.AM_SRV_BATCHED, TJ.AM_KERNEL_FUSED, plain_seconds * 1.5,
-                             warmup_s=1.0, rate=hi_rate),
-        "sequential_fused": serve_run(TJ, W, pbs, TJ.AM_SRV_SEQUENTIAL, TJ.AM_KERNEL_FUSED,
-                                      plain_seconds * 1.5, warmup_s=1.0, rate=hi_rate),
-        "batched_auto": serve_run(TJ, W, pbs, TJ.AM_SRV_BATCHED, TJ.AM_KERNEL_AUTO, plain_seconds * 1.5,
-                                  warmup_s=1.0, rate=hi_rate),
-    }
+    out["high_load"] = {"offered_per_s": hi_rate, "runs": 3}
+    for name, mode, kern in (("batched", TJ.AM_SRV_BATCHED, TJ.AM_KERNEL_FUSED),
+                             ("sequential_fused", TJ.AM_SRV_SEQUENTIAL, TJ.AM_KERNEL_FUSED),
+                             ("batched_auto", TJ.AM_SRV_BATCHED, TJ.AM_KERNEL_AUTO),
+                             ("sequential_auto", TJ.AM_SRV_SEQUENTIAL, TJ.AM_KERNEL_AUTO)):
+        out["high_load"][name] = [serve_run(TJ, W, pbs, mode, kern, plain_seconds, warmup_s=1.0, rate=hi_rate,
+                                            seed=7 + rep) for rep in range(3)]
     return out
 
 

@@ -386,7 +386,9 @@ AM_API void am_group_destroy(am_group *g);
  * first) among the scenes not already in flight, applies each request's
  * updates (start state, obstacle tracks), advances the scenes by `iters`
  * iterations -- all of them in one grouped launch (AM_SRV_BATCHED; a round
- * of one request uses the scene's own kernel), or one request per round
+ * of one request uses the scene's own kernel, and a round groups scenes
+ * only when at least three requests are admissible, else it takes one and
+ * the next goes to the next free lane), or one request per round
  * with the scene's own kernel (AM_SRV_SEQUENTIAL, the comparator) --
  * selects each scene's best trajectory and completes the requests.  Up to
  * `lanes` rounds are in flight at once, each on its own stream: the worker

@@ -881,7 +881,12 @@ int group_launch(am_group *g, int iters, cudaStream_t st)
             !std::memcmp(c.smem, g->vsmem, sizeof(c.smem)) && !std::memcmp(c.slots, g->vslots, sizeof(c.slots)))
             hit = &c;
     if (!hit) {
-        if (g->graphs.size() >= 16) drop_graph(g);
+        // a server's rounds bring many variant sets: keep up to 64 graphs,
+        // dropping the oldest
+        if (g->graphs.size() >= 64) {
+            cudaGraphExecDestroy(g->graphs.front().exec);
+            g->graphs.erase(g->graphs.begin());
+        }
         cudaGraph_t graph_obj = nullptr;
         CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
         rc = issue_variants(g, mask, threads, sms, true, st, nullptr);
