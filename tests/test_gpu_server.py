@@ -102,6 +102,32 @@ def test_request_arriving_during_a_round_overlaps_it():
         assert r["cost"] == a["cost"]
 
 
+def test_round_groups_from_three_admissible_requests():
+    """Two queued requests for different scenes go to two lanes as rounds of
+    one (grouping two costs what two launches cost); three queued requests
+    form one grouped round.  Every result equals its scene served alone, bit
+    for bit."""
+    pbs = scenes(count=3, seed=25)
+    alone = []
+    for k in range(3):
+        S, probs = make_server(pbs, 10)
+        alone.append(S.wait(S.submit(k)))
+        close(S, probs)
+    for count in (2, 3):
+        S, probs = make_server(pbs, 10, start=False)
+        tickets = [S.submit(k) for k in range(count)]
+        S.start()
+        rs = [S.wait(t) for t in tickets]
+        close(S, probs)
+        assert all(r["status"] == 0 for r in rs)
+        if count == 2:
+            assert all(r["batch"] == 1 for r in rs) and rs[0]["round"] != rs[1]["round"]
+        else:
+            assert all(r["batch"] == 3 and r["round"] == 0 for r in rs)
+        for r, a in zip(rs, alone):
+            np.testing.assert_array_equal(np.asarray(r["coeffs"]), np.asarray(a["coeffs"]))
+
+
 def test_batched_round_holds_many_scenes_and_matches_oracle():
     """One round advances six scenes of different shapes; a second request for
     a scene already in the round waits for the next round."""
