@@ -29,6 +29,11 @@
  *  - lam_psi -= rho_psi P^T (P xi2 - psi_t)  (method-of-multipliers sign).
  *  - the xi3/xi4 step uses cos/sin of P xi2 (Eq. compute_zeta_33); the
  *    residual uses the slack rows of F (Eq. coll_con).
+ *
+ * Every function here is pinned by a CPU test against something other than
+ * itself (exact values, scipy, brute force, closed forms, a numpy KKT solve).
+ * Parity unpinned: the per-trajectory monotonicity of the residual and the
+ * absolute values of the final cost, which the paper prints for no instance.
  */
 #include "am_oracle.h"
 
