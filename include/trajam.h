@@ -412,7 +412,9 @@ typedef struct {
     size_t budget_bytes;    /* device bytes all scenes together may hold      */
     int iters;              /* AM iterations per request                       */
     int mode;               /* AM_SRV_BATCHED | AM_SRV_SEQUENTIAL              */
-    int max_batch;          /* requests per round (0 = up to one per scene)    */
+    int max_batch;          /* requests per round (0 = up to one per scene);
+                               a round takes several only when at least
+                               three are admissible                          */
     int max_pending;        /* queue bound (0 = 65536)                         */
     int lanes;              /* rounds in flight (0 = 2 batched, 1 sequential;
                                at most 8); AM_SRV_SEQUENTIAL takes 1          */
