@@ -386,9 +386,13 @@ def bench_precision(TJ, W, torch, dev, flush, steps: int, iters: int = 100) -> d
     init = torch.tensor(pb["init"], dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
     out, ref = {}, None
-    for prec, name in ((TJ.AM_FP32, "fp32"), (TJ.AM_TF32, "tf32"), (TJ.AM_BF16, "bf16"),
-                       (TJ.AM_SPLIT_BF16, "split_bf16")):
-        P = TJ.Problem(pb, precision=prec)
+    # the reduced forms act on the small-tile kernel's tensor-core product;
+    # the warp-pair kernel (FP32 SIMT contractions) is timed beside them
+    for prec, name, kern in ((TJ.AM_FP32, "fp32", TJ.AM_KERNEL_FUSED), (TJ.AM_TF32, "tf32", TJ.AM_KERNEL_FUSED),
+                             (TJ.AM_BF16, "bf16", TJ.AM_KERNEL_FUSED),
+                             (TJ.AM_SPLIT_BF16, "split_bf16", TJ.AM_KERNEL_FUSED),
+                             (TJ.AM_FP32, "fp32_warp_pair", TJ.AM_KERNEL_WARP)):
+        P = TJ.Problem(pb, precision=prec, kernel=kern)
         P.solve(init, 10, stream=stream)
         xi = P.state()[:, :55].astype(np.float64)
         ms = []
