@@ -14,9 +14,13 @@
  * Conventions
  *  - Every function returns AM_OK (0) or a negative AM_ERR_* code and never
  *    throws; am_last_error() gives a message for the calling thread.
- *  - Pointers are borrowed for the duration of the call only.  An argument
- *    named `mem` says whether the caller's buffers are host (AM_HOST) or
- *    device (AM_DEVICE) memory; host buffers should be pinned for speed.
+ *  - The library keeps no caller pointer after a call.  An argument named
+ *    `mem` says whether the caller's buffers are host (AM_HOST) or device
+ *    (AM_DEVICE) memory; host buffers should be pinned for speed.  Inputs
+ *    are read in stream order: a device buffer or a pinned host buffer
+ *    passed to a call that queues work must stay unchanged until the stream
+ *    has reached that work (a pageable host buffer is read before the call
+ *    returns).
  *  - The handle owns all of its device memory.  Calls on one handle must not
  *    run concurrently from several host threads.
  *  - Work is queued on the CUDA stream passed to am_solve_batch (NULL = the

@@ -439,18 +439,26 @@ int am_solve_batch(am_problem *h, int B, const float *init, const float *warm_la
     h->launches = 0;
     int rc = check_B(h, B);
     if (rc) return rc;
-    CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream), "status reset");
     if (init) {
-        CK(cudaMemcpyAsync(h->d_in, init, sizeof(float) * 33 * B, kind_in(mem), h->stream), "init copy");
-        const float *warm = nullptr;
-        if (warm_lambda) {
-            CK(cudaMemcpyAsync(h->d_in + 33 * size_t(B), warm_lambda, sizeof(float) * 55 * B,
-                               kind_in(mem), h->stream),
-               "warm copy");
-            warm = h->d_in + 33 * size_t(B);
+        // device inputs are read in place by the initial-state launch (which
+        // also resets the status word); host inputs go through the handle's
+        // staging buffer
+        const float *src = init, *warm = warm_lambda;
+        if (mem == AM_HOST) {
+            CK(cudaMemcpyAsync(h->d_in, init, sizeof(float) * 33 * B, cudaMemcpyHostToDevice, h->stream),
+               "init copy");
+            src = h->d_in;
+            if (warm_lambda) {
+                CK(cudaMemcpyAsync(h->d_in + 33 * size_t(B), warm_lambda, sizeof(float) * 55 * B,
+                                   cudaMemcpyHostToDevice, h->stream),
+                   "warm copy");
+                warm = h->d_in + 33 * size_t(B);
+            }
         }
-        if (launch_init_state(h->d_state, h->d_in, warm, B, h->stream, &h->launches))
+        if (launch_init_state(h->d_state, src, warm, B, h->stream, &h->launches, nullptr, h->d_err))
             return fail(AM_ERR_CUDA, "init launch failed");
+    } else {
+        CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream), "status reset");
     }
     h->B = B;
     float *hist = nullptr;
@@ -939,18 +947,22 @@ int am_init_state(am_problem *h, int B, const float *init, const float *warm_lam
     h->stream = static_cast<cudaStream_t>(stream);
     int rc = check_B(h, B);
     if (rc) return rc;
-    CK(cudaMemcpyAsync(h->d_in, init, sizeof(float) * 33 * B, kind_in(mem), h->stream), "init copy");
-    const float *warm = nullptr;
-    if (warm_lambda) {
-        CK(cudaMemcpyAsync(h->d_in + 33 * size_t(B), warm_lambda, sizeof(float) * 55 * B, kind_in(mem),
-                           h->stream),
-           "warm copy");
-        warm = h->d_in + 33 * size_t(B);
+    // device inputs are read in place by the initial-state launch, which also
+    // clears the results and the status word; host inputs are staged first
+    const float *src = init, *warm = warm_lambda;
+    if (mem == AM_HOST) {
+        CK(cudaMemcpyAsync(h->d_in, init, sizeof(float) * 33 * B, cudaMemcpyHostToDevice, h->stream),
+           "init copy");
+        src = h->d_in;
+        if (warm_lambda) {
+            CK(cudaMemcpyAsync(h->d_in + 33 * size_t(B), warm_lambda, sizeof(float) * 55 * B,
+                               cudaMemcpyHostToDevice, h->stream),
+               "warm copy");
+            warm = h->d_in + 33 * size_t(B);
+        }
     }
-    if (launch_init_state(h->d_state, h->d_in, warm, B, h->stream, nullptr))
+    if (launch_init_state(h->d_state, src, warm, B, h->stream, nullptr, h->d_out, h->d_err))
         return fail(AM_ERR_CUDA, "init launch failed");
-    CK(cudaMemsetAsync(h->d_out, 0, sizeof(float) * 4 * B, h->stream), "memset");
-    CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream), "status reset");
     h->B = B;
     h->solved = true;
     return AM_OK;

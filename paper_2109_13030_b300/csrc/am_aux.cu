@@ -16,9 +16,14 @@ namespace {
 // g), so they start at cos / sin of the heading control points: a reference
 // close to the slacks the first step will produce, which keeps the
 // incremental position update of the kernels well scaled.
-__global__ void init_state_kernel(float *state, const float *init, const float *warm, int B)
+// With out (4 B floats: res, res_psi, cost, mind) and err, the same launch
+// clears the results and the status word.
+__global__ void init_state_kernel(float *state, const float *init, const float *warm, int B, float *out,
+                                  int *err)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (out && i < 4 * B) out[i] = 0.f;  // 4 B < B * STATE threads
+    if (err && i == 0) *err = 0;
     if (i >= B * STATE) return;
     const int l = i / STATE, e = i - STATE * l;
     float v = 0.f;
@@ -203,11 +208,11 @@ __global__ void group_argmin_kernel(const FusedProblem *probs, const int *list, 
 }  // namespace
 
 int launch_init_state(float *state, const float *init, const float *warm, int B, void *stream,
-                      int *launches)
+                      int *launches, float *out, int *err)
 {
     const int n = B * STATE;
     init_state_kernel<<<(n + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(state, init,
-                                                                                      warm, B);
+                                                                                      warm, B, out, err);
     if (launches) ++*launches;
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }

@@ -287,8 +287,11 @@ int launch_cem_refit(const CemArgs &a, void *stream);
 // [0, 1] (blossoming): row-major 11 x 11, c' = S c.
 void shift_matrix(double s, double S[121]);
 
+// The initial state from B x 33 initial coefficients and optional B x 55 warm
+// multipliers (device memory, read when the stream reaches the launch); with
+// out and err also clears the 4 B results and the status word.
 int launch_init_state(float *state, const float *init, const float *warm, int B, void *stream,
-                      int *launches);
+                      int *launches, float *out = nullptr, int *err = nullptr);
 // Queues the best selection of a group's last solve on st and copies the
 // records (36 floats per active problem) and the kernels' status words into
 // pinned host memory, without waiting; group_status reads those status words
