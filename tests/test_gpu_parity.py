@@ -307,6 +307,44 @@ def test_device_inputs_equal_host_inputs():
     Q.close()
 
 
+def test_init_state_device_and_host_inputs():
+    """am_init_state reads device inputs in place and clears the results and
+    the status word in its launch: the state from device and from host
+    inputs (with warm multipliers) is the same bit for bit, the results read
+    zero before a solve, and a device input overwritten after the stream has
+    passed the work leaves the state unchanged."""
+    import torch
+    T = tj()
+    pb = W.make_problem("paper", 2, B=24)
+    rng = np.random.default_rng(5)
+    warm = rng.normal(size=(24, 55)).astype(np.float32)
+    init = pb["init"].astype(np.float32)
+    P = T.Problem(pb, kernel=T.AM_KERNEL_WARP)
+    P.solve(init, 3)                      # results and status from a solve
+    T.am_init_state(P.h, 24, init, warm)  # host inputs, staged
+    sh = P.state()
+    r = P.results()
+    assert all(np.all(v == 0) for v in r.values())
+    stream = torch.cuda.current_stream()
+    init_d = torch.tensor(init, device="cuda")
+    warm_d = torch.tensor(warm, device="cuda")
+    T.am_init_state(P.h, 24, init_d, warm_d, stream)  # device inputs, read in place
+    torch.cuda.synchronize()
+    init_d.fill_(float("nan"))
+    warm_d.fill_(float("nan"))
+    sd = P.state()
+    np.testing.assert_array_equal(sd, sh)
+    assert np.all(np.isfinite(sd))
+    # a solve from the device-initialised state equals one from host inputs
+    P.solve(None, 10, stream=stream)
+    a = P.state()
+    Q = T.Problem(pb, kernel=T.AM_KERNEL_WARP)
+    Q.solve(init, 10, warm_lambda=warm)
+    np.testing.assert_array_equal(Q.state(), a)
+    P.close()
+    Q.close()
+
+
 def test_best_selection_matches_oracle_key():
     pb = W.make_problem("tiny", 0)
     g = gpu_solve(pb, 100)
