@@ -826,6 +826,12 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
+        # The clock sampler's NVML reads slow this process's host-side CUDA
+        # calls severalfold, so the host would fall behind the GPU and its
+        # launch gaps would enter the steps' events.  A fixed-length device
+        # delay (a clock-count wait, 60 ms) ahead of the steps lets the host
+        # queue all of them first; it lies outside every step's events.
+        torch.cuda._sleep(int(0.06 * 2.0e9))
         for i in range(args.steps):
             flush.fill_(float(i))
             starts[i].record(stream)
