@@ -733,18 +733,20 @@ def main():
     init_h = torch.tensor(pb["init"], dtype=torch.float32).pin_memory()
     outs = [torch.empty(B, dtype=torch.float32).pin_memory() for _ in range(4)]
     best_h = torch.empty(36, dtype=torch.float32).pin_memory()
+    # numpy views of the pinned buffers, made once
+    init_np, outs_np, best_np = init_h.numpy(), [o.numpy() for o in outs], best_h.numpy()
 
     def e2e_step():
-        TJ.am_solve_batch(P.h, B, init_h.numpy(), None, ITERS, stream)
+        TJ.am_solve_batch(P.h, B, init_np, None, ITERS, stream)
         if dist is None:
             # the selection queued behind the solve into pinned memory; the
             # results read below waits once for the solve, the status and it
-            TJ.am_get_best_async(P.h, best_h, stream)
-            TJ.am_get_results(P.h, *[o.numpy() for o in outs])
-            if not np.isfinite(best_h[1].item()):
+            TJ.am_get_best_async(P.h, best_np, stream)
+            TJ.am_get_results(P.h, *outs_np)
+            if not np.isfinite(best_np[1]):
                 raise RuntimeError("every trajectory of the batch is non-finite")
-            return int(best_h[0].item())
-        TJ.am_get_results(P.h, *[o.numpy() for o in outs])
+            return int(best_np[0])
+        TJ.am_get_results(P.h, *outs_np)
         return merged_best()
 
     for _ in range(2):

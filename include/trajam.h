@@ -135,7 +135,10 @@ AM_API int am_solve_batch(am_problem *h, int B, const float *init, const float *
 /* Per-trajectory results of the last solve, each B floats (NULL to skip):
  * final residual ||F xi1 - g||_2, heading residual ||P xi2 - psi_t||_2, cost
  * sum_t xdd^2 + ydd^2 + psidd^2 (Eq. acc_cost), and the smallest ellipse
- * distance sqrt(xt^2/a^2 + yt^2/b^2) over circles, obstacles and steps. */
+ * distance sqrt(xt^2/a^2 + yt^2/b^2) over circles, obstacles and steps.
+ * Host outputs wait for the handle's stream.  When all four go to host
+ * memory (and 4 B <= 2^22) they arrive through one copy into a pinned area
+ * the handle allocates on first use and keeps; otherwise one copy per array. */
 AM_API int am_get_results(am_problem *h, float *res, float *res_psi, float *cost, float *mind, int mem);
 
 /* The best trajectory of the last solve: lowest cost among those whose

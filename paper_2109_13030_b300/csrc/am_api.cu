@@ -92,6 +92,8 @@ struct am_problem {
     int diag_stall = 0;
     int select = AM_SELECT_COST;
     float *h_best = nullptr;  // pinned: best record (36 floats), status word at 40
+    float *h_out = nullptr;   // pinned: staging of the four result arrays (am_get_results)
+    size_t h_out_cap = 0;
     // CEM comparator: samples, scores, distribution and best of the last run
     float *d_cem = nullptr, *d_score = nullptr;
     size_t cem_cap = 0, score_cap = 0;
@@ -123,6 +125,10 @@ int status_error(int err)
     if (err) return fail(AM_ERR_TIMEOUT, "a kernel gave up a bounded wait (status %d)", err);
     return AM_OK;
 }
+
+// Largest result set (floats, four arrays of B) that am_get_results stages
+// through the handle's pinned area (16 MiB; larger batches copy per array).
+constexpr size_t kStagedResultsMax = size_t(1) << 22;
 
 int wait_stream(am_problem *h)
 {
@@ -297,6 +303,7 @@ void am_destroy(am_problem *h)
     cudaFree(h->d_cem);
     cudaFree(h->d_score);
     if (h->h_best) cudaFreeHost(h->h_best);
+    if (h->h_out) cudaFreeHost(h->h_out);
     if (h->ev) cudaEventDestroy(h->ev);
     if (h->order_ev) cudaEventDestroy(h->order_ev);
     delete h;
@@ -509,6 +516,24 @@ int am_get_results(am_problem *h, float *res, float *res_psi, float *cost, float
     if (!h->solved) return fail(AM_ERR_STATE, "no solve yet");
     if (mem != AM_HOST && mem != AM_DEVICE) return fail(AM_ERR_ARG, "bad mem flag");
     float *dst[4] = {res, res_psi, cost, mind};
+    const size_t nb = size_t(h->B);
+    if (mem == AM_HOST && res && res_psi && cost && mind && 4 * nb <= kStagedResultsMax) {
+        // all four to host memory: one copy of the contiguous result arrays
+        // into the handle's pinned staging area, then host copies
+        if (h->h_out_cap < 4 * nb) {
+            if (h->h_out) cudaFreeHost(h->h_out);  // no copy into it is pending
+            h->h_out = nullptr;
+            h->h_out_cap = 0;
+            CK(cudaMallocHost(&h->h_out, sizeof(float) * 4 * nb), "result staging area");
+            h->h_out_cap = 4 * nb;
+        }
+        CK(cudaMemcpyAsync(h->h_out, h->d_out, sizeof(float) * 4 * nb, cudaMemcpyDeviceToHost, h->stream),
+           "result copy");
+        const int rc = wait_stream(h);
+        if (rc) return rc;
+        for (int i = 0; i < 4; ++i) std::memcpy(dst[i], h->h_out + i * nb, sizeof(float) * nb);
+        return AM_OK;
+    }
     for (int i = 0; i < 4; ++i)
         if (dst[i])
             CK(cudaMemcpyAsync(dst[i], h->d_out + size_t(i) * h->B, sizeof(float) * h->B,
