@@ -138,6 +138,7 @@ def summary_sections(extra: dict) -> dict:
         if "auto" in u:
             out["uneven"]["auto_value"] = u["auto"]["value"]
             out["uneven"]["auto_ms"] = u["auto"]["ms_per_solve"]
+            out["uneven"]["auto_slots_cap"] = u["auto"].get("warp_slots_cap")
     if "precision" in extra:
         pr = extra["precision"]
         out["precision_b4096"] = {k: {"value": v["value"], **({"dev10": v["coef_dev_vs_fp32_after_10"]["max"]}
@@ -339,7 +340,8 @@ def bench_uneven(TJ, W, torch, dev, flush, steps: int, iters: int = 100) -> dict
     probs = [TJ.Problem(pb, kernel=TJ.AM_KERNEL_AUTO) for pb in pbs]
     reset()
     G = TJ.Group(probs)
-    G.autotune(iters, stream=side)
+    G.autotune(iters, stream=side)   # here: the cap on the warp-pair kernels' slots per CTA
+    a_slots = G.warp_slots()
     for _ in range(2):
         reset()
         G.solve(iters, stream=side)
@@ -363,7 +365,7 @@ def bench_uneven(TJ, W, torch, dev, flush, steps: int, iters: int = 100) -> dict
     return {"metric": "trajectory-AM-iterations/sec over 64 mixed problems", "value": total * iters / (g_ms / 1e3),
             "bf16": {"value": total * iters / (b_ms / 1e3), "unit": UNIT, "ms_per_solve": b_ms},
             "auto": {"value": total * iters / (a_ms / 1e3), "unit": UNIT, "ms_per_solve": a_ms,
-                     "launches_per_solve": a_launches,
+                     "launches_per_solve": a_launches, "warp_slots_cap": a_slots,
                      "problems_two_warps": sum(1 for pb in pbs if pb["q"] <= 128),
                      "problems_three_warps": sum(1 for pb in pbs if 128 < pb["q"] <= 192)},
             "unit": UNIT, "ms_per_solve": g_ms, "problems": len(pbs), "trajectories": total,

@@ -361,14 +361,26 @@ AM_API int am_group_create(am_problem *const *problems, int count, am_group **ou
 /* Runs iters iterations of every problem of the group; asynchronous. */
 AM_API int am_group_solve(am_group *g, int iters, void *stream);
 /* Times the group's solve over the block sizes that fit every problem and
- * keeps the fastest; the problems' states are restored afterwards.  Writes
- * the chosen block size and its time per solve (ms). */
+ * keeps the fastest; with problems on the warp-pair kernels, then over caps
+ * on their trajectory slots per CTA (none, 7 .. 3) and keeps the fastest.
+ * The problems' states are restored afterwards.  Writes the chosen block
+ * size and the time per solve (ms) of the chosen settings. */
 AM_API int am_group_autotune(am_group *g, int iters, void *stream, int *threads, float *ms);
-/* AM_GOPT_THREADS: block size (0 = largest, else a multiple of 32).
- * AM_GOPT_GRAPH: 1 = capture and replay on non-default streams (default). */
+/* AM_GOPT_THREADS: block size of the small-tile group kernels (0 = largest,
+ * else a multiple of 32).
+ * AM_GOPT_GRAPH: 1 = capture and replay on non-default streams (default).
+ * AM_GOPT_WARP_SLOTS: at most this many trajectory slots per CTA in the
+ * warp-pair group kernels (0 = as many as fit shared memory, the default;
+ * else 1..AM_GROUP_MAX_WARP_SLOTS).
+ * am_group_autotune sets AM_GOPT_THREADS and, when the group has problems
+ * on the warp-pair kernels, AM_GOPT_WARP_SLOTS; am_group_get_option reads
+ * any of them back. */
 #define AM_GOPT_THREADS 1
 #define AM_GOPT_GRAPH 2
+#define AM_GOPT_WARP_SLOTS 3
+#define AM_GROUP_MAX_WARP_SLOTS 8
 AM_API int am_group_set_option(am_group *g, int option, int value);
+AM_API int am_group_get_option(am_group *g, int option, int *value);
 /* Restricts the following solves (and am_group_get_best) to the listed
  * problems, given by their position in am_group_create's array, each at most
  * once, in any order; count = 0 selects every problem again.  A captured

@@ -656,6 +656,7 @@ struct am_group {
     std::vector<am_problem *> probs;
     std::vector<int> active;  // problems the next solve advances; empty = all
     int threads = 0;          // block size; 0 = tuned or the kernel maximum
+    int warp_slots = 0;       // cap on the warp-pair variants' trajectory slots per CTA; 0 = as many as fit
     bool use_graph = true;
     // One upload region per solve, device and pinned host copies:
     //   [count per variant, list offset per variant] [descriptors]
@@ -739,7 +740,8 @@ int build_work(am_group *g, int threads, int iters, int sms)
     for (int i = 0; i < np; ++i) {
         const int v = problem_variant(g->probs[i]);
         if (v < kGroupWarpVariant0) continue;
-        const int t = warp_group_traj(g->probs[i]->L);
+        int t = warp_group_traj(g->probs[i]->L);
+        if (g->warp_slots > 0 && t > g->warp_slots) t = g->warp_slots;
         if (g->vslots[v] == 0 || t < g->vslots[v]) g->vslots[v] = t;
     }
     for (int i = 0; i < np; ++i) {
@@ -1289,7 +1291,23 @@ int am_group_set_option(am_group *g, int option, int value)
         if (!g->use_graph) drop_graph(g);
         return AM_OK;
     }
+    if (option == AM_GOPT_WARP_SLOTS) {
+        if (value < 0 || value > AM_GROUP_MAX_WARP_SLOTS)
+            return fail(AM_ERR_ARG, "warp slots must be in [0, %d]", AM_GROUP_MAX_WARP_SLOTS);
+        g->warp_slots = value;
+        return AM_OK;
+    }
     return fail(AM_ERR_ARG, "unknown group option %d", option);
+}
+
+int am_group_get_option(am_group *g, int option, int *value)
+{
+    if (!g || !value) return fail(AM_ERR_ARG, "null argument");
+    if (option == AM_GOPT_THREADS) *value = g->threads;
+    else if (option == AM_GOPT_GRAPH) *value = g->use_graph ? 1 : 0;
+    else if (option == AM_GOPT_WARP_SLOTS) *value = g->warp_slots;
+    else return fail(AM_ERR_ARG, "unknown group option %d", option);
+    return AM_OK;
 }
 
 int am_group_set_active(am_group *g, const int *idx, int count)
@@ -1414,28 +1432,54 @@ int am_group_autotune(am_group *g, int iters, void *stream, int *threads_out, fl
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const int saved = g->threads;
-    int best = 0;
-    float best_ms = 1e30f;
-    for (int threads = 128; threads <= fused_max_threads(); threads += 64) {
-        g->threads = threads;
-        if (build_work(g, threads, iters, sms) != AM_OK) continue;
-        if (am_group_solve(g, iters, stream) != AM_OK) continue;  // warm-up (and graph capture)
+    const int saved = g->threads, saved_slots = g->warp_slots;
+    bool has_small = false, has_warp = false;
+    for (const am_problem *h : g->probs) (problem_variant(h) >= kGroupWarpVariant0 ? has_warp : has_small) = true;
+    // average time of three solves in the current settings (a warm-up, which
+    // also captures the graph, first); < 0 when they do not run
+    auto time_solves = [&]() -> float {
+        if (build_work(g, g->threads > 0 ? g->threads : fused_max_threads(), iters, sms) != AM_OK) return -1.f;
+        if (am_group_solve(g, iters, stream) != AM_OK) return -1.f;
         cudaEventRecord(e0, st);
         for (int r = 0; r < 3; ++r) am_group_solve(g, iters, stream);
         cudaEventRecord(e1, st);
-        if (wait_event(g->ev, st) != AM_OK) break;
+        if (wait_event(g->ev, st) != AM_OK) return -1.f;
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
-        ms /= 3.f;
-        if (ms < best_ms) {
+        return ms / 3.f;
+    };
+    // the small-tile variants' block size (the warp-pair variants' block is
+    // their slot count times 32 NW and does not depend on it)
+    int best = 0;
+    float best_ms = 1e30f;
+    for (int threads = 128; threads <= fused_max_threads(); threads += 64) {
+        if (!has_small && threads != fused_max_threads()) continue;
+        g->threads = threads;
+        const float ms = time_solves();
+        if (ms >= 0.f && ms < best_ms) {
             best_ms = ms;
             best = threads;
         }
     }
+    g->threads = best ? best : saved;
+    // then the warp-pair variants' trajectory slots per CTA: as many as fit
+    // (0), or at most 7 .. 3
+    int best_slots = saved_slots;
+    if (has_warp && best) {
+        float slots_ms = 1e30f;
+        for (int cap : {0, 7, 6, 5, 4, 3}) {
+            g->warp_slots = cap;
+            const float ms = time_solves();
+            if (ms >= 0.f && ms < slots_ms) {
+                slots_ms = ms;
+                best_slots = cap;
+            }
+        }
+        if (slots_ms < 1e30f) best_ms = slots_ms;
+    }
+    g->warp_slots = best_slots;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    g->threads = best ? best : saved;
     o = 0;
     for (am_problem *h : g->probs) {
         CK(cudaMemcpyAsync(h->d_state, g->d_save + o, sizeof(float) * STATE * h->B,

@@ -22,7 +22,7 @@ AM_FP32, AM_TF32, AM_BF16, AM_SPLIT_BF16 = 0, 1, 2, 3
 AM_KERNEL_FUSED, AM_KERNEL_PLAIN, AM_KERNEL_LARGE, AM_KERNEL_WARP, AM_KERNEL_AUTO = 0, 1, 2, 3, 4
 AM_OPT_KERNEL, AM_OPT_TILE, AM_OPT_DIAG_STALL, AM_OPT_SELECT = 1, 2, 3, 4
 AM_SELECT_COST, AM_SELECT_CLEARANCE = 0, 1
-AM_GOPT_THREADS, AM_GOPT_GRAPH = 1, 2
+AM_GOPT_THREADS, AM_GOPT_GRAPH, AM_GOPT_WARP_SLOTS = 1, 2, 3
 AM_PENDING = 1
 AM_SRV_BATCHED, AM_SRV_SEQUENTIAL = 0, 1
 AM_REQ_GOAL, AM_REQ_RESAMPLE, AM_REQ_SHIFT, AM_REQ_SCALE_LAMBDA = 1, 2, 4, 8
@@ -33,7 +33,7 @@ EXPORTS = ["am_init_problem", "am_set_obstacles", "am_set_boundary", "am_solve_b
            "am_get_history", "am_set_option", "am_set_stream", "am_last_solve_stats",
            "am_solve_batch_noalloc", "am_init_state", "am_resample", "am_shift", "am_scale_multipliers", "am_plan_eval", "am_cem_solve",
            "am_cem_get_best", "am_cem_get_samples", "am_cem_score", "am_group_create", "am_group_solve",
-           "am_group_autotune", "am_group_set_option", "am_group_set_active", "am_group_get_best",
+           "am_group_autotune", "am_group_set_option", "am_group_get_option", "am_group_set_active", "am_group_get_best",
            "am_group_stats", "am_group_destroy", "am_server_create", "am_server_add_scene",
            "am_server_start", "am_server_submit", "am_server_poll", "am_server_stats",
            "am_server_destroy", "am_scene_bytes", "am_destroy", "am_last_error"]
@@ -114,6 +114,7 @@ def _load():
         "am_group_solve": ([vp, ip, vp], ip),
         "am_group_autotune": ([vp, ip, vp, C.POINTER(C.c_int), C.POINTER(C.c_float)], ip),
         "am_group_set_option": ([vp, ip, ip], ip),
+        "am_group_get_option": ([vp, ip, C.POINTER(C.c_int)], ip),
         "am_group_stats": ([vp, C.POINTER(C.c_int), C.POINTER(C.c_int)], ip),
         "am_group_set_active": ([vp, C.POINTER(C.c_int), ip], ip),
         "am_group_get_best": ([vp, fp, ip, vp], ip),
@@ -373,6 +374,12 @@ def am_group_set_option(g, option, value):
     _check(_lib.am_group_set_option(g, int(option), int(value)))
 
 
+def am_group_get_option(g, option) -> int:
+    v = C.c_int()
+    _check(_lib.am_group_get_option(g, int(option), C.byref(v)))
+    return v.value
+
+
 def am_group_stats(g):
     n, k = C.c_int(), C.c_int()
     _check(_lib.am_group_stats(g, C.byref(n), C.byref(k)))
@@ -484,6 +491,7 @@ class Problem:
         self.h = am_init_problem(self.desc)
         self.q, self.m, self.n = int(pb["q"]), int(pb["m"]), int(pb["n"])
         self.precision = int(precision)
+        self.kernel = int(kernel)
         self.B = 0
         self.iters = 0
         am_set_option(self.h, AM_OPT_KERNEL, kernel)
@@ -569,21 +577,29 @@ class Group:
         return self
 
     def autotune(self, iters, stream=None, cache=None, sms=0):
-        """Time the block sizes and keep the fastest; with cache (a JSON path),
-        reuse a choice stored for the same shapes, precision, SM count and
+        """Time the block sizes (and, with problems on the warp-pair kernels,
+        the caps on their trajectory slots per CTA) and keep the fastest;
+        returns (threads, ms).  With cache (a JSON path), reuse a choice
+        stored for the same shapes, kernel choices, precision, SM count and
         iterations (sms: the device's SM count, part of the key)."""
         if cache is None:
             return am_group_autotune(self.g, iters, stream)
         from . import tune_cache
         k = tune_cache.key([(p.q, p.m, p.n, p.B) for p in self.problems],
-                           self.problems[0].precision, sms, iters)
+                           self.problems[0].precision, sms, iters, [p.kernel for p in self.problems])
         hit = tune_cache.lookup(cache, k)
         if hit is not None:
             am_group_set_option(self.g, AM_GOPT_THREADS, hit[0])
-            return hit
+            am_group_set_option(self.g, AM_GOPT_WARP_SLOTS, hit[2])
+            return hit[0], hit[1]
         threads, ms = am_group_autotune(self.g, iters, stream)
-        tune_cache.store(cache, k, threads, ms)
+        tune_cache.store(cache, k, threads, ms, am_group_get_option(self.g, AM_GOPT_WARP_SLOTS))
         return threads, ms
+
+    def warp_slots(self):
+        """The cap on the warp-pair group kernels' trajectory slots per CTA
+        (0: as many as fit)."""
+        return am_group_get_option(self.g, AM_GOPT_WARP_SLOTS)
 
     def stats(self):
         return am_group_stats(self.g)

@@ -1,11 +1,12 @@
-"""Persistent cache of the grouped launch's autotuned block size.
+"""Persistent cache of the grouped launch's autotuned settings.
 
 The autotuner (am_group_autotune) times the block sizes that fit every
-problem of a group and keeps the fastest.  The choice depends on the shapes
-in the group, not on the data, so it is stored in a JSON file keyed by the
+problem of a group, and the caps on the warp-pair group kernels' trajectory
+slots per CTA, and keeps the fastest.  The choice depends on the shapes in
+the group, not on the data, so it is stored in a JSON file keyed by the
 sorted problem shapes (q, m, n, batch rounded to a power of two), the
-precision form, the SM count and the iteration count; a later group of the
-same key reuses it without timing.
+problems' kernel choices, the precision form, the SM count and the
+iteration count; a later group of the same key reuses it without timing.
 """
 from __future__ import annotations
 
@@ -21,9 +22,12 @@ def batch_bucket(B: int) -> int:
     return b
 
 
-def key(shapes, precision: int, sms: int, iters: int) -> str:
-    """shapes: iterable of (q, m, n, B) per problem."""
-    norm = sorted((int(q), int(m), int(n), batch_bucket(int(B))) for q, m, n, B in shapes)
+def key(shapes, precision: int, sms: int, iters: int, kernels=None) -> str:
+    """shapes: iterable of (q, m, n, B) per problem; kernels: the problems'
+    kernel options in the same order (None: the small-tile default for all)."""
+    shapes = list(shapes)
+    ks = [0] * len(shapes) if kernels is None else [int(k) for k in kernels]
+    norm = sorted((int(q), int(m), int(n), batch_bucket(int(B)), k) for (q, m, n, B), k in zip(shapes, ks))
     return json.dumps({"shapes": norm, "precision": int(precision), "sms": int(sms), "iters": int(iters)},
                       sort_keys=True)
 
@@ -38,16 +42,17 @@ def load(path: str) -> dict:
 
 
 def lookup(path: str, k: str):
-    """(threads, ms) stored for key k, or None."""
+    """(threads, ms, warp_slots) stored for key k, or None (an entry without
+    warp_slots reads 0: as many as fit)."""
     v = load(path).get(k)
     if isinstance(v, dict) and "threads" in v:
-        return int(v["threads"]), float(v.get("ms", 0.0))
+        return int(v["threads"]), float(v.get("ms", 0.0)), int(v.get("warp_slots", 0))
     return None
 
 
-def store(path: str, k: str, threads: int, ms: float) -> None:
+def store(path: str, k: str, threads: int, ms: float, warp_slots: int = 0) -> None:
     data = load(path)
-    data[k] = {"threads": int(threads), "ms": float(ms)}
+    data[k] = {"threads": int(threads), "ms": float(ms), "warp_slots": int(warp_slots)}
     tmp = path + ".tmp"
     with open(tmp, "w") as f:
         json.dump(data, f, indent=1, sort_keys=True)

@@ -207,7 +207,7 @@ def test_group_autotune_cache(tmp_path):
     G.close()
     from paper_2109_13030_b300 import tune_cache
     k = tune_cache.key([(pb["q"], pb["m"], pb["n"], pb["B"]) for pb in pbs], 0, 148, 10)
-    assert tune_cache.lookup(cache, k) == (threads, ms)
+    assert tune_cache.lookup(cache, k) == (threads, ms, 0)  # no warp-pair problems: no slot cap
     tune_cache.store(cache, k, 256, 0.5)
     G = T.Group(probs)
     assert G.autotune(10, cache=cache, sms=148) == (256, 0.5)

@@ -73,6 +73,36 @@ def test_auto_group_equals_alone_bit_for_bit_and_oracle():
         check_oracle(pb, g)
 
 
+def test_autotune_picks_a_warp_slot_cap_and_every_cap_gives_the_same_bits():
+    """The autotuner times caps on the warp-pair group kernels' trajectory
+    slots per CTA and keeps one; since a trajectory's arithmetic does not
+    depend on the CTA slot that runs it, every cap gives the same bits."""
+    T = tj()
+    pbs = mix(count=6, seed=12)
+    states = {}
+    for cap in (None, 0, 5, 3, 1):
+        probs = [T.Problem(pb, kernel=T.AM_KERNEL_AUTO).init_state(pb["init"].astype(np.float32)) for pb in pbs]
+        G = T.Group(probs)
+        if cap is None:
+            threads, ms = G.autotune(10)
+            assert G.warp_slots() in (0, 7, 6, 5, 4, 3) and ms > 0
+        else:
+            T.am_group_set_option(G.g, T.AM_GOPT_WARP_SLOTS, cap)
+            assert G.warp_slots() == cap
+        G.solve(10)
+        states[cap] = [P.state() for P in probs]
+        G.close()
+        for P in probs:
+            P.close()
+    for cap in (0, 5, 3, 1):
+        for a, b in zip(states[cap], states[None]):
+            np.testing.assert_array_equal(a, b)
+    G = T.Group([T.Problem(pbs[0], kernel=T.AM_KERNEL_AUTO).init_state(pbs[0]["init"].astype(np.float32))])
+    with pytest.raises(T.TrajamError):
+        T.am_group_set_option(G.g, T.AM_GOPT_WARP_SLOTS, 9)
+    G.close()
+
+
 def test_warp_group_equals_warp_alone():
     """Every problem selects AM_KERNEL_WARP: the same bits as lone warp-pair
     solves, also when the captured launch is replayed on a stream."""
