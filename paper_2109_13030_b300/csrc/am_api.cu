@@ -438,30 +438,34 @@ int am_solve_batch(am_problem *h, int B, const float *init, const float *warm_la
     if (h->kernel == AM_KERNEL_WARP && (h->tile < 0 || h->tile > warp_max_traj(h->L)))
         return fail(AM_ERR_ARG, "the warp-pair kernel runs 1..%d trajectories per CTA at q = %d (tile %d)",
                     warp_max_traj(h->L), h->pp.q, h->tile);
-    if (mem == AM_HOST) {
-        if (init && !finite_floats(init, size_t(B) * 33)) return fail(AM_ERR_ARG, "non-finite initial coefficients");
-        if (warm_lambda && !finite_floats(warm_lambda, size_t(B) * 55)) return fail(AM_ERR_ARG, "non-finite warm multipliers");
-    }
     h->stream = static_cast<cudaStream_t>(stream);
     h->launches = 0;
+    const float *src = init, *warm = warm_lambda;
+    if (init && mem == AM_HOST) {
+        // The copies to the handle's staging buffer are queued first and the
+        // inputs checked while they run.  A non-finite input returns before
+        // anything reads the staging buffer and before the state is touched
+        // (check_B below may reallocate it).
+        int rc = ensure(h->d_in, h->in_cap, size_t(B) * (33 + 55), "input staging");
+        if (rc) return rc;
+        CK(cudaMemcpyAsync(h->d_in, init, sizeof(float) * 33 * B, cudaMemcpyHostToDevice, h->stream), "init copy");
+        src = h->d_in;
+        if (warm_lambda) {
+            CK(cudaMemcpyAsync(h->d_in + 33 * size_t(B), warm_lambda, sizeof(float) * 55 * B,
+                               cudaMemcpyHostToDevice, h->stream),
+               "warm copy");
+            warm = h->d_in + 33 * size_t(B);
+        }
+        if (!finite_floats(init, size_t(B) * 33)) return fail(AM_ERR_ARG, "non-finite initial coefficients");
+        if (warm_lambda && !finite_floats(warm_lambda, size_t(B) * 55))
+            return fail(AM_ERR_ARG, "non-finite warm multipliers");
+    }
     int rc = check_B(h, B);
     if (rc) return rc;
     if (init) {
         // device inputs are read in place by the initial-state launch (which
-        // also resets the status word); host inputs go through the handle's
-        // staging buffer
-        const float *src = init, *warm = warm_lambda;
-        if (mem == AM_HOST) {
-            CK(cudaMemcpyAsync(h->d_in, init, sizeof(float) * 33 * B, cudaMemcpyHostToDevice, h->stream),
-               "init copy");
-            src = h->d_in;
-            if (warm_lambda) {
-                CK(cudaMemcpyAsync(h->d_in + 33 * size_t(B), warm_lambda, sizeof(float) * 55 * B,
-                                   cudaMemcpyHostToDevice, h->stream),
-                   "warm copy");
-                warm = h->d_in + 33 * size_t(B);
-            }
-        }
+        // also resets the status word); host inputs come from the staging
+        // buffer
         if (launch_init_state(h->d_state, src, warm, B, h->stream, &h->launches, nullptr, h->d_err))
             return fail(AM_ERR_CUDA, "init launch failed");
     } else {

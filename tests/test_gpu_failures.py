@@ -44,6 +44,19 @@ def test_non_finite_host_inputs_refused():
         P.solve(init, 5)
     assert e.value.code == T.AM_ERR_ARG
     P.solve(pb["init"].astype(np.float32), 5)   # the handle is unharmed
+    # a refused input for a larger batch leaves the state of the last solve
+    # as it was: its warm continuation equals an undisturbed one
+    big = np.tile(pb["init"].astype(np.float32), (3, 1, 1))
+    big[7, 1, 4] = np.nan
+    with pytest.raises(T.TrajamError) as e:
+        T.am_solve_batch(P.h, 12, big, None, 5)
+    assert e.value.code == T.AM_ERR_ARG
+    P.solve(None, 5)
+    Q = T.Problem(pb)
+    Q.solve(pb["init"].astype(np.float32), 5)
+    Q.solve(None, 5)
+    np.testing.assert_array_equal(P.state(), Q.state())
+    Q.close()
     P.close()
 
 
