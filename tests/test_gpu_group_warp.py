@@ -103,6 +103,36 @@ def test_autotune_picks_a_warp_slot_cap_and_every_cap_gives_the_same_bits():
     G.close()
 
 
+_MIX_ORACLE = {}
+
+
+@pytest.mark.parametrize("kernel", ["auto", "small_tile"])
+def test_full_size_uneven_mix_sampled_against_the_oracle(kernel):
+    """The benchmark's uneven mix at full size (64 problems, B 128..2048, about
+    70 k trajectories) in one grouped solve of 10 iterations; the first and
+    the last trajectory of every problem (the first and last tiles) against
+    the FP64 oracle, with the mix's noise-derived tolerance."""
+    from test_gpu_group import coef_tolerance
+    from test_gpu_parity import assert_coefs
+    T = tj()
+    k = T.AM_KERNEL_AUTO if kernel == "auto" else T.AM_KERNEL_FUSED
+    pbs = W.make_uneven(0, count=64)
+    assert sum(pb["B"] for pb in pbs) > 60000
+    probs = [T.Problem(pb, kernel=k).init_state(pb["init"].astype(np.float32)) for pb in pbs]
+    G = T.Group(probs)
+    G.solve(10)
+    for i, (pb, P) in enumerate(zip(pbs, probs)):
+        st = T.split_state(P.state())
+        idx = [0, pb["B"] - 1]
+        if i not in _MIX_ORACLE:  # shared by both kernels' runs
+            _MIX_ORACLE[i] = coef_tolerance(dict(pb, init=pb["init"][idx], B=len(idx)), 10)
+        o, tol = _MIX_ORACLE[i]
+        assert_coefs({key: st[key][idx] for key in ("xi1", "xi2")}, o, tol=tol)
+    G.close()
+    for P in probs:
+        P.close()
+
+
 def test_warp_group_equals_warp_alone():
     """Every problem selects AM_KERNEL_WARP: the same bits as lone warp-pair
     solves, also when the captured launch is replayed on a stream."""
