@@ -102,6 +102,41 @@ def test_request_arriving_during_a_round_overlaps_it():
         assert r["cost"] == a["cost"]
 
 
+@pytest.mark.parametrize("kernel", ["small_tile", "auto"])
+def test_full_size_scenes_alone_equal_in_a_round(kernel):
+    """Four scenes of the benchmark's serving mix at full size (batches of a
+    few hundred to 2048 trajectories), 30 iterations per request: each scene
+    served alone, then all four in one grouped round, give the same bits."""
+    T = tj()
+    k = T.AM_KERNEL_AUTO if kernel == "auto" else T.AM_KERNEL_FUSED
+    pbs = W.make_uneven(0, count=64)[:4]
+    assert max(pb["B"] for pb in pbs) > 1000
+
+    def serve(ks, start_after_submit):
+        S = T.Server(8 * GB, 30)
+        probs = []
+        for pb in pbs:
+            P = T.Problem(pb, kernel=k)
+            S.add_scene(P, pb["init"].astype(np.float32))
+            probs.append(P)
+        if not start_after_submit:
+            S.start()
+        tickets = [S.submit(i) for i in ks]
+        if start_after_submit:
+            S.start()
+        out = [S.wait(t) for t in tickets]
+        close(S, probs)
+        return out
+
+    alone = [serve([i], False)[0] for i in range(len(pbs))]
+    mixed = serve(range(len(pbs)), True)
+    assert all(r["status"] == 0 for r in alone + mixed)
+    assert all(r["batch"] == len(pbs) and r["round"] == 0 for r in mixed)
+    for a, m in zip(alone, mixed):
+        np.testing.assert_array_equal(np.asarray(m["coeffs"]), np.asarray(a["coeffs"]))
+        assert m["cost"] == a["cost"] and m["index"] == a["index"]
+
+
 def test_round_groups_from_three_admissible_requests():
     """Two queued requests for different scenes go to two lanes as rounds of
     one (grouping two costs what two launches cost); three queued requests
