@@ -721,10 +721,15 @@ def main():
         TJ.am_solve_batch(P.h, B, None, None, ITERS, stream)     # the fused kernel
         if i is not None:
             kends[i].record(stream)
+        TJ.am_get_best_async(P.h, best_d, stream)                # selection on the device, no host wait
         if dist is None:
-            TJ.am_get_best_async(P.h, best_d, stream)            # selection on the device, no host wait
             return None
-        return merged_best()
+        # sharded batch: the cross-rank merge on the device too (the local
+        # best's collision flag from its smallest distance, one all-gather
+        # of every rank's key and coefficients, the lexicographic minimum)
+        TJ.am_get_results(P.h, mind=mind_d)
+        collides = mind_d.index_select(0, best_d[0:1].long()) < 0.99
+        return D.merge_best_device(best_d, collides, lo)
 
     # Host-facing measurements first, before any clock sampling: reading the
     # GPU's clocks through NVML (nvidia-smi, or the library in-process) slows

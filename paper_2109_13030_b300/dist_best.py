@@ -44,3 +44,34 @@ def merge_best(collides: bool, cost: float, global_index: int, coeffs, device, g
                    group=group)
     return dict(coeffs=buf.reshape(3, 11), cost=best_cost, index=best_idx, collides=bool(flag),
                 rank=owner)
+
+
+def merge_best_device(record, collides, offset: int, group=None):
+    """The same merge with every step on the tensors' device and no host
+    synchronisation, for use inside a stream of queued work.
+
+    record: the rank's local best as the 36-float selection record (index,
+    cost, residual, then the 33 coefficients c_x, c_y, c_psi), e.g. what
+    am_get_best_async writes to device memory; collides: a one-element bool
+    or float tensor (the record's trajectory collides); offset: the global
+    index of the rank's first trajectory.  Every rank gathers every rank's
+    key and coefficients in one all-gather and takes the lexicographically
+    smallest key (collision-free first, then cost, then global index; a
+    non-finite cost ranks last).  Returns the winner as a 36-float record on
+    the same device, its index global."""
+    world = dist.get_world_size(group)
+    rec = record.reshape(36).to(torch.float64)
+    col = collides.reshape(1).to(torch.float64)
+    cost = rec[1:2]
+    flag = torch.where(torch.isfinite(cost), col, torch.full_like(col, 2.0))
+    row = torch.cat([flag, torch.nan_to_num(cost, nan=float("inf")), rec[0:1] + float(offset), rec[1:36]])
+    rows = [torch.empty_like(row) for _ in range(world)]
+    dist.all_gather(rows, row, group=group)
+    table = torch.stack(rows)                       # [world, 38]: flag, cost, gidx, cost, residual, coeffs
+    inf = torch.full_like(table[:, 0], float("inf"))
+    m = table[:, 0] == table[:, 0].min()
+    c = torch.where(m, table[:, 1], inf)
+    m = m & (table[:, 1] == c.min())
+    w = torch.argmin(torch.where(m, table[:, 2], inf))
+    win = table[w]
+    return torch.cat([win[2:3], win[3:5], win[5:38]]).to(record.dtype)

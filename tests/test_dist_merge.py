@@ -45,8 +45,12 @@ def worker(rank, world, port, pb, iters, out):
     o = O.solve(sub, iters)
     collides, cost, gidx, coeffs = local_best(o, lo)
     best = D.merge_best(collides, cost, gidx, coeffs, torch.device("cpu"))
+    # the device-side form on the same local bests (record: local index,
+    # cost, residual, coefficients)
+    rec = torch.tensor([gidx - lo, cost, 0.0, *coeffs.ravel()], dtype=torch.float32)
+    win = D.merge_best_device(rec, torch.tensor([collides]), lo)
     out[rank] = (best["index"], best["cost"], best["collides"], best["rank"],
-                 best["coeffs"].numpy().copy())
+                 best["coeffs"].numpy().copy(), win.numpy().copy())
     dist.barrier()
     dist.destroy_process_group()
 
@@ -69,10 +73,13 @@ def test_merge_matches_whole_batch(world):
     whole = O.solve(pb, iters)
     collides, cost, gidx, coeffs = local_best(whole, 0)
     for r in range(world):
-        idx, c, col, owner, co = res[r]
+        idx, c, col, owner, co, win = res[r]
         assert idx == gidx and col == collides
         assert c == pytest.approx(cost, rel=1e-12)
         np.testing.assert_array_equal(co, coeffs)
+        # the device-side merge picks the same trajectory on every rank
+        assert int(win[0]) == gidx and win[1] == np.float32(cost)
+        np.testing.assert_array_equal(win[3:], coeffs.ravel())
     # the owner is the rank whose range holds the winner
     from paper_2109_13030_b300 import dist_best as D
     lo, hi = D.shard_range(pb["B"], res[0][3], world)
@@ -86,6 +93,26 @@ def test_shard_ranges_cover_batch():
             spans = [D.shard_range(B, r, world) for r in range(world)]
             assert spans[0][0] == 0 and spans[-1][1] == B
             assert all(a[1] == b[0] for a, b in zip(spans, spans[1:]))
+
+
+def test_device_merge_order_single_rank_rules():
+    """The device-side merge's ordering on one gloo rank (world 1): the
+    record comes back with its index made global, and a non-finite cost is
+    kept as it is."""
+    import torch
+    import torch.distributed as dist
+    from paper_2109_13030_b300 import dist_best as D
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(free_port()))
+    dist.init_process_group("gloo", rank=0, world_size=1)
+    try:
+        rec = torch.arange(36, dtype=torch.float32)
+        win = D.merge_best_device(rec, torch.tensor([False]), 100)
+        assert win[0] == 100 and torch.equal(win[1:], rec[1:])
+        rec[1] = float("nan")
+        win = D.merge_best_device(rec, torch.tensor([True]), 5)
+        assert win[0] == 5 and torch.isnan(win[1])
+    finally:
+        dist.destroy_process_group()
 
 
 def test_key_order():
