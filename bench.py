@@ -139,6 +139,8 @@ def summary_sections(extra: dict) -> dict:
             out["uneven"]["auto_value"] = u["auto"]["value"]
             out["uneven"]["auto_ms"] = u["auto"]["ms_per_solve"]
             out["uneven"]["auto_slots_cap"] = u["auto"].get("warp_slots_cap")
+            out["uneven"]["auto_frac"] = u["auto"].get("frac_of_fp32_peak")
+            out["uneven"]["auto_frac_finer"] = u["auto"].get("frac_finer_count")
     if "precision" in extra:
         pr = extra["precision"]
         out["precision_b4096"] = {k: {"value": v["value"], **({"dev10": v["coef_dev_vs_fp32_after_10"]["max"]}
@@ -306,6 +308,8 @@ def bench_uneven(TJ, W, torch, dev, flush, steps: int, iters: int = 100) -> dict
         seq.append(e0.elapsed_time(e1))
     total = sum(pb["B"] for pb in pbs)
     flops = sum(algorithmic_flops(pb["q"], pb["m"], pb["n"]) * pb["B"] for pb in pbs) * iters
+    flops_scope = sum(survey_flops(pb["q"], pb["m"], pb["n"]) * pb["B"] for pb in pbs) * iters
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     g_ms, s_ms = statistics.mean(ms), statistics.mean(seq)
     G.close()
     for P in probs:
@@ -366,6 +370,8 @@ def bench_uneven(TJ, W, torch, dev, flush, steps: int, iters: int = 100) -> dict
             "bf16": {"value": total * iters / (b_ms / 1e3), "unit": UNIT, "ms_per_solve": b_ms},
             "auto": {"value": total * iters / (a_ms / 1e3), "unit": UNIT, "ms_per_solve": a_ms,
                      "launches_per_solve": a_launches, "warp_slots_cap": a_slots,
+                     "frac_of_fp32_peak": flops_scope / (a_ms / 1e3) / 1e12 / peak_fp32_tflops(sms),
+                     "frac_finer_count": flops / (a_ms / 1e3) / 1e12 / peak_fp32_tflops(sms),
                      "problems_two_warps": sum(1 for pb in pbs if pb["q"] <= 128),
                      "problems_three_warps": sum(1 for pb in pbs if 128 < pb["q"] <= 192)},
             "unit": UNIT, "ms_per_solve": g_ms, "problems": len(pbs), "trajectories": total,
