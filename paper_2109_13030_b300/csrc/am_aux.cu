@@ -3,6 +3,9 @@
 #include <cuda_runtime.h>
 
 #include <cfloat>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "am_internal.h"
 #include "am_rng.cuh"
@@ -206,6 +209,21 @@ __global__ void group_argmin_kernel(const FusedProblem *probs, const int *list, 
 }
 
 }  // namespace
+
+int raise_smem_limit(const void *kernel, size_t smem)
+{
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, size_t> limit;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return int(e);
+    std::lock_guard<std::mutex> lk(mu);
+    size_t &cur = limit[{kernel, dev}];
+    if (smem <= cur) return 0;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e == cudaSuccess) cur = smem;
+    return int(e);
+}
 
 int launch_init_state(float *state, const float *init, const float *warm, int B, void *stream,
                       int *launches, float *out, int *err)

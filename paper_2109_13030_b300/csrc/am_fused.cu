@@ -1149,8 +1149,7 @@ int launch_group(const GroupLaunch &g, void *stream, int *launches, const char *
     switch (g.variant) {
 #define AM_GCASE(MM, LL, PP)                                                                    \
     case PP * 8 + MM * 2 + LL - 2:                                                              \
-        e = cudaFuncSetAttribute(am_group_kernel<MM, LL, PP>,                                   \
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, int(g.smem));     \
+        e = cudaError_t(raise_smem_limit(reinterpret_cast<const void *>(am_group_kernel<MM, LL, PP>), g.smem)); \
         if (e != cudaSuccess) {                                                                 \
             *why = cudaGetErrorString(e);                                                       \
             return -2;                                                                          \

@@ -207,6 +207,12 @@ constexpr int kGroupVariants = 44;
 // Dynamic shared memory a warp-pair group kernel may take (its problem
 // descriptor and work-item slot are static shared memory).
 constexpr size_t kGroupSmemLimit = 227 * 1024 - 1024;
+// Raises a kernel's dynamic shared-memory limit on the current device to at
+// least smem and never lowers it, so that a CUDA graph captured with a larger
+// launch of the kernel stays launchable after smaller launches (a profiler
+// re-launches graph nodes one at a time with the function's current limit).
+// Returns 0 (cudaSuccess) or the cudaError_t of the failed call.
+int raise_smem_limit(const void *kernel, size_t smem);
 struct GroupLaunch {
     const FusedProblem *d_probs;  // device array, one per problem
     const int *d_items;           // device array of (problem, tile) pairs, all variants

@@ -1205,8 +1205,7 @@ int launch_warp_mn(const FusedProblem &p, int T, size_t smem, int grid, cudaStre
 template <int M, int NW>
 cudaError_t launch_group_warp_mn(const GroupLaunch &g, cudaStream_t st)
 {
-    cudaError_t r = cudaFuncSetAttribute(am_group_warp_kernel<M, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         int(g.smem));
+    cudaError_t r = cudaError_t(raise_smem_limit(reinterpret_cast<const void *>(am_group_warp_kernel<M, NW>), g.smem));
     if (r != cudaSuccess) return r;
     am_group_warp_kernel<M, NW><<<g.grid, g.slots * WS<NW>::kThreads, g.smem, st>>>(
         g.d_probs, g.d_items, g.d_head, g.d_ctl, g.variant);
