@@ -3,9 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cfloat>
-#include <map>
 #include <mutex>
-#include <utility>
 
 #include "am_internal.h"
 #include "am_rng.cuh"
@@ -212,17 +210,15 @@ __global__ void group_argmin_kernel(const FusedProblem *probs, const int *list, 
 
 int raise_smem_limit(const void *kernel, size_t smem)
 {
+    // the current limit is read back each time (a device reset clears it);
+    // the lock keeps two threads from lowering each other's setting
     static std::mutex mu;
-    static std::map<std::pair<const void *, int>, size_t> limit;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return int(e);
     std::lock_guard<std::mutex> lk(mu);
-    size_t &cur = limit[{kernel, dev}];
-    if (smem <= cur) return 0;
-    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e == cudaSuccess) cur = smem;
-    return int(e);
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return int(e);
+    if (smem <= size_t(fa.maxDynamicSharedSizeBytes)) return 0;
+    return int(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
 }
 
 int launch_init_state(float *state, const float *init, const float *warm, int B, void *stream,

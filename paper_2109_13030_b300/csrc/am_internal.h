@@ -211,6 +211,7 @@ constexpr size_t kGroupSmemLimit = 227 * 1024 - 1024;
 // least smem and never lowers it, so that a CUDA graph captured with a larger
 // launch of the kernel stays launchable after smaller launches (a profiler
 // re-launches graph nodes one at a time with the function's current limit).
+// Thread-safe.
 // Returns 0 (cudaSuccess) or the cudaError_t of the failed call.
 int raise_smem_limit(const void *kernel, size_t smem);
 struct GroupLaunch {
