@@ -207,6 +207,14 @@ constexpr int kGroupVariants = 44;
 // Dynamic shared memory a warp-pair group kernel may take (its problem
 // descriptor and work-item slot are static shared memory).
 constexpr size_t kGroupSmemLimit = 227 * 1024 - 1024;
+// The closed-form obstacle step in the ellipse-scaled frame (Eq. zeta_2,
+// compute_zeta_3): offset (xh, yh) of a circle centre from the obstacle's,
+// projected to (xh, yh) max(1, 1/|.|).  kCoincideX is added to xh, so that a
+// centre exactly at the obstacle's takes the direction +x (alpha = atan2(0,
+// 0) = 0, d = 1: the point (a, 0)), as the oracle does; it rounds away
+// unless |xh| < 2e-8.  kTinyD keeps the squared norm positive.
+constexpr float kCoincideX = 1e-15f;
+constexpr float kTinyD = 2e-38f;
 // Raises a kernel's dynamic shared-memory limit on the current device to at
 // least smem and never lowers it, so that a CUDA graph captured with a larger
 // launch of the kernel stays launchable after smaller launches (a profiler

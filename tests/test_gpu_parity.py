@@ -345,6 +345,25 @@ def test_init_state_device_and_host_inputs():
     Q.close()
 
 
+@pytest.mark.parametrize("kernel", [0, 1, 2, 3])  # small-tile, plain, large-batch, warp-pair
+def test_circle_exactly_at_an_obstacle_centre(kernel):
+    """A degenerate case of the obstacle step: an obstacle parked at the start
+    (0, 0), where the robot's middle circle (offset 0, heading 0) sits at
+    step 0 of every iteration, exactly at the obstacle's centre.  The
+    direction is undefined there; like the oracle (atan2(0, 0) = 0), every
+    kernel pushes that circle to (a, 0)."""
+    pb = W.make_problem("paper", 4, B=16)
+    xo, yo = pb["xo"].copy(), pb["yo"].copy()
+    xo[0, :] = 0.0
+    yo[0, :] = 0.0
+    pb = dict(pb, xo=xo, yo=yo)
+    assert pb["x_bc"][0] == 0 and pb["y_bc"][0] == 0 and pb["psi_bc"][0] == 0 and 0.0 in list(pb["r"])
+    o = O.solve(pb, 10)
+    g = gpu_solve(pb, 10, kernel=kernel)
+    assert_coefs(g, o)
+    assert np.all(g["mind"] < 1e-6) and np.all(o["mind"] < 1e-6)   # the start is inside the obstacle
+
+
 def test_best_selection_matches_oracle_key():
     pb = W.make_problem("tiny", 0)
     g = gpu_solve(pb, 100)
