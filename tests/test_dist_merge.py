@@ -120,3 +120,46 @@ def test_key_order():
     assert D.key_of(False, 5.0, 9) < D.key_of(True, 1.0, 0)
     assert D.key_of(False, 1.0, 9) < D.key_of(False, 2.0, 0)
     assert D.key_of(False, 1.0, 3) < D.key_of(False, 1.0, 4)
+
+
+def rules_worker(rank, world, port, cases, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import torch
+    import torch.distributed as dist
+    from paper_2109_13030_b300 import dist_best as D
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    res = []
+    for case in cases:
+        idx, cost, collides, offset = case[rank]
+        rec = torch.zeros(36, dtype=torch.float32)
+        rec[0], rec[1] = float(idx), float(cost)
+        rec[3:] = float(rank + 1)  # coefficients tell the owner apart
+        win = D.merge_best_device(rec, torch.tensor([collides]), offset)
+        res.append((int(win[0]), float(win[3])))
+    out[rank] = res
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_device_merge_rules_on_two_ranks():
+    """Equal costs go to the lower global index; a collision-free trajectory
+    beats a cheaper colliding one; a non-finite cost ranks last."""
+    cases = [
+        [(3, 5.0, False, 0), (0, 5.0, False, 10)],              # tie: global 3 < 10
+        [(2, 1.0, True, 0), (4, 9.0, False, 10)],               # collision-free first: global 14
+        [(1, float("nan"), False, 0), (7, 50.0, True, 10)],     # non-finite last: global 17
+        [(0, 2.0, False, 0), (0, 1.0, False, 10)],              # lower cost: global 10
+    ]
+    expect = [(3, 1.0), (14, 2.0), (17, 2.0), (10, 2.0)]
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as man:
+        out = man.dict()
+        port = free_port()
+        procs = [ctx.Process(target=rules_worker, args=(r, 2, port, cases, out)) for r in range(2)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(120)
+            assert p.exitcode == 0
+        res = dict(out)
+    assert res[0] == res[1] == expect
