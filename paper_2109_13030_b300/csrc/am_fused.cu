@@ -740,13 +740,13 @@ __device__ __forceinline__ void sweep_pair(float *sm, const Smem &S, const Const
         const float2 ia = f2(ci.x, ci.y), ib = f2(ci.z, ci.w), aa = f2(ca.x, ca.y), bb = f2(ca.z, ca.w);
 #pragma unroll
         for (int i = 0; i < M; ++i) {
-            const float2 xh = fadd2(ffma2(X[i], ia, ox), dup2(kCoincideX));  // (x + r_i cos psi - x_j) / a_j
+            const float2 xh = ffma2(X[i], ia, ox);  // (x + r_i cos psi - x_j) / a_j
             const float2 yh = ffma2(Y[i], ib, oy);
             const float2 D = ffma2(xh, xh, ffma2(yh, yh, dup2(kTinyD)));
             float2 tx, ty;
             if (!LIT) {
                 const float2 h = f2(fmaxf(rsqrtf(D.x), 1.f) - 1.f, fmaxf(rsqrtf(D.y), 1.f) - 1.f);  // max(1, 1/d) - 1
-                tx = fmul2(xh, h);
+                tx = fmul2(fadd2(xh, dup2(kCoincideT)), h);  // see kCoincideT
                 ty = fmul2(yh, h);
             } else {
                 literal_offset(xh.x, yh.x, ca.x, ca.z, ci.x, ci.z, tx.x, ty.x);

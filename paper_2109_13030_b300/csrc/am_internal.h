@@ -208,13 +208,16 @@ constexpr int kGroupVariants = 44;
 // descriptor and work-item slot are static shared memory).
 constexpr size_t kGroupSmemLimit = 227 * 1024 - 1024;
 // The closed-form obstacle step in the ellipse-scaled frame (Eq. zeta_2,
-// compute_zeta_3): offset (xh, yh) of a circle centre from the obstacle's,
-// projected to (xh, yh) max(1, 1/|.|).  kCoincideX is added to xh, so that a
-// centre exactly at the obstacle's takes the direction +x (alpha = atan2(0,
-// 0) = 0, d = 1: the point (a, 0)), as the oracle does; it rounds away
-// unless |xh| < 2e-8.  kTinyD keeps the squared norm positive.
-constexpr float kCoincideX = 1e-15f;
+// compute_zeta_3): the offset (xh, yh) of a circle centre from the
+// obstacle's is projected to (xh, yh) max(1, 1/|.|), a correction of
+// (xh, yh) h with h = max(1, 1/sqrt(D)) - 1 and D = xh^2 + yh^2 + kTinyD
+// (kTinyD keeps D positive).  The x part is (xh + kCoincideT) h, where
+// kCoincideT = sqrt(kTinyD).  A centre exactly at the obstacle's (D =
+// kTinyD) then gets the correction (1, 0), the oracle's alpha = atan2(0, 0)
+// = 0 with d = 1 (the point (a, 0)).  kCoincideT rounds away unless
+// |xh| < 3e-12, and the add runs beside the rsqrt, not after it.
 constexpr float kTinyD = 2e-38f;
+constexpr float kCoincideT = 1.4142135e-19f;
 // Raises a kernel's dynamic shared-memory limit on the current device to at
 // least smem and never lowers it, so that a CUDA graph captured with a larger
 // launch of the kernel stays launchable after smaller launches (a profiler

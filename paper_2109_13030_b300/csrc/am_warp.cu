@@ -440,11 +440,11 @@ __device__ __forceinline__ void sweep_pair(const float *cob, const ConstLayout &
         const float2 ia = f2(ci.x, ci.y), ib = f2(ci.z, ci.w), aa = f2(ca.x, ca.y), bb = f2(ca.z, ca.w);
 #pragma unroll
         for (int i = 0; i < M; ++i) {
-            const float2 xh = fadd2(ffma2(X[i], ia, ox), dup2(kCoincideX));  // (x + r_i cos psi - x_j) / a_j
+            const float2 xh = ffma2(X[i], ia, ox);  // (x + r_i cos psi - x_j) / a_j
             const float2 yh = ffma2(Y[i], ib, oy);
             const float2 D = ffma2(xh, xh, ffma2(yh, yh, dup2(kTinyD)));
             const float2 h = f2(fmaxf(rsqrtf(D.x), 1.f) - 1.f, fmaxf(rsqrtf(D.y), 1.f) - 1.f);  // max(1, 1/d) - 1
-            const float2 tx = fmul2(xh, h), ty = fmul2(yh, h);
+            const float2 tx = fmul2(fadd2(xh, dup2(kCoincideT)), h), ty = fmul2(yh, h);  // see kCoincideT
             if (RES) {
                 const float2 ex = fmul2(aa, tx), ey = fmul2(bb, ty);
                 ax[i] = fadd2(ax[i], ex);
